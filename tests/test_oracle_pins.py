@@ -1,0 +1,523 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of the paper (or the mathematical fact) it pins.
+A plausible mistake in the oracle -- a dropped term, a wrong sign, a
+transposed V, a wrong index in the ordering -- fails at least one of them:
+
+* closed form of the 2x2 symmetric eigenproblem; off^2 drops by exactly
+  2 a_pq^2 per rotation (Sec. 1);
+* diagonal input -> no rotation, Q = I bit-exactly;
+* matrices built with a known spectrum; trace / Frobenius invariance;
+  the block form of the off^2 identity over one parallel step (Algorithm 2);
+* exact characteristic-polynomial roots (rational arithmetic + Sturm
+  bisection) for n <= 4;
+* LAPACK (numpy) as an independent accuracy witness; mpmath in 40 digits for
+  the relative accuracy on a graded DHD matrix;
+* the paper's printed ordering list, label matrix and transformation
+  patterns (Sec. 3, eqs. (disjoint), (group_one_transformation),
+  (alt_transformations), (parallel_list); Algorithm 3);
+* Gram block as a sum over row tiles (Sec. 6, eq. after (SVD_subproblem)).
+"""
+from __future__ import annotations
+
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as gen
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+U = 2.0 ** -53
+
+
+def _offsq(A):
+    A = np.asarray(A)
+    return float(np.sum(A * A) - np.sum(np.diag(A) ** 2))
+
+
+# ------------------------------------------------------------------ 2x2 / one rotation
+def test_rotation_matches_2x2_closed_form():
+    r = np.random.default_rng(11)
+    for _ in range(2000):
+        a, b, c = r.standard_normal(3) * 10.0 ** r.uniform(-3, 3, 3)
+        cs, sn, t = oracle.rotation(a, c, b)
+        J = np.array([[cs, sn], [-sn, cs]])
+        M = np.array([[a, b], [b, c]])
+        D = J.T @ M @ J
+        scale = np.abs(M).max()
+        assert abs(D[0, 1]) <= 8 * U * scale
+        # closed-form eigenvalues (a+c)/2 -+ sqrt(((a-c)/2)^2 + b^2)
+        mid, rad = 0.5 * (a + c), np.hypot(0.5 * (a - c), b)
+        lo, hi = mid - rad, mid + rad
+        got = sorted([a - t * b, c + t * b])
+        assert abs(got[0] - lo) <= 8 * U * scale and abs(got[1] - hi) <= 8 * U * scale
+        assert abs(cs * cs + sn * sn - 1.0) <= 4 * U
+        assert abs(t) <= 1.0  # |angle| <= pi/4 (inner rotation)
+
+
+def test_rotation_large_zeta_branch():
+    cs, sn, t = oracle.rotation(0.0, 1e300, 1e-10)
+    assert cs == 1.0 and abs(t - 0.5 / (1e300 / 2e-10)) <= 1e-16 * abs(t)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_rotation_drops_off2_by_2apq2(seed):
+    r = np.random.default_rng(seed)
+    n = 9
+    A = gen.sym_gaussian(n, 100 + seed)
+    p, q = sorted(r.choice(n, 2, replace=False))
+    apq = A[p, q]
+    A2, Q2, applied = oracle.rotate(A, np.eye(n), p, q)
+    assert applied and A2[p, q] == 0.0 and A2[q, p] == 0.0
+    assert abs(_offsq(A2) - (_offsq(A) - 2 * apq * apq)) <= 1e-13 * _offsq(A)
+    # similarity: Q A2 Q^T == A, Q orthogonal
+    assert np.abs(Q2 @ A2 @ Q2.T - A).max() <= 1e-14 * np.abs(A).max() * n
+    assert np.abs(Q2.T @ Q2 - np.eye(n)).max() <= 4 * U * n
+    assert np.allclose(np.linalg.eigvalsh(A2), np.linalg.eigvalsh(A), atol=1e-13, rtol=0)
+
+
+def test_zero_entry_is_not_rotated():
+    A = np.diag([1.0, 2.0, 3.0])
+    A2, Q2, applied = oracle.rotate(A, np.eye(3), 0, 2)
+    assert not applied and np.array_equal(A2, A) and np.array_equal(Q2, np.eye(3))
+
+
+# ------------------------------------------------------------------ special inputs
+@pytest.mark.parametrize("scalar", [False, True])
+def test_diagonal_input_no_rotation(scalar):
+    d = np.array([-3.0, -1.0, 0.0, 0.5, 2.0, 7.0, 7.5, 9.0, 11.0, 12.0])
+    A = np.diag(d)
+    w, Q, Af, st, status = oracle.syev(A, b=2, scalar=scalar)
+    assert status == 0 and st.rotations == 0 and st.sweeps == 0
+    assert np.array_equal(w, d) and np.array_equal(Q, np.eye(len(d)))
+
+
+def test_sorted_output_permutes_q():
+    d = np.array([3.0, -1.0, 2.0, 0.0])
+    w, Q, *_ = oracle.syev(np.diag(d), b=1)
+    assert np.array_equal(w, np.sort(d))
+    P = np.eye(4)[:, np.argsort(d, kind="stable")]
+    assert np.array_equal(Q, P)
+
+
+# ------------------------------------------------------------------ known spectrum
+@pytest.mark.parametrize("b,ordering,kind", [
+    (8, oracle.ORDER_ROUND_ROBIN, "uniform"),
+    (5, oracle.ORDER_ROUND_ROBIN, "uniform"),     # ragged: 64 = 12*5 + 4
+    (8, oracle.ORDER_ANTI_DIAGONAL, "uniform"),
+    (8, oracle.ORDER_ROUND_ROBIN, "graded"),
+    (64, oracle.ORDER_ROUND_ROBIN, "uniform"),    # n <= b: a single padded pair
+])
+def test_known_spectrum_blocked(b, ordering, kind):
+    n = 64
+    A, lam = gen.sym_known(n, kind, seed=21)
+    w, Q, Af, st, status = oracle.syev(A, b=b, ordering=ordering)
+    nrm2 = np.abs(lam).max()
+    assert status == 0
+    assert np.abs(w - np.sort(lam)).max() <= 1e-13 * nrm2
+    assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * n
+
+
+def test_known_spectrum_scalar():
+    n = 48
+    A, lam = gen.sym_known(n, "uniform", seed=22)
+    w, Q, Af, st, status = oracle.syev(A, scalar=True)
+    assert status == 0
+    assert np.abs(w - np.sort(lam)).max() <= 1e-13
+    assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_trace_and_frobenius_invariance_through_steps():
+    n, b = 40, 4
+    A = gen.sym_gaussian(n, 31)
+    N = oracle.padded_blocks(n, b)
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)
+    Q = np.eye(n)
+    tr0, fr0 = np.trace(A), np.linalg.norm(A)
+    Ak = A.copy()
+    for s in range(len(tab)):
+        Ak, Q, _ = oracle.syev_step(Ak, Q, b, tab[s])
+        assert abs(np.trace(Ak) - tr0) <= 1e-13 * fr0
+        assert abs(np.linalg.norm(Ak) - fr0) <= 1e-13 * fr0
+    assert np.abs(Q @ Ak @ Q.T - A).max() <= 1e-13 * fr0
+
+
+def test_block_off2_identity_over_one_step():
+    """off^2(A') = off^2(A) - sum_p (off^2(Ahat_p) - off^2(Dhat_p)) (Algorithm 2:
+    every non-pivot block is multiplied by orthogonal factors only, and the
+    pivot blocks are replaced by Dhat)."""
+    n, b = 48, 6
+    A = gen.sym_gaussian(n, 32)
+    N = oracle.padded_blocks(n, b)
+    step = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)[3]
+    drop = 0.0
+    for (I, J) in step:
+        idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+        Ah = A[np.ix_(idx, idx)]
+        D, V, rot, sw = oracle.pivot_solve(Ah)
+        drop += _offsq(Ah) - _offsq(D)
+    A2, _, _ = oracle.syev_step(A, None, b, step)
+    assert abs(_offsq(A2) - (_offsq(A) - drop)) <= 1e-12 * np.sum(A * A)
+
+
+def test_step_pivot_blocks_hold_dhat_and_match_explicit_product():
+    """The update formulas of Algorithm 2 applied to the pivot itself give
+    Vhat^T Ahat Vhat = Dhat, and the step writes Dhat there."""
+    n, b = 32, 4
+    A = gen.sym_gaussian(n, 33)
+    N = oracle.padded_blocks(n, b)
+    step = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)[0]
+    A2, _, _ = oracle.syev_step(A, None, b, step)
+    W = np.eye(n)
+    for (I, J) in step:
+        idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+        Ah = A[np.ix_(idx, idx)]
+        D, V, rot, sw = oracle.pivot_solve(Ah)
+        assert np.abs(V.T @ Ah @ V - D).max() <= 1e-14 * np.abs(Ah).max() * 2 * b
+        assert np.array_equal(A2[np.ix_(idx, idx)], D)
+        W[np.ix_(idx, idx)] = V
+    # the whole step is A' = W^T A W off the pivot blocks (W = direct sum of Vhat)
+    ref = W.T @ A @ W
+    assert np.abs(A2 - ref).max() <= 1e-13 * np.abs(A).max() * n
+
+
+def test_pivot_solve_orthogonal_and_diagonal():
+    Ah = gen.sym_gaussian(32, 34)
+    D, V, rot, sw = oracle.pivot_solve(Ah)
+    assert rot > 0 and sw >= 2
+    assert np.abs(V.T @ V - np.eye(32)).max() <= 1e-14
+    od = np.abs(D - np.diag(np.diag(D)))
+    dd = np.sqrt(np.abs(np.diag(D)))
+    assert (od <= 4 * U * np.outer(dd, dd) + 1e-300).all()
+    assert np.allclose(np.sort(np.diag(D)), np.linalg.eigvalsh(Ah), atol=1e-13, rtol=0)
+
+
+def test_inner_sweep_cap_gives_approximate_solve():
+    Ah = gen.sym_gaussian(32, 35)
+    D, V, rot, sw = oracle.pivot_solve(Ah, max_sweeps=1)
+    assert sw == 1 and _offsq(D) > 0 and _offsq(D) < _offsq(Ah)
+    assert np.abs(V.T @ Ah @ V - D).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ brute force n <= 4
+def _charpoly_exact(A):
+    """Coefficients (highest first) of det(x I - A) in exact rationals, by
+    Faddeev-LeVerrier: M_0 = 0, c_n = 1; M_k = A M_{k-1} + c_{n-k+1} I,
+    c_{n-k} = -tr(A M_k)/k."""
+    n = len(A)
+    F = [[Fraction(float(A[i][j])) for j in range(n)] for i in range(n)]
+    coeffs = [Fraction(1)]
+    M = [[Fraction(0)] * n for _ in range(n)]
+    c_prev = Fraction(1)
+    for k in range(1, n + 1):
+        AM = [[sum(F[i][l] * M[l][j] for l in range(n)) for j in range(n)] for i in range(n)]
+        M = [[AM[i][j] + (c_prev if i == j else 0) for j in range(n)] for i in range(n)]
+        AMk = [[sum(F[i][l] * M[l][j] for l in range(n)) for j in range(n)] for i in range(n)]
+        c = -sum(AMk[i][i] for i in range(n)) / k
+        coeffs.append(c)
+        c_prev = c
+    return coeffs
+
+
+def _peval(p, x):
+    v = Fraction(0)
+    for c in p:
+        v = v * x + c
+    return v
+
+
+def _prem(a, b):
+    a = list(a)
+    while len(a) >= len(b) and any(a):
+        f = a[0] / b[0]
+        for i in range(len(b)):
+            a[i] -= f * b[i]
+        a.pop(0)
+    while a and a[0] == 0:
+        a.pop(0)
+    return a
+
+
+def _sturm_roots(p, lo, hi, iters=80):
+    deriv = [c * (len(p) - 1 - i) for i, c in enumerate(p[:-1])]
+    chain = [p, deriv]
+    while len(chain[-1]) > 1:
+        r = _prem(chain[-2], chain[-1])
+        if not r:
+            break
+        chain.append([-c for c in r])
+
+    def count(x):  # sign changes of the chain at x
+        s = [_peval(q, x) for q in chain]
+        s = [v for v in s if v != 0]
+        return sum(1 for a, b in zip(s, s[1:]) if (a > 0) != (b > 0))
+
+    n = len(p) - 1
+    roots = []
+    for kth in range(n):  # kth smallest root: count(lo) - count(x) = #roots in (lo, x]
+        a, b = Fraction(lo), Fraction(hi)
+        c_lo = count(a)
+        for _ in range(iters):
+            mid = (a + b) / 2
+            if c_lo - count(mid) > kth:
+                b = mid
+            else:
+                a = mid
+            a = Fraction(float(a)) if _ % 8 == 7 else a
+        roots.append(float((a + b) / 2))
+    return roots
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("seed", [40, 41, 42])
+def test_brute_force_charpoly_roots(n, seed):
+    A = gen.sym_gaussian(n, seed)
+    p = _charpoly_exact(A)
+    R = float(np.abs(A).sum(axis=1).max()) + 1.0
+    roots = _sturm_roots(p, -R, R)
+    for scalar in (False, True):
+        w, Q, *_ = oracle.syev(A, b=1, scalar=scalar)
+        assert np.abs(w - np.array(roots)).max() <= 1e-14 * max(1.0, np.abs(roots).max())
+
+
+# ------------------------------------------------------------------ LAPACK witness
+@pytest.mark.parametrize("n,b", [(100, 8), (77, 10)])
+def test_lapack_witness(n, b):
+    A = gen.sym_gaussian(n, 50 + n)
+    w, Q, Af, st, status = oracle.syev(A, b=b)
+    wl = np.linalg.eigvalsh(A)
+    nrm2 = np.abs(wl).max()
+    assert status == 0 and st.sweeps >= 3
+    assert np.abs(w - wl).max() <= 1e-13 * nrm2
+    assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * n
+    assert st.off_final <= 1e-14 * st.norm_fro or st.stalled
+
+
+def test_blocked_and_scalar_agree_and_sweep_history_decreases():
+    A = gen.sym_gaussian(60, 61)
+    w1, *_ , st1, _ = oracle.syev(A, b=6)
+    w2, *_ , st2, _ = oracle.syev(A, scalar=True)
+    assert np.abs(w1 - w2).max() <= 1e-13 * np.abs(w1).max()
+    h = st1.off_hist
+    assert all(h[i + 1] < h[i] for i in range(len(h) - 1))
+
+
+def test_max_sweeps_reports_nonconvergence():
+    A = gen.sym_gaussian(40, 62)
+    w, Q, Af, st, status = oracle.syev(A, b=4, max_sweeps=1)
+    assert status == 1 and st.sweeps == 1
+
+
+# ------------------------------------------------------------------ padding
+def test_padding_is_exact():
+    """b that does not divide n: zero rows/columns stay exactly zero, so the
+    ragged run equals the run on the explicitly zero-padded matrix."""
+    n, b = 10, 4
+    A = gen.sym_gaussian(n, 70)
+    Ap = np.zeros((12, 12), order="F")
+    Ap[:n, :n] = A
+    w, Q, Af, st, s1 = oracle.syev(A, b=b)
+    wp, Qp, Afp, stp, s2 = oracle.syev(Ap, b=b)
+    assert st.rotations == stp.rotations and st.sweeps == stp.sweeps
+    # the padded run has two extra exact zero eigenvalues; removing them gives w
+    z = np.where(wp == 0.0)[0]
+    assert len(z) >= 2
+    keep = np.ones(12, bool)
+    keep[z[:2]] = False
+    assert np.array_equal(wp[keep], w)
+    assert np.all(Afp[n:, :] == 0.0) and np.all(Afp[:, n:] == 0.0)
+
+
+def test_padding_inside_a_step():
+    n, b = 12, 4
+    A = np.zeros((n, n), order="F")
+    A[:10, :10] = gen.sym_gaussian(10, 71)
+    tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, 3)
+    Ak = A
+    for step in tab:
+        Ak, _, _ = oracle.syev_step(Ak, None, b, step)
+        assert np.all(Ak[10:, :] == 0.0) and np.all(Ak[:, 10:] == 0.0)
+
+
+# ------------------------------------------------------------------ graded spectra
+def test_graded_dhd_relative_accuracy_vs_mpmath():
+    mpmath = pytest.importorskip("mpmath")
+    n = 24
+    A, d, H = gen.graded_dhd(n, seed=4)
+    mpmath.mp.dps = 40
+    ev = mpmath.eigsy(mpmath.matrix(A.tolist()), eigvals_only=True)
+    exact = np.sort(np.array([float(x) for x in ev]))
+    w, Q, Af, st, status = oracle.syev(A, b=4, conv=oracle.CONV_REL, tol=4 * U)
+    assert status == 0
+    assert exact.min() > 0 and exact.max() / exact.min() > 1e10
+    assert np.abs(w - exact).max() / 1.0 <= 1e-12 * exact.max()
+    assert (np.abs(w - exact) / exact).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ orderings
+def _read_groups():
+    out = []
+    for line in open(os.path.join(GOLD, "anti_diagonal_N8_list.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        out.append({tuple(int(x) - 1 for x in tok.split(",")) for tok in line.split()})
+    return out
+
+
+def test_algorithm3_matches_printed_list():
+    printed = _read_groups()
+    tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, 8)
+    assert len(tab) == 8 and len(printed) == 8
+    assert {frozenset(g) for g in tab} == {frozenset(g) for g in printed}
+    # our group K holds the pairs with (I+J) mod 8 == K (1-based); the printed
+    # list is ordered by label l = 1..8 with K = (2 - l) mod 8
+    for ell, g in enumerate(printed, start=1):
+        assert set(tab[(2 - ell) % 8]) == g
+
+
+def test_algorithm3_matches_printed_label_matrix():
+    tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, 8)
+    label = {}
+    for K, g in enumerate(tab):
+        for (I, J) in g:
+            label[(I, J)] = (2 - K) % 8 or 8
+    rows = [l.split() for l in open(os.path.join(GOLD, "anti_diagonal_N8_labels.txt"))
+            if l.strip() and not l.startswith("#")]
+    for I, row in enumerate(rows):
+        for k, tok in enumerate(row):
+            assert label[(I, I + 1 + k)] == int(tok)
+
+
+@pytest.mark.parametrize("fname,ell", [("group_one_pattern.txt", 1), ("group_two_pattern.txt", 2)])
+def test_transformation_patterns(fname, ell):
+    tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, 8)
+    group = sorted(tab[(2 - ell) % 8], key=lambda p: -p[0])  # numbered in printed order
+    owner = {}
+    for t, (I, J) in enumerate(group, start=1):
+        owner[I] = t
+        owner[J] = t
+    rows = [l.split() for l in open(os.path.join(GOLD, fname))
+            if l.strip() and not l.startswith("#")]
+    for I, row in enumerate(rows):
+        for k, tok in enumerate(row):
+            J = I + k
+            L, R = owner.get(I), owner.get(J)
+            if L is not None and L == R:
+                want = f"{L}*"
+            else:
+                want = f"{L if L else '_'}{R if R else '_'}"
+            assert tok == want, (I, J, tok, want)
+
+
+@pytest.mark.parametrize("N", list(range(2, 41, 2)))
+def test_round_robin_covers_every_pair_once(N):
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)
+    assert len(tab) == N - 1
+    seen = set()
+    for g in tab:
+        assert len(g) == N // 2
+        used = [x for p in g for x in p]
+        assert len(set(used)) == len(used)  # disjoint
+        for (I, J) in g:
+            assert 0 <= I < J < N
+            seen.add((I, J))
+    assert len(seen) == N * (N - 1) // 2
+
+
+@pytest.mark.parametrize("N", list(range(2, 30)))
+def test_anti_diagonal_covers_every_pair_once(N):
+    tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, N)
+    assert len(tab) == N
+    allp = [p for g in tab for p in g]
+    assert len(allp) == len(set(allp)) == N * (N - 1) // 2
+    for K, g in enumerate(tab):
+        used = [x for p in g for x in p]
+        assert len(set(used)) == len(used)
+        assert all((I + 1 + J + 1) % N == K for (I, J) in g)
+        assert len(g) in (N // 2, N // 2 - 1, (N - 1) // 2)
+
+
+# ------------------------------------------------------------------ one-sided SVD
+def test_hestenes_rotation_orthogonalises_two_columns():
+    G = gen.tall_gaussian(50, 2, 80, dtype=np.float64)
+    U, s, V, st, status = oracle.gesvd(G, b=1, scalar=True, max_sweeps=1)
+    Gr = U * s[None, :]
+    assert abs(Gr[:, 0] @ Gr[:, 1]) <= 1e-15 * s[0] * s[1] * 50
+    sl = np.linalg.svd(G, compute_uv=False)
+    assert np.abs(s - sl).max() <= 1e-14 * sl[0]
+
+
+@pytest.mark.parametrize("scalar,b", [(False, 4), (False, 6), (True, 1)])
+def test_known_singular_values(scalar, b):
+    m, n = 200, 40
+    G, sig = gen.svd_known(m, n, seed=81, decades=6.0)
+    U, s, V, st, status = oracle.gesvd(G, b=b, scalar=scalar)
+    assert status == 0
+    assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+    big = sig >= 1e-3 * sig[0]
+    assert (np.abs(s - sig)[big] / sig[big]).max() <= 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
+
+
+def test_svd_lapack_witness_and_zero_column():
+    m, n = 90, 30
+    G = gen.tall_gaussian(m, n, 82, dtype=np.float64)
+    G[:, 7] = 0.0
+    U, s, V, st, status = oracle.gesvd(G, b=4)
+    sl = np.linalg.svd(G, compute_uv=False)
+    assert status == 0
+    assert np.abs(s - sl).max() <= 1e-13 * sl[0]
+    assert s[-1] == 0.0 and np.all(U[:, -1] == 0.0)
+    assert np.all(np.isfinite(U))
+
+
+def test_gram_is_sum_over_row_tiles():
+    m, b = 300, 5
+    G = gen.tall_gaussian(m, 20, 83, dtype=np.float64)
+    full = oracle.gram_pair(G, b, 1, 3)
+    idx = np.r_[1 * b:2 * b, 3 * b:4 * b]
+    assert np.abs(full - G[:, idx].T @ G[:, idx]).max() <= 1e-13 * m
+    parts = sum(oracle.gram_pair(G[r:r + 64], b, 1, 3) for r in range(0, m, 64))
+    assert np.abs(parts - full).max() <= 1e-13 * m
+
+
+def test_svd_step_returns_pre_rotation_measure():
+    m, b = 60, 3
+    G = gen.tall_gaussian(m, 12, 84, dtype=np.float64)
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, 4)
+    G2, V2, r = oracle.gesvd_step(G, np.eye(12), b, tab[0], tol_rel=1e-15)
+    want = 0.0
+    for (I, J) in tab[0]:
+        idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+        Ah = G[:, idx].T @ G[:, idx]
+        d = np.sqrt(np.diag(Ah))
+        R = np.abs(Ah) / np.outer(d, d)
+        np.fill_diagonal(R, 0)
+        want = max(want, R.max())
+    assert abs(r - want) <= 1e-13
+    assert np.abs(G2 @ V2.T - G).max() <= 1e-13 * np.abs(G).max() * 12
+
+
+# ------------------------------------------------------------------ bf16 split
+def test_bf16_split_definition():
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(90)
+    x = (r.standard_normal(20000) * 10.0 ** r.uniform(-5, 5, 20000)).astype(np.float32)
+    hi, lo = oracle.split_bf16(x)
+    hi_t = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(hi, hi_t)  # round-to-nearest-even, as torch's cast
+    assert np.array_equal(lo, torch.from_numpy(x - hi).to(torch.bfloat16).float().numpy())
+    assert np.all(hi.view(np.uint32) & 0xFFFF == 0)
+    rel = np.abs((hi.astype(np.float64) + lo) - x) / np.abs(x)
+    assert rel.max() <= 2.0 ** -16
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], np.float32)
+    h, _ = oracle.split_bf16(ties)
+    assert h[0] == 1.0 and h[1] == np.float32(1 + 2 ** -6)
