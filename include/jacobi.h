@@ -1,0 +1,213 @@
+/*
+ * jacobi.h -- C ABI of the GB300 (sm_103a) blocked Jacobi library.
+ *
+ * The method is the blocked Jacobi algorithm for the symmetric eigenvalue
+ * problem A = Q D Q^T and the one-sided Jacobi SVD G = U Sigma V^T analysed in
+ * Demmel, Luo, Schneider & Wang, "Minimizing the Arithmetic and Communication
+ * Complexity of Jacobi's Method for Eigenvalues and Singular Values: Part Two
+ * -- Parallel Algorithms".  Each step of a sweep pairs the N = n/b blocks into
+ * N/2 disjoint pairs (Sec. 3, item 1), solves every 2b x 2b pivot subproblem,
+ * and applies the orthogonal transforms to A and Q (Algorithms 1 and 2) or to
+ * the column pairs of G and V (Algorithm 6).
+ *
+ * Conventions (all entry points):
+ *   - matrices are column-major with a leading dimension (lda, ldq, ...);
+ *   - pointers are DEVICE pointers unless the entry point name ends in "_h"
+ *     (host pointers) or the argument is named h_*;
+ *   - the caller owns every buffer; the library allocates its workspace with
+ *     cudaMallocAsync on the given stream and frees it before returning;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); the calls return only after the work is complete;
+ *   - nothing is printed, nothing throws, nothing exits;
+ *   - return value: 0 converged, >0 the sweep count when max_sweeps ran out
+ *     (outputs then hold the current iterate), <0 an error (JACOBI_ERR_* or
+ *     -k for an invalid k-th argument).
+ */
+#ifndef JACOBI_GB300_H
+#define JACOBI_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ codes */
+#define JACOBI_OK 0
+#define JACOBI_ERR_NONFINITE (-100) /* NaN or Inf in the input                     */
+#define JACOBI_ERR_CUDA (-101)      /* a CUDA runtime call failed                  */
+#define JACOBI_ERR_ALLOC (-102)     /* workspace allocation failed                 */
+#define JACOBI_ERR_TIMEOUT (-103)   /* a bounded device wait ran out               */
+#define JACOBI_ERR_UNSUPPORTED (-104) /* valid but not supported (e.g. b > 128)    */
+
+/* Orderings of the pairs within a sweep (Sec. 3).
+ *  ROUND_ROBIN: tournament; block 0 fixed, positions 1..N-1 rotate by one per
+ *               step, step s pairs position j with position N-1-j (N even).
+ *  ANTI_DIAGONAL: Algorithm 3, group K = {(I,J): I<J, (I+J) mod N = K}
+ *               (1-based I,J), groups emitted for K = 0..N-1. */
+#define JACOBI_ORDER_ROUND_ROBIN 0
+#define JACOBI_ORDER_ANTI_DIAGONAL 1
+
+/* Arithmetic of the update GEMMs.  Pivot solves, the off-norm test and the
+ * closing sweeps are FP64 in every mode. */
+#define JACOBI_PREC_FP64 0
+#define JACOBI_PREC_FP32 1
+#define JACOBI_PREC_MIXED_BF16X3 2
+#define JACOBI_PREC_MIXED_FP16X3 3
+#define JACOBI_PREC_MIXED_TF32 4
+
+/* Stop criteria.
+ *  OFF_ABS: Xi(A) = sqrt(sum_{i!=j} a_ij^2) <= tol * ||A||_F (Sec. 2.1,
+ *           eq. (Omega_A)); ||A||_F is taken once from the input.
+ *  REL:     max_{i!=j} |a_ij| / sqrt(|a_ii| |a_jj|) <= tol. */
+#define JACOBI_CONV_OFF_ABS 0
+#define JACOBI_CONV_REL 1
+
+typedef struct {
+    int b;                /* block size, 1 <= b <= 128; n need not be a multiple
+                             (zero padding, exact: see the design notes)       */
+    int ordering;         /* JACOBI_ORDER_*                                     */
+    int max_sweeps;       /* outer sweep cap (default 30)                       */
+    int inner_max_sweeps; /* cap on the sweeps of one pivot solve (default 30);
+                             a small cap gives the approximate solve the paper
+                             allows (Sec. 3, after Algorithm 3)                 */
+    double tol;           /* outer tolerance (default 1e-14; SVD: see gesvd)    */
+    double inner_tol;     /* a scalar rotation inside a pivot solve is skipped
+                             when |a_pq| <= inner_tol sqrt|a_pp| sqrt|a_qq|
+                             (default 4 * 2^-53)                                */
+    int precision;        /* JACOBI_PREC_* (default FP64)                       */
+    int conv;             /* JACOBI_CONV_* (default OFF_ABS)                    */
+    int want_vectors;     /* 1: accumulate Q / V (default 1)                    */
+    int warm_start;       /* 1: Q (or V) holds an orthogonal start: resume
+                             from the caller's (A, Q); 0: start from Q = I      */
+    double switch_tol;    /* mixed forms: leave the low-precision sweeps when
+                             off(A_w) <= switch_tol ||A||_F (0 = default)        */
+    int refine_steps;     /* mixed forms: FP64 refinement steps (default 1)     */
+    int pivot_order;      /* permutation after each pivot solve, Qhat <- Qhat P
+                             (the slot of the pivoting step, Sec. 2.1):
+                             0 = eigenpairs as solved (the pseudocode of
+                             Algorithms 1, 2 and 6); 1 = sorted by descending
+                             eigenvalue over the pivot's non-padding rows
+                             (default; far fewer sweeps on graded spectra)    */
+} jacobi_params;
+
+typedef struct {
+    int status;              /* the return code                                */
+    int sweeps;              /* outer sweeps run (all precisions)              */
+    int sweeps_lowp;         /* of which in the low-precision phase (mixed)    */
+    int stalled;             /* stopped by the stall rule                      */
+    long long steps;         /* parallel steps run                             */
+    long long pair_solves;   /* 2b x 2b pivot solves                           */
+    long long rotations;     /* scalar rotations applied inside pivot solves   */
+    long long inner_sweeps;  /* sum over pivot solves of their sweeps          */
+    double norm_fro;         /* ||A||_F of the input (EVD)                      */
+    double off_initial;      /* Xi(A) of the input (EVD) / first sweep's max
+                                normalised Gram off-diagonal (SVD)              */
+    double off_final;        /* same measure at exit                           */
+    double off_hist[64];     /* per sweep                                      */
+    double ms_total;         /* device time of the call (CUDA events)          */
+    double ms_pivot;         /* device time in the pivot-solve kernels         */
+    double ms_update;        /* device time in the update kernels (A and Q /
+                                G and V; for the SVD including the Gram)        */
+    long long launches;      /* kernels this call launched                     */
+    long long pivot_launches;  /* of which pivot-solve kernels                 */
+    long long update_launches; /* of which update kernels                      */
+    double flops_fp64;       /* FP64 flops issued (updates + pivot solves)     */
+    double flops_fp32;       /* FP32 flops issued                              */
+    double flops_lowp;       /* bf16 / fp16 / tf32 tensor flops issued         */
+} jacobi_stats;
+
+/* Fill *p with the defaults above.  Returns 0. */
+int jacobi_params_default(jacobi_params* p);
+
+/* Static text for a return code. */
+const char* jacobi_status_string(int status);
+
+/*
+ * jacobi_syev -- eigen-decomposition of a real symmetric n x n matrix by
+ * blocked two-sided Jacobi (Algorithm 1, swept in the parallel order of
+ * Algorithm 2; ordering from Algorithm 3 or round-robin).
+ *
+ *   n        order of A (n >= 1)
+ *   A        device, n x n, leading dimension lda >= n.  Only the lower
+ *            triangle is read (it is mirrored).  On exit A holds the final,
+ *            nearly diagonal iterate D (Algorithm 1, Ensure).
+ *   w        device, n doubles: the eigenvalues, ascending (the diagonal of D)
+ *   Q        device, n x n, ldq >= n (may be NULL if p->want_vectors == 0):
+ *            on exit the orthonormal eigenvectors, column j belonging to w[j].
+ *            With p->warm_start, on entry an orthogonal start (resume): the
+ *            call then continues from the caller's A and Q.
+ *   p        parameters (NULL = defaults)
+ *   st       statistics out (may be NULL)
+ *   stream   cudaStream_t as void*
+ * FP64 throughout for precision == JACOBI_PREC_FP64; the MIXED_* values run
+ * the early sweeps' update GEMMs on the tensor cores from FP32 working copies
+ * and return to FP64 for the closing sweeps and the refinement.
+ */
+int jacobi_syev(int n, double* A, int lda, double* w, double* Q, int ldq,
+                const jacobi_params* p, jacobi_stats* st, void* stream);
+
+/* Same as jacobi_syev with HOST buffers: the library copies A (and Q for a
+ * warm start) to the device, runs, and copies A, w and Q back. */
+int jacobi_syev_h(int n, double* h_A, int lda, double* h_w, double* h_Q, int ldq,
+                  const jacobi_params* p, jacobi_stats* st, void* stream);
+
+/*
+ * jacobi_gesvd -- one-sided blocked Jacobi SVD of an m x n matrix, m >= n
+ * (Algorithm 6 in the parallel order): the pivot of block-column pair (I,J)
+ * is the Gram block G(:,[I,J])^T G(:,[I,J]) (Sec. 6, eq. (SVD_subproblem)),
+ * its eigenvectors rotate the column pair of G and of V; at exit
+ * sigma_i = ||G(:,i)||_2 and U = G Sigma^+ (Algorithm 6, last two lines),
+ * sorted descending.
+ *
+ *   G      device, m x n, ldg >= m; in: G, out: U (zero column for sigma = 0)
+ *   sigma  device, n doubles, descending
+ *   V      device, n x n, ldv >= n (NULL if p->want_vectors == 0)
+ * The stop test and the inner rotation threshold both use
+ * tol_eff = max(p->tol, sqrt(m) * 2^-53): a sweep whose largest normalised
+ * Gram off-diagonal |a_ij| / sqrt(a_ii a_jj) is <= tol_eff ends the
+ * iteration.  p->conv is ignored.
+ */
+int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, double* V, int ldv,
+                 const jacobi_params* p, jacobi_stats* st, void* stream);
+
+/* Same as jacobi_gesvd with HOST buffers. */
+int jacobi_gesvd_h(int m, int n, double* h_G, int ldg, double* h_sigma, double* h_V, int ldv,
+                   const jacobi_params* p, jacobi_stats* st, void* stream);
+
+/*
+ * jacobi_syev_step -- exactly one parallel step of Algorithm 2: the pivot
+ * solves of step `step` (0-based) of the sweep schedule, then the block-row
+ * and block-column updates of A and the column updates of Q, then the pivot
+ * blocks overwritten by D.  Operates in place on a full symmetric np x np
+ * matrix (both triangles read; it must be exactly symmetric) with np = N * p->b
+ * and N the block count (even for round-robin).  No sorting, no stop test.
+ *   A  device, np x np, lda >= np;   Q  device, np x np, ldq >= np, or NULL.
+ * Returns 0, or <0 on an invalid argument / CUDA error.
+ */
+int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq, const jacobi_params* p,
+                     int step, void* stream);
+
+/*
+ * jacobi_gesvd_step -- exactly one step of the one-sided method (Algorithm
+ * 6): for every column-block pair of step `step`, the Gram block (Sec. 6,
+ * eq. (SVD_subproblem)), its FP64 Jacobi solve with the relative threshold
+ * tol_eff (as in jacobi_gesvd), and G(:,[I,J]) <- G(:,[I,J]) Vhat,
+ * V(:,[I,J]) <- V(:,[I,J]) Vhat.  G is m x np (np = N * p->b), V np x np or
+ * NULL.  *relmax_out (host, may be NULL) receives the step's largest
+ * normalised Gram off-diagonal before rotation.
+ */
+int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, int ldv,
+                      const jacobi_params* p, int step, double* relmax_out, void* stream);
+
+/*
+ * jacobi_ordering_table -- the library's pair schedule for N blocks
+ * (host-side logic, no GPU needed): kind is JACOBI_ORDER_*; pairs receives
+ * 2 ints (I < J, 0-based) per pair, step after step (room for N*(N-1) ints);
+ * step_ptr (N+1 ints) the offset of each step in pairs.  Returns the number of
+ * steps, or -1 for an invalid (kind, N) (N < 2, or odd N for round-robin).
+ */
+int jacobi_ordering_table(int kind, int N, int* pairs, int* step_ptr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JACOBI_GB300_H */

@@ -33,7 +33,8 @@ U64 = 2.0 ** -53
 class _Params(C.Structure):
     _fields_ = [("b", C.c_int), ("ordering", C.c_int), ("max_sweeps", C.c_int),
                 ("inner_max_sweeps", C.c_int), ("conv", C.c_int), ("tol", C.c_double),
-                ("inner_tol", C.c_double), ("want_vectors", C.c_int), ("threads", C.c_int)]
+                ("inner_tol", C.c_double), ("want_vectors", C.c_int), ("threads", C.c_int),
+                ("pivot_order", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -90,7 +91,7 @@ def lib():
         L.oracle_padded_blocks.argtypes = [C.c_int, C.c_int, C.c_int]
         L.oracle_padded_blocks.restype = C.c_int
         L.oracle_syev_step.argtypes = [C.c_int, C.c_int, _DP, _DP, C.c_int, _IP, C.c_double,
-                                       C.c_int]
+                                       C.c_int, C.c_int]
         L.oracle_syev_step.restype = C.c_longlong
         for name in ("oracle_syev_blocked", "oracle_syev_scalar"):
             f = getattr(L, name)
@@ -105,7 +106,7 @@ def lib():
         L.oracle_gram_pair.argtypes = [C.c_int, C.c_int, _DP, C.c_int, C.c_int, C.c_int, _DP]
         L.oracle_gram_pair.restype = None
         L.oracle_gesvd_step.argtypes = [C.c_int, C.c_int, C.c_int, _DP, C.c_int, _DP, C.c_int,
-                                        _IP, C.c_double, C.c_int]
+                                        _IP, C.c_double, C.c_int, C.c_int]
         L.oracle_gesvd_step.restype = C.c_double
         L.oracle_split_bf16.argtypes = [C.c_int, _FP, _FP, _FP]
         L.oracle_split_bf16.restype = None
@@ -180,14 +181,15 @@ def pivot_solve(Ahat: np.ndarray, tol_rel: float = 4 * U64, max_sweeps: int = 30
 
 # ---------------------------------------------------------------- EVD
 def _params(b, ordering, max_sweeps, inner_max_sweeps, conv, tol, inner_tol, want_vectors,
-            threads):
+            threads, pivot_order=1):
     return _Params(b, ordering, max_sweeps, inner_max_sweeps, conv, tol, inner_tol,
-                   int(want_vectors), threads)
+                   int(want_vectors), threads, pivot_order)
 
 
 def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U64,
-              inner_max=30):
-    """One parallel step (Algorithm 2 structure) on a full np x np matrix.
+              inner_max=30, pivot_order=1):
+    """One parallel step (Algorithm 2 structure) on a full np x np matrix;
+    pivot_order 1 sorts each pivot's eigenpairs descending (Qhat <- Qhat P).
 
     Returns (A', Q', rotations)."""
     A = _f64F(A)
@@ -195,14 +197,15 @@ def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U6
     Qc = _f64F(Q) if Q is not None else None
     pr = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
     rot = lib().oracle_syev_step(npd, b, _dp(A), _dp(Qc) if Qc is not None else None,
-                                 len(pairs), pr.ctypes.data_as(_IP), tol_rel, inner_max)
+                                 len(pairs), pr.ctypes.data_as(_IP), tol_rel, inner_max,
+                                 pivot_order)
     return A, Qc, int(rot)
 
 
 def syev(A: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float = 1e-14,
          ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 30,
          conv: int = CONV_OFF_ABS, inner_tol: float = 4 * U64, want_vectors: bool = True,
-         threads: int = 0):
+         threads: int = 0, pivot_order: int = 1):
     """Blocked (Algorithm 1 in the parallel order of Algorithm 2) or scalar
     cyclic Jacobi EVD of the symmetric A (lower triangle read).
 
@@ -212,7 +215,7 @@ def syev(A: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float = 1e-14
     w = np.zeros(n)
     Q = np.zeros((n, n), order="F") if want_vectors else None
     p = _params(b, ordering, max_sweeps, inner_max_sweeps, conv, tol, inner_tol, want_vectors,
-                threads)
+                threads, pivot_order)
     st = _Stats()
     f = lib().oracle_syev_scalar if scalar else lib().oracle_syev_blocked
     status = f(n, _dp(A), n, _dp(w), _dp(Q) if Q is not None else None, n, C.byref(p),
@@ -238,20 +241,21 @@ def gram_pair(G: np.ndarray, b: int, I: int, J: int) -> np.ndarray:
 
 
 def gesvd_step(G: np.ndarray, V: np.ndarray | None, b: int, pairs, tol_rel: float,
-               inner_max: int = 30):
+               inner_max: int = 30, pivot_order: int = 1):
     """One one-sided step over disjoint column pairs.  Returns (G', V', max_rel_off)."""
     G = _f64F(G)
     m, npd = G.shape
     Vc = _f64F(V) if V is not None else None
     pr = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
     r = lib().oracle_gesvd_step(m, npd, b, _dp(G), m, _dp(Vc) if Vc is not None else None,
-                                len(pairs), pr.ctypes.data_as(_IP), tol_rel, inner_max)
+                                len(pairs), pr.ctypes.data_as(_IP), tol_rel, inner_max,
+                                pivot_order)
     return G, Vc, r
 
 
 def gesvd(G: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float | None = None,
           ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 30,
-          want_vectors: bool = True, threads: int = 0):
+          want_vectors: bool = True, threads: int = 0, pivot_order: int = 1):
     """Blocked one-sided Jacobi SVD (Algorithm 6 in the parallel order) or the
     scalar Hestenes form.  Returns (U, sigma descending, V or None, Stats, status)."""
     G = _f64F(G)
@@ -261,7 +265,7 @@ def gesvd(G: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float | None
     s = np.zeros(n)
     V = np.zeros((n, n), order="F") if want_vectors else None
     p = _params(b, ordering, max_sweeps, inner_max_sweeps, CONV_REL, tol, tol, want_vectors,
-                threads)
+                threads, pivot_order)
     st = _Stats()
     f = lib().oracle_gesvd_scalar if scalar else lib().oracle_gesvd_blocked
     status = f(m, n, _dp(G), m, _dp(s), _dp(V) if V is not None else None, n, C.byref(p),

@@ -13,7 +13,7 @@ SRC = os.path.join(HERE, "jacobi_oracle.c")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-          "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas"]
+          "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas", "-Wno-maybe-uninitialized"]
 
 
 def build(force: bool = False) -> str:

@@ -39,10 +39,15 @@
  *     step s pairs position k with position N-1-k;
  *   - anti-diagonal groups are emitted in the order K = 0..N-1;
  *   - b that does not divide n: pad with zero rows/columns; N is raised to
- *     at least 2 and, for round-robin, to an even number;
+ *     at least 2 and to an even number (for both orderings);
  *   - a scalar rotation is skipped when |a_pq| <= tol_rel*sqrt|a_pp|*sqrt|a_qq|;
  *   - the inner solve stops after a sweep with no rotation, or after
  *     inner_max_sweeps sweeps;
+ *   - after a pivot solve its eigenpairs may be permuted, Qhat <- Qhat P (the
+ *     slot of the pivoting step of Sec. 2.1, items 1-2 after Algorithm 1); the
+ *     permutation used here sorts the pivot's eigenvalues in descending order
+ *     (ties keep their index order) over the pivot's real rows, leaving the
+ *     zero padding rows where they are; the GPU path applies the same rule;
  *   - the outer loop stops when off(A) <= tol*||A||_F (or, for the relative
  *     criterion, max |a_ij|/sqrt|a_ii a_jj| <= tol), or when the measure is
  *     already <= 100*tol and did not halve over the last sweep (stall).
@@ -74,6 +79,7 @@ typedef struct {
     double inner_tol;     /* relative threshold of one scalar rotation            */
     int want_vectors;     /* accumulate Q (EVD) / V (SVD)                         */
     int threads;          /* OpenMP threads (0 = runtime default)                 */
+    int pivot_order;      /* 0: eigenpairs as solved; 1: sorted descending        */
 } orc_params;
 
 typedef struct {
@@ -382,6 +388,36 @@ int oracle_pivot_solve(int k, double *Ah, double *V, double tol_rel, int max_swe
     return total;
 }
 
+/* Permutation step after a pivot solve: reorder the eigenpairs (Dhat's
+ * rows/columns and Vhat's columns) so that diag(Dhat) is descending over the
+ * pivot's real positions (global index < n_real); padding positions stay put;
+ * ties keep their index order.  Dhat <- P^T Dhat P, Vhat <- Vhat P. */
+static void sort_pivot_desc(int k, double *Ah, double *V, double *tmp, int *idx, int I, int J,
+                            int b, int n_real)
+{
+    double *d = tmp;
+    int *pos = (int *)malloc(sizeof(int) * (size_t)k);
+    int *ord = (int *)malloc(sizeof(int) * (size_t)k);
+    int nr = 0;
+    for (int x = 0; x < k; x++) {
+        int g = x < b ? I * b + x : J * b + (x - b);
+        idx[x] = x;
+        if (g < n_real) pos[nr++] = x;
+    }
+    for (int t = 0; t < nr; t++) d[t] = AT(Ah, k, pos[t], pos[t]);
+    stable_argsort(nr, d, ord, 0);
+    for (int t = 0; t < nr; t++) idx[pos[t]] = pos[ord[t]];
+    free(pos);
+    free(ord);
+    double *B = tmp + k;
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) AT(B, k, i, j) = AT(Ah, k, idx[i], idx[j]);
+    memcpy(Ah, B, sizeof(double) * (size_t)k * k);
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) AT(B, k, i, j) = AT(V, k, i, idx[j]);
+    memcpy(V, B, sizeof(double) * (size_t)k * k);
+}
+
 /* ------------------------------------------------------------------ */
 /* Blocked two-sided step (Algorithm 2 structure, one group of pairs)      */
 /* ------------------------------------------------------------------ */
@@ -394,9 +430,9 @@ typedef struct {
 /* One parallel step on the np x np working matrix (ld np) with np = N*b.
  * pairs[2*e], pairs[2*e+1] (0-based I<J), npairs of them.  Q may be NULL.
  * Rows, then columns, then the pivot blocks <- Dhat. */
-static void evd_step(int np, int b, double *A, double *Q, int npairs, const int *pairs,
-                     double tol_rel, int inner_max, pair_ws *ws, double *tmp_all,
-                     long long *rot_acc, long long *isw_acc)
+static void evd_step(int np, int n_real, int b, double *A, double *Q, int npairs,
+                     const int *pairs, double tol_rel, int inner_max, int order, pair_ws *ws,
+                     double *tmp_all, long long *rot_acc, long long *isw_acc)
 {
     int k = 2 * b;
     long long rot = 0, isw = 0;
@@ -414,6 +450,13 @@ static void evd_step(int np, int b, double *A, double *Q, int npairs, const int 
         int sw = 0;
         ws[e].rot = oracle_pivot_solve(k, Ah, ws[e].V, tol_rel, inner_max, &sw);
         ws[e].sw = sw;
+        if (order == 1 && ws[e].rot > 0) {
+            double *t = (double *)malloc(sizeof(double) * (size_t)(k + k * k));
+            int *ix = (int *)malloc(sizeof(int) * (size_t)k);
+            sort_pivot_desc(k, Ah, ws[e].V, t, ix, I, J, b, n_real);
+            free(t);
+            free(ix);
+        }
         rot += ws[e].rot;
         isw += sw;
     }
@@ -489,7 +532,8 @@ int oracle_padded_blocks(int n, int b, int ordering)
 {
     int N = (n + b - 1) / b;
     if (N < 2) N = 2;
-    if (ordering == ORC_ORDER_ROUND_ROBIN && (N % 2)) N++;
+    if (N % 2) N++;
+    (void)ordering;
     return N;
 }
 
@@ -505,7 +549,7 @@ static void set_threads(const orc_params *p)
 /* Public: one parallel step on an np x np matrix (np = N*b, ld np) with the
  * given pairs; Q may be NULL.  Returns the rotations applied. */
 long long oracle_syev_step(int np, int b, double *A, double *Q, int npairs, const int *pairs,
-                           double tol_rel, int inner_max)
+                           double tol_rel, int inner_max, int order)
 {
     int k = 2 * b;
     pair_ws *ws = (pair_ws *)calloc((size_t)npairs, sizeof(pair_ws));
@@ -516,7 +560,7 @@ long long oracle_syev_step(int np, int b, double *A, double *Q, int npairs, cons
     }
     double *tmp = buf + (size_t)npairs * 2 * k * k;
     long long rot = 0, isw = 0;
-    evd_step(np, b, A, Q, npairs, pairs, tol_rel, inner_max, ws, tmp, &rot, &isw);
+    evd_step(np, np, b, A, Q, npairs, pairs, tol_rel, inner_max, order, ws, tmp, &rot, &isw);
     free(ws);
     free(buf);
     return rot;
@@ -570,8 +614,9 @@ int oracle_syev_blocked(int n, double *A, int lda, double *w, double *Q, int ldq
         for (sw = 0; sw < p->max_sweeps; sw++) {
             for (int st_i = 0; st_i < S; st_i++) {
                 int np_st = sptr[st_i + 1] - sptr[st_i];
-                evd_step(np, b, Aw, Qw, np_st, pairs + 2 * sptr[st_i], p->inner_tol,
-                         p->inner_max_sweeps, ws, tmp, &s.rotations, &s.inner_sweeps);
+                evd_step(np, n, b, Aw, Qw, np_st, pairs + 2 * sptr[st_i], p->inner_tol,
+                         p->inner_max_sweeps, p->pivot_order, ws, tmp, &s.rotations,
+                         &s.inner_sweeps);
                 s.steps++;
                 s.pair_solves += np_st;
             }
@@ -693,9 +738,9 @@ void oracle_gram_pair(int m, int b, const double *G, int ldg, int I, int J, doub
 
 /* One step of the one-sided method over disjoint column pairs.  Returns the
  * step's maximum normalised Gram off-diagonal (before rotation). */
-static double svd_step(int m, int np, int b, double *G, int ldg, double *V, int npairs,
-                       const int *pairs, double tol_rel, int inner_max, pair_ws *ws,
-                       double *tmp_all, long long *rot_acc, long long *isw_acc)
+static double svd_step(int m, int np, int n_real, int b, double *G, int ldg, double *V,
+                       int npairs, const int *pairs, double tol_rel, int inner_max, int order,
+                       pair_ws *ws, double *tmp_all, long long *rot_acc, long long *isw_acc)
 {
     int k = 2 * b;
     long long rot = 0, isw = 0;
@@ -709,6 +754,13 @@ static double svd_step(int m, int np, int b, double *G, int ldg, double *V, int 
         int sw = 0;
         ws[e].rot = oracle_pivot_solve(k, ws[e].Ah, ws[e].V, tol_rel, inner_max, &sw);
         ws[e].sw = sw;
+        if (order == 1 && ws[e].rot > 0) {
+            double *t = (double *)malloc(sizeof(double) * (size_t)(k + k * k));
+            int *ix = (int *)malloc(sizeof(int) * (size_t)k);
+            sort_pivot_desc(k, ws[e].Ah, ws[e].V, t, ix, I, J, b, n_real);
+            free(t);
+            free(ix);
+        }
         rot += ws[e].rot;
         isw += sw;
     }
@@ -772,7 +824,7 @@ static void finalize_svd(int m, int n, double *Gw, int ldgw, double *G, int ldg,
 /* Public: one step of the one-sided method on G (m x np, ld ldg) and V
  * (np x np, ld np, may be NULL).  Returns the max normalised Gram off-diagonal. */
 double oracle_gesvd_step(int m, int np, int b, double *G, int ldg, double *V, int npairs,
-                         const int *pairs, double tol_rel, int inner_max)
+                         const int *pairs, double tol_rel, int inner_max, int order)
 {
     int k = 2 * b;
     pair_ws *ws = (pair_ws *)calloc((size_t)npairs, sizeof(pair_ws));
@@ -782,7 +834,7 @@ double oracle_gesvd_step(int m, int np, int b, double *G, int ldg, double *V, in
         ws[e].V = ws[e].Ah + (size_t)k * k;
     }
     long long rot = 0, isw = 0;
-    double mx = svd_step(m, np, b, G, ldg, V, npairs, pairs, tol_rel, inner_max, ws,
+    double mx = svd_step(m, np, np, b, G, ldg, V, npairs, pairs, tol_rel, inner_max, order, ws,
                          buf + (size_t)npairs * 2 * k * k, &rot, &isw);
     free(ws);
     free(buf);
@@ -827,8 +879,9 @@ int oracle_gesvd_blocked(int m, int n, double *G, int ldg, double *sigma, double
         long long rot_before = s.rotations;
         for (int st_i = 0; st_i < S; st_i++) {
             int np_st = sptr[st_i + 1] - sptr[st_i];
-            double r = svd_step(m, np, b, Gw, m, Vw, np_st, pairs + 2 * sptr[st_i], p->tol,
-                                p->inner_max_sweeps, ws, tmp, &s.rotations, &s.inner_sweeps);
+            double r = svd_step(m, np, n, b, Gw, m, Vw, np_st, pairs + 2 * sptr[st_i], p->tol,
+                                p->inner_max_sweeps, p->pivot_order, ws, tmp, &s.rotations,
+                                &s.inner_sweeps);
             if (r > mx) mx = r;
             s.steps++;
             s.pair_solves += np_st;

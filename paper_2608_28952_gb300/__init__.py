@@ -1,0 +1,288 @@
+"""GB300 (sm_103a) blocked Jacobi: symmetric EVD and one-sided SVD.
+
+Thin ctypes binding over the C ABI in ``include/jacobi.h`` (library
+``_build/libjacobi_gb300.so``, built by ``build.py``).  Every step of the
+computation runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch provides device memory and streams.
+
+The same names as the C ABI are exported (``jacobi_syev``, ``jacobi_gesvd``,
+...), each taking column-major tensors; ``syev`` / ``gesvd`` are convenience
+wrappers that allocate the outputs.  If the library is missing the import of
+any entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libjacobi_gb300.so")
+
+ORDER_ROUND_ROBIN = 0
+ORDER_ANTI_DIAGONAL = 1
+PREC_FP64 = 0
+PREC_FP32 = 1
+PREC_MIXED_BF16X3 = 2
+PREC_MIXED_FP16X3 = 3
+PREC_MIXED_TF32 = 4
+CONV_OFF_ABS = 0
+CONV_REL = 1
+ERR_NONFINITE = -100
+ERR_CUDA = -101
+ERR_ALLOC = -102
+ERR_TIMEOUT = -103
+ERR_UNSUPPORTED = -104
+
+
+class jacobi_params(C.Structure):
+    _fields_ = [("b", C.c_int), ("ordering", C.c_int), ("max_sweeps", C.c_int),
+                ("inner_max_sweeps", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("precision", C.c_int), ("conv", C.c_int), ("want_vectors", C.c_int),
+                ("warm_start", C.c_int), ("switch_tol", C.c_double), ("refine_steps", C.c_int),
+                ("pivot_order", C.c_int)]
+
+
+class jacobi_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("sweeps", C.c_int), ("sweeps_lowp", C.c_int),
+                ("stalled", C.c_int), ("steps", C.c_longlong), ("pair_solves", C.c_longlong),
+                ("rotations", C.c_longlong), ("inner_sweeps", C.c_longlong),
+                ("norm_fro", C.c_double), ("off_initial", C.c_double), ("off_final", C.c_double),
+                ("off_hist", C.c_double * 64), ("ms_total", C.c_double),
+                ("ms_pivot", C.c_double), ("ms_update", C.c_double),
+                ("launches", C.c_longlong), ("pivot_launches", C.c_longlong),
+                ("update_launches", C.c_longlong),
+                ("flops_fp64", C.c_double), ("flops_fp32", C.c_double),
+                ("flops_lowp", C.c_double)]
+
+
+@dataclass
+class Stats:
+    status: int
+    sweeps: int
+    sweeps_lowp: int
+    stalled: int
+    steps: int
+    pair_solves: int
+    rotations: int
+    inner_sweeps: int
+    norm_fro: float
+    off_initial: float
+    off_final: float
+    ms_total: float
+    ms_pivot: float
+    ms_update: float
+    launches: int
+    pivot_launches: int
+    update_launches: int
+    flops_fp64: float
+    flops_fp32: float
+    flops_lowp: float
+    off_hist: list = field(default_factory=list)
+
+
+def _stats(s: jacobi_stats) -> Stats:
+    return Stats(s.status, s.sweeps, s.sweeps_lowp, s.stalled, s.steps, s.pair_solves,
+                 s.rotations, s.inner_sweeps, s.norm_fro, s.off_initial, s.off_final,
+                 s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
+                 s.update_launches, s.flops_fp64, s.flops_fp32, s.flops_lowp,
+                 list(s.off_hist)[: max(0, min(64, s.sweeps))])
+
+
+# Every symbol include/jacobi.h declares, with its ctypes signature.
+_I, _D, _P = C.c_int, C.c_double, C.c_void_p
+_PP = C.POINTER(jacobi_params)
+_SP = C.POINTER(jacobi_stats)
+SIGNATURES = {
+    "jacobi_params_default": (_I, [_PP]),
+    "jacobi_status_string": (C.c_char_p, [_I]),
+    "jacobi_syev": (_I, [_I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
+    "jacobi_syev_h": (_I, [_I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
+    "jacobi_gesvd": (_I, [_I, _I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
+    "jacobi_gesvd_h": (_I, [_I, _I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
+    "jacobi_ordering_table": (_I, [_I, _I, _P, _P]),
+    "jacobi_syev_step": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
+    "jacobi_gesvd_step": (_I, [_I, _I, _P, _I, _P, _I, _PP, _I, C.POINTER(C.c_double), _P]),
+}
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA extension {LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def params(**kw) -> jacobi_params:
+    """Default parameters with keyword overrides (names as in jacobi_params)."""
+    p = jacobi_params()
+    lib().jacobi_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def status_string(code: int) -> str:
+    return lib().jacobi_status_string(code).decode()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _colmajor_ld(t) -> int:
+    """Leading dimension of a column-major 2-D tensor (stride(0) == 1)."""
+    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[0] > 1):
+        raise ValueError("expected a column-major 2-D tensor (stride(0) == 1)")
+    return max(t.stride(1), t.shape[0], 1)
+
+
+def colmajor(x, device=None, dtype=None):
+    """Column-major copy of a 2-D tensor or array (as a torch tensor)."""
+    import torch
+    t = torch.as_tensor(x)
+    if dtype is not None:
+        t = t.to(dtype)
+    if device is not None:
+        t = t.to(device)
+    return t.t().contiguous().t()
+
+
+def colmajor_empty(rows, cols, dtype, device):
+    import torch
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+# ------------------------------------------------------------------ C-ABI names
+def jacobi_syev(A, w, Q, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev`` on CUDA tensors: A (n x n, column-major, float64,
+    overwritten by D), w (n), Q (n x n column-major or None).
+    Returns (status, Stats)."""
+    n = A.shape[0]
+    st = jacobi_stats()
+    rc = lib().jacobi_syev(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
+                           _colmajor_ld(Q) if Q is not None else n,
+                           C.byref(p) if p is not None else None, C.byref(st), _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_syev_h(A, w, Q, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev_h`` on HOST buffers (torch CPU tensors, ideally
+    pinned): same layout as jacobi_syev."""
+    n = A.shape[0]
+    st = jacobi_stats()
+    rc = lib().jacobi_syev_h(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
+                             _colmajor_ld(Q) if Q is not None else n,
+                             C.byref(p) if p is not None else None, C.byref(st),
+                             _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_gesvd(G, sigma, V, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_gesvd`` on CUDA tensors: G (m x n column-major float64, out:
+    U), sigma (n), V (n x n or None).  Returns (status, Stats)."""
+    m, n = G.shape
+    st = jacobi_stats()
+    rc = lib().jacobi_gesvd(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
+                            _colmajor_ld(V) if V is not None else n,
+                            C.byref(p) if p is not None else None, C.byref(st), _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_gesvd_h(G, sigma, V, p: jacobi_params | None = None, stream=None):
+    m, n = G.shape
+    st = jacobi_stats()
+    rc = lib().jacobi_gesvd_h(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
+                              _colmajor_ld(V) if V is not None else n,
+                              C.byref(p) if p is not None else None, C.byref(st),
+                              _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_syev_step(A, Q, step: int, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev_step``: one parallel step in place on the full
+    symmetric np x np column-major CUDA tensor A (and Q or None)."""
+    np_ = A.shape[0]
+    return lib().jacobi_syev_step(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
+                                  _colmajor_ld(Q) if Q is not None else np_,
+                                  C.byref(p) if p is not None else None, step,
+                                  _stream_ptr(stream))
+
+
+def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_gesvd_step``: one one-sided step in place on G (m x np) and
+    V (np x np or None).  Returns (status, relmax)."""
+    m, np_ = G.shape
+    r = C.c_double(0.0)
+    rc = lib().jacobi_gesvd_step(m, np_, _ptr(G), _colmajor_ld(G), _ptr(V),
+                                 _colmajor_ld(V) if V is not None else np_,
+                                 C.byref(p) if p is not None else None, step, C.byref(r),
+                                 _stream_ptr(stream))
+    return rc, r.value
+
+
+def jacobi_ordering_table(kind: int, N: int):
+    """The library's pair schedule: list of steps, each a list of (I, J)."""
+    import numpy as np
+    pairs = np.zeros(max(1, N * (N - 1)), dtype=np.int32)
+    ptr = np.zeros(N + 1, dtype=np.int32)
+    S = lib().jacobi_ordering_table(kind, N, pairs.ctypes.data, ptr.ctypes.data)
+    if S < 0:
+        raise ValueError("bad ordering arguments")
+    return [[(int(pairs[2 * e]), int(pairs[2 * e + 1])) for e in range(ptr[s], ptr[s + 1])]
+            for s in range(S)]
+
+
+# ------------------------------------------------------------------ convenience
+def syev(A, b: int = 32, *, want_vectors: bool = True, stream=None, **kw):
+    """Eigen-decomposition of the symmetric A (any 2-D tensor/array; only its
+    lower triangle is read).  Returns (w, Q, D, Stats) as CUDA tensors
+    (Q column-major, None without vectors); raises on an error status."""
+    import torch
+    dev = torch.device("cuda")
+    Ad = colmajor(A, device=dev, dtype=torch.float64)
+    n = Ad.shape[0]
+    w = torch.empty(n, dtype=torch.float64, device=dev)
+    Q = colmajor_empty(n, n, torch.float64, dev) if want_vectors else None
+    p = params(b=b, want_vectors=int(want_vectors), **kw)
+    rc, st = jacobi_syev(Ad, w, Q, p, stream)
+    if rc < 0:
+        raise RuntimeError(f"jacobi_syev: {rc} ({status_string(rc)})")
+    return w, Q, Ad, st
+
+
+def gesvd(G, b: int = 32, *, want_vectors: bool = True, stream=None, **kw):
+    """One-sided Jacobi SVD of G (m x n, m >= n).  Returns (U, sigma, V, Stats)."""
+    import torch
+    dev = torch.device("cuda")
+    Gd = colmajor(G, device=dev, dtype=torch.float64)
+    m, n = Gd.shape
+    s = torch.empty(n, dtype=torch.float64, device=dev)
+    V = colmajor_empty(n, n, torch.float64, dev) if want_vectors else None
+    p = params(b=b, want_vectors=int(want_vectors), **kw)
+    rc, st = jacobi_gesvd(Gd, s, V, p, stream)
+    if rc < 0:
+        raise RuntimeError(f"jacobi_gesvd: {rc} ({status_string(rc)})")
+    return Gd, s, V, st

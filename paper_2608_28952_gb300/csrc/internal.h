@@ -1,0 +1,133 @@
+// internal.h -- declarations shared by the translation units of the GB300
+// Jacobi library (kernels, host driver, C ABI).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/jacobi.h"
+
+namespace jac {
+
+// ----------------------------------------------------------------- ordering
+// A sweep's ordering: steps[s] is a list of disjoint 0-based block pairs
+// (I < J).  Round-robin is the default; anti-diagonal is Algorithm 3.
+struct Ordering {
+    int N = 0;                    // blocks (after padding)
+    int S = 0;                    // steps per sweep
+    std::vector<int> step_ptr;    // S + 1 offsets into pairs (in pairs)
+    std::vector<int> pairs;       // 2 ints per pair
+    int max_pairs = 0;            // largest step
+    // Device schedule: exactly N/2 entries per step.  Steps of Algorithm 3
+    // that leave two blocks out get an extra "frozen" entry holding them
+    // (stored as {-1-I, -1-J}); its transform is the identity.
+    std::vector<int> dev_pairs;
+    int dev_per_step = 0;
+};
+int padded_blocks(int n, int b, int ordering);
+bool make_ordering(int kind, int N, Ordering* out);
+
+// ----------------------------------------------------------------- device data
+// Counters accumulated on the device (integers only: deterministic).
+struct DevCounters {
+    unsigned long long rotations;
+    unsigned long long inner_sweeps;
+    unsigned long long pair_solves;
+    unsigned long long flops_fp64;   // issued update + pivot flops
+    unsigned long long flops_fp32;
+    unsigned long long flops_lowp;
+    int nonfinite;                   // input scan flag
+    int pad_;
+};
+
+// ----------------------------------------------------------------- launchers (FP64 path)
+// Each returns the cudaError_t of its launch.
+
+// A_w <- mirrored lower triangle of A (n x n, lda), zero padded to np; Q_w <- I
+// (or the caller's Q with identity on the pads when warm).  Flags non-finite
+// input in cnt->nonfinite.
+cudaError_t launch_load_sym(int n, int np, const double* A, int lda, double* Aw,
+                            const double* Qin, int ldq, double* Qw, int warm,
+                            DevCounters* cnt, cudaStream_t s);
+
+// Sum of squares of the off-diagonal (and, separately, all) entries of the
+// np x np matrix Aw, and max_{i!=j}|a_ij|/sqrt(|a_ii a_jj|).  Deterministic
+// two-level reduction; result[0] = off^2, result[1] = ||A||_F^2,
+// result[2] = relative measure.  partial must hold 3 * reduce_blocks doubles.
+int reduce_blocks_for(int np);
+cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned int* ticket,
+                           double* result, bool want_rel, cudaStream_t s);
+
+// Pivot solves of one step (one CTA per pair): reads Ain's pivot blocks
+// (EVD) or sums the Gram partials (SVD), runs the FP64 inner Jacobi, writes
+// V (and V^T) per pair, D into Aout's pivot blocks (EVD), the rotation count
+// per pair and, for the SVD, the pre-rotation max normalised off-diagonal.
+struct PivotArgs {
+    const double* Ain;         // EVD: working A (np x np, ld np); SVD: null
+    double* Aout;              // EVD: next working A (pivot blocks written)
+    int ld;                    // np
+    const double* gram;        // SVD: Gram partials [pair][panel][k*k] or null
+    int npanels;
+    const int2* pairs;         // this step's pairs
+    int npairs;
+    int b, k;
+    double* V;                 // [pair][2][k*k]: V then V^T, column-major
+    int* rot;                  // [pair] rotations applied (0 => V == I)
+    double* relmax;            // [pair] (SVD) pre-rotation max normalised off-diag
+    double tol_rel;
+    int max_sweeps;
+    int order;                 // 1: sort eigenpairs descending over real rows
+    int n_real;                // rows/columns >= n_real are zero padding
+    double* gscratch;          // k > 128: per-pair global scratch (packed A + V)
+    DevCounters* cnt;
+};
+cudaError_t launch_pivot(const PivotArgs& a, cudaStream_t s);
+size_t pivot_gscratch_doubles(int k);   // per pair, 0 when shared memory suffices
+
+// Update of one step (EVD): sandwich items A'_{P1P2} = V1^T A_{P1P2} V2 for
+// P1 < P2 (written with their mirror), Q column items Q'(:,P) = Q(:,P) V_P.
+struct UpdateArgs {
+    const double* Ain; double* Aout; int lda;   // np x np, double-buffered
+    const double* Qin; double* Qout; int ldq;   // rows x np, double-buffered (may be null)
+    int qrows;                                  // rows of Q (np)
+    const int2* pairs; int npairs;
+    int b, k;
+    const double* V; const int* rot;
+    DevCounters* cnt;
+};
+cudaError_t launch_update_evd(const UpdateArgs& a, cudaStream_t s);
+
+// One-sided update: G'(:,P) = G(:,P) V_P (m rows) and V'(:,P) = V(:,P) V_P.
+struct ColUpdateArgs {
+    const double* Gin; double* Gout; int ldg; int m;
+    const double* Vin; double* Vout; int ldv; int vrows;
+    const int2* pairs; int npairs;
+    int b, k;
+    const double* Vh; const int* rot;
+    DevCounters* cnt;
+};
+cudaError_t launch_update_cols(const ColUpdateArgs& a, cudaStream_t s);
+
+// Gram partials of one step: for each pair P and row panel r,
+// part[P][r] = G(rows_r, P)^T G(rows_r, P) (k x k).
+int gram_panels_for(int m);
+int gram_panel_rows();
+cudaError_t launch_gram(const double* G, int ldg, int m, const int2* pairs, int npairs, int b,
+                        int k, double* part, DevCounters* cnt, cudaStream_t s);
+
+// Finalisation (EVD): w <- sorted diag(Aw)[0:n] (ascending, stable), Q(:, j)
+// <- Qw(0:n, perm j), A <- Aw(0:n, 0:n).
+cudaError_t launch_finalize_evd(int n, int np, const double* Aw, const double* Qw, double* w,
+                                double* Q, int ldq, double* A, int lda, int* rank_ws,
+                                cudaStream_t s);
+// Finalisation (SVD): sigma_j = ||G(:,j)||, U = G Sigma^+, sorted descending.
+cudaError_t launch_finalize_svd(int m, int n, const double* Gw, int ldgw, const double* Vw,
+                                int ldvw, double* U, int ldu, double* sigma, double* V, int ldv,
+                                double* norms_ws, int* rank_ws, cudaStream_t s);
+// Copy G (m x n, ldg) into Gw (m x np, ld m) with zero pad columns; Vw <- I.
+cudaError_t launch_load_svd(int m, int n, int np, const double* G, int ldg, double* Gw,
+                            double* Vw, DevCounters* cnt, cudaStream_t s);
+// Max over pairs of relmax[0..npairs) into *out (max with its prior value).
+cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaStream_t s);
+
+}  // namespace jac

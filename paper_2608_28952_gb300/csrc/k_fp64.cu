@@ -1,0 +1,958 @@
+// k_fp64.cu -- FP64 kernels of the blocked Jacobi step on sm_103a.
+//
+// GB300's FP64 pipe issues about two DFMA per clock per SM (1.2 TFLOP/s for
+// the GPU), so every kernel here is shaped to issue as few FP64 operations as
+// possible; memory traffic is far below what HBM/L2 can move at that rate.
+//
+//   k_pivot      one CTA per pair: the 2b x 2b pivot of Algorithm 2 (line
+//                "diagonalise the subproblem"), solved by parallel-ordered
+//                scalar Jacobi (Algorithm 2 applied with b = 1) in FP64.  The
+//                symmetric pivot lives in shared memory in packed lower form;
+//                one round rotates every disjoint 2x2 "quad" from both sides
+//                (J_i^T X J_j), a third fewer operations than separate row and
+//                column passes.
+//   k_update_evd the block-row and block-column updates of Algorithm 2 for all
+//                pairs of a step, fused per pair-block: A'_{P1P2} =
+//                V_{P1}^T A_{P1P2} V_{P2} is computed once and written with its
+//                mirror (A stays exactly symmetric), plus Q'(:,P) = Q(:,P) V_P.
+//                A and Q are double-buffered, so no tile is read after it has
+//                been overwritten.
+//   k_gram       split-K Gram blocks G(rows, P)^T G(rows, P) of the one-sided
+//                method (Sec. 6), lower triangle only.
+//   k_update_cols  G'(:,P) = G(:,P) V_P and V'(:,P) = V(:,P) V_P (Algorithm 6).
+//   k_offnorm    Xi(A)^2 (Sec. 2.1) and ||A||_F^2 with a fixed-order two-level
+//                reduction (deterministic), plus the relative measure.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace jac {
+
+// Global row/column of local index x (0..2b-1) of the block pair (I, J).
+__device__ __forceinline__ int pair_map(int I, int J, int b, int x)
+{
+    return x < b ? I * b + x : J * b + (x - b);
+}
+
+// Schedule entry e: the two blocks and whether the entry is frozen (blocks a
+// step of Algorithm 3 leaves out; their transform is the identity).
+__device__ __forceinline__ bool entry(const int2* pairs, int e, int& I, int& J)
+{
+    const int2 pr = pairs[e];
+    const bool frozen = pr.x < 0;
+    I = frozen ? -1 - pr.x : pr.x;
+    J = frozen ? -1 - pr.y : pr.y;
+    return frozen;
+}
+
+// Packed lower-triangular index of symmetric entry (i, j).
+__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+__device__ __forceinline__ int sidx(int i, int j) { return i >= j ? tri(i) + j : tri(j) + i; }
+
+// The textbook 2x2 symmetric Schur rotation: zeta = (aqq - app)/(2 apq),
+// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)) with sgn(0) = +1, c = 1/sqrt(1+t^2),
+// s = t c; J = [[c, s], [-s, c]] makes J^T [[app, apq], [apq, aqq]] J diagonal
+// with diagonal (app - t apq, aqq + t apq).  Every operation is rounded
+// separately (no contraction) so that the decision and the angle are the
+// correctly rounded values of these formulas.
+__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& c, double& s,
+                                       double& dp, double& dq)
+{
+    double zeta = __ddiv_rn(__dsub_rn(aqq, app), __dmul_rn(2.0, apq));
+    double t;
+    if (fabs(zeta) > 1e150) {
+        t = __ddiv_rn(0.5, zeta);
+    } else {
+        double r = __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(zeta, zeta)));
+        t = __ddiv_rn(zeta >= 0.0 ? 1.0 : -1.0, __dadd_rn(fabs(zeta), r));
+    }
+    c = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(t, t))));
+    s = __dmul_rn(t, c);
+    dp = __dsub_rn(app, __dmul_rn(t, apq));
+    dq = __dadd_rn(aqq, __dmul_rn(t, apq));
+}
+
+__device__ __forceinline__ bool rotation_wanted(double app, double aqq, double apq, double tol)
+{
+    if (apq == 0.0) return false;
+    return fabs(apq) > __dmul_rn(__dmul_rn(tol, __dsqrt_rn(fabs(app))), __dsqrt_rn(fabs(aqq)));
+}
+
+// ======================================================================== load
+__global__ void k_load_sym(int n, int np, const double* __restrict__ A, int lda,
+                           double* __restrict__ Aw, const double* __restrict__ Qin, int ldq,
+                           double* __restrict__ Qw, int warm, DevCounters* cnt)
+{
+    const long long total = (long long)np * np;
+    int bad = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(idx % np), j = (int)(idx / np);
+        double v = 0.0;
+        if (i < n && j < n) {
+            v = i >= j ? A[i + (size_t)lda * j] : A[j + (size_t)lda * i];
+            if (!isfinite(v)) bad = 1;
+        }
+        Aw[idx] = v;
+        if (Qw) {
+            double q = (i == j) ? 1.0 : 0.0;
+            if (warm && i < n && j < n) q = Qin[i + (size_t)ldq * j];
+            Qw[idx] = q;
+        }
+    }
+    if (bad) atomicExch(&cnt->nonfinite, 1);
+}
+
+cudaError_t launch_load_sym(int n, int np, const double* A, int lda, double* Aw,
+                            const double* Qin, int ldq, double* Qw, int warm, DevCounters* cnt,
+                            cudaStream_t s)
+{
+    long long total = (long long)np * np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_load_sym<<<blocks, 256, 0, s>>>(n, np, A, lda, Aw, Qin, ldq, Qw, warm, cnt);
+    return cudaGetLastError();
+}
+
+__global__ void k_load_svd(int m, int n, int np, const double* __restrict__ G, int ldg,
+                           double* __restrict__ Gw, double* __restrict__ Vw, DevCounters* cnt)
+{
+    const long long totg = (long long)m * np, totv = (long long)np * np;
+    int bad = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < totg + totv;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < totg) {
+            int r = (int)(idx % m), j = (int)(idx / m);
+            double v = j < n ? G[r + (size_t)ldg * j] : 0.0;
+            if (!isfinite(v)) bad = 1;
+            Gw[idx] = v;
+        } else if (Vw) {
+            long long t = idx - totg;
+            int i = (int)(t % np), j = (int)(t / np);
+            Vw[t] = (i == j) ? 1.0 : 0.0;
+        }
+    }
+    if (bad) atomicExch(&cnt->nonfinite, 1);
+}
+
+cudaError_t launch_load_svd(int m, int n, int np, const double* G, int ldg, double* Gw,
+                            double* Vw, DevCounters* cnt, cudaStream_t s)
+{
+    long long total = (long long)m * np + (long long)np * np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_load_svd<<<blocks, 256, 0, s>>>(m, n, np, G, ldg, Gw, Vw, cnt);
+    return cudaGetLastError();
+}
+
+// ======================================================================== off-norm
+constexpr int RED_T = 256;
+
+int reduce_blocks_for(int np)
+{
+    int g = np < 608 ? np : 608;  // 4 per SM at most
+    return g < 1 ? 1 : g;
+}
+
+__global__ void __launch_bounds__(RED_T) k_offnorm(int np, const double* __restrict__ Aw,
+                                                   double* partial, unsigned int* ticket,
+                                                   double* result, int want_rel)
+{
+    __shared__ double s_off[RED_T], s_all[RED_T], s_rel[RED_T];
+    __shared__ bool last;
+    const int tid = threadIdx.x, G = gridDim.x;
+    double off = 0.0, all = 0.0, rel = 0.0;
+    for (int j = blockIdx.x; j < np; j += G) {
+        const double* col = Aw + (size_t)np * j;
+        const double ajj = fabs(col[j]);
+        for (int i = tid; i < np; i += RED_T) {
+            double v = col[i];
+            double v2 = v * v;
+            all += v2;
+            if (i != j) {
+                off += v2;
+                if (want_rel && v != 0.0) {
+                    double d = fabs(Aw[(size_t)np * i + i]) * ajj;
+                    double r = d > 0.0 ? v2 / d : INFINITY;
+                    rel = fmax(rel, r);
+                }
+            }
+        }
+    }
+    s_off[tid] = off;
+    s_all[tid] = all;
+    s_rel[tid] = rel;
+    __syncthreads();
+    for (int w = RED_T / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+            s_off[tid] += s_off[tid + w];
+            s_all[tid] += s_all[tid + w];
+            s_rel[tid] = fmax(s_rel[tid], s_rel[tid + w]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        partial[3 * blockIdx.x + 0] = s_off[0];
+        partial[3 * blockIdx.x + 1] = s_all[0];
+        partial[3 * blockIdx.x + 2] = s_rel[0];
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == (unsigned int)G - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        double o = 0.0, a = 0.0, r = 0.0;
+        for (int g = 0; g < G; ++g) {  // fixed order
+            o += ((volatile double*)partial)[3 * g + 0];
+            a += ((volatile double*)partial)[3 * g + 1];
+            r = fmax(r, ((volatile double*)partial)[3 * g + 2]);
+        }
+        result[0] = o;
+        result[1] = a;
+        result[2] = sqrt(r);
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned int* ticket,
+                           double* result, bool want_rel, cudaStream_t s)
+{
+    k_offnorm<<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, want_rel);
+    return cudaGetLastError();
+}
+
+// ======================================================================== pivot
+constexpr int PIV_T = 512;
+
+__host__ __device__ static inline size_t tri_pad(int k) { return ((size_t)k * (k + 1) / 2 + 1) & ~(size_t)1; }
+
+size_t pivot_gscratch_doubles(int k) { return k <= 128 ? 0 : tri_pad(k) + (size_t)k * k; }
+
+static size_t pivot_smem_bytes(int k)
+{
+    const int half = k / 2, nq = half * (half - 1) / 2;
+    size_t small = (size_t)4 * half * sizeof(double) + (size_t)3 * half * sizeof(int) +
+                   (size_t)nq * sizeof(unsigned) + 64;
+    if (k <= 128) small += (tri_pad(k) + (size_t)k * k) * sizeof(double);
+    return small;
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
+{
+    extern __shared__ __align__(16) double smem[];
+    const int e = blockIdx.x, tid = threadIdx.x;
+    const int k = a.k, b = a.b, half = k >> 1, nq = half * (half - 1) / 2;
+    int I, J;
+    const bool frozen = entry(a.pairs, e, I, J);
+    const size_t ntp = tri_pad(k);
+
+    double *Ap, *V, *tail;
+    if (SMEM) {
+        Ap = smem;
+        V = smem + ntp;
+        tail = V + (size_t)k * k;
+    } else {
+        Ap = a.gscratch + (size_t)e * (ntp + (size_t)k * k);
+        V = Ap + ntp;
+        tail = smem;
+    }
+    double* rc = tail;
+    double* rs = rc + half;
+    double* rdp = rs + half;
+    double* rdq = rdp + half;
+    int* rp = (int*)(rdq + half);
+    int* rq = rp + half;
+    int* ron = rq + half;
+    unsigned* quad = (unsigned*)(ron + half);
+    __shared__ int s_cnt;
+    __shared__ double s_red[PIV_T / 32];
+    __shared__ int s_dest[256];   // output slot of each eigenpair (k <= 256)
+    __shared__ int s_pos[256];    // the pivot's non-padding positions, ascending
+
+    // ---- pivot Ahat (lower triangle) and V = I
+    if (a.gram == nullptr) {
+        for (int idx = tid; idx < k * k; idx += PIV_T) {
+            int ii = idx % k, jj = idx / k;
+            if (ii >= jj)
+                Ap[tri(ii) + jj] =
+                    a.Ain[pair_map(I, J, b, ii) + (size_t)a.ld * pair_map(I, J, b, jj)];
+        }
+    } else {
+        const double* g = a.gram + (size_t)e * a.npanels * k * k;
+        for (int idx = tid; idx < k * k; idx += PIV_T) {
+            int ii = idx % k, jj = idx / k;
+            if (ii < jj) continue;
+            double s = 0.0;
+            for (int r = 0; r < a.npanels; ++r) s += g[(size_t)r * k * k + idx];  // fixed order
+            Ap[tri(ii) + jj] = s;
+        }
+    }
+    for (int idx = tid; idx < k * k; idx += PIV_T) V[idx] = (idx % k == idx / k) ? 1.0 : 0.0;
+    for (int e2 = 1 + tid; e2 < half; e2 += PIV_T)
+        for (int e1 = 0; e1 < e2; ++e1) quad[(e2 * (e2 - 1) >> 1) + e1] = (unsigned)e1 | ((unsigned)e2 << 16);
+    __syncthreads();
+
+    // ---- one-sided stop statistic: max_{i != j} |a_ij| / sqrt(a_ii a_jj) before rotating
+    if (a.relmax) {
+        double mx = 0.0;
+        if (!frozen)
+        for (int idx = tid; idx < k * k; idx += PIV_T) {
+            int ii = idx % k, jj = idx / k;
+            if (ii <= jj) continue;
+            double d = sqrt(Ap[tri(ii) + ii]) * sqrt(Ap[tri(jj) + jj]);
+            if (d > 0.0) mx = fmax(mx, fabs(Ap[tri(ii) + jj]) / d);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int w = 0; w < PIV_T / 32; ++w) m = fmax(m, s_red[w]);
+            a.relmax[e] = m;
+        }
+    }
+
+    // ---- inner sweeps: round-robin over the k indices, k-1 rounds of k/2 rotations
+    const double tol = a.tol_rel;
+    int total_rot = 0, sweeps = 0;
+    const int max_sweeps = frozen ? 0 : a.max_sweeps;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        for (int r = 0; r < k - 1; ++r) {
+            for (int ee = tid; ee < half; ee += PIV_T) {
+                const int pa = ee, pb = k - 1 - ee;
+                const int ia = pa == 0 ? 0 : 1 + (pa - 1 + r) % (k - 1);
+                const int ib = 1 + (pb - 1 + r) % (k - 1);
+                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+                const double app = Ap[tri(p) + p], aqq = Ap[tri(q) + q], apq = Ap[tri(q) + p];
+                const bool on = rotation_wanted(app, aqq, apq, tol);
+                rp[ee] = p;
+                rq[ee] = q;
+                ron[ee] = on;
+                if (on) {
+                    double c, s, dp, dq;
+                    schur2(app, aqq, apq, c, s, dp, dq);
+                    rc[ee] = c;
+                    rs[ee] = s;
+                    rdp[ee] = dp;
+                    rdq[ee] = dq;
+                    atomicAdd(&s_cnt, 1);
+                }
+            }
+            __syncthreads();
+            // both-sided rotation of every 2x2 quad (rows of pair e1, columns of pair e2)
+            for (int qi = tid; qi < nq; qi += PIV_T) {
+                const unsigned qq = quad[qi];
+                const int e1 = qq & 0xffff, e2 = qq >> 16;
+                const int on1 = ron[e1], on2 = ron[e2];
+                if (!(on1 | on2)) continue;
+                const int p1 = rp[e1], q1 = rq[e1], p2 = rp[e2], q2 = rq[e2];
+                const int i00 = sidx(p1, p2), i01 = sidx(p1, q2), i10 = sidx(q1, p2),
+                          i11 = sidx(q1, q2);
+                double x00 = Ap[i00], x01 = Ap[i01], x10 = Ap[i10], x11 = Ap[i11];
+                if (on1) {  // rows: J1^T X
+                    const double c = rc[e1], s = rs[e1];
+                    double y00 = c * x00 - s * x10, y10 = s * x00 + c * x10;
+                    double y01 = c * x01 - s * x11, y11 = s * x01 + c * x11;
+                    x00 = y00; x10 = y10; x01 = y01; x11 = y11;
+                }
+                if (on2) {  // columns: X J2
+                    const double c = rc[e2], s = rs[e2];
+                    double y00 = c * x00 - s * x01, y01 = s * x00 + c * x01;
+                    double y10 = c * x10 - s * x11, y11 = s * x10 + c * x11;
+                    x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+                }
+                Ap[i00] = x00; Ap[i01] = x01; Ap[i10] = x10; Ap[i11] = x11;
+            }
+            for (int ee = tid; ee < half; ee += PIV_T) {
+                if (!ron[ee]) continue;
+                const int p = rp[ee], q = rq[ee];
+                Ap[tri(p) + p] = rdp[ee];
+                Ap[tri(q) + q] = rdq[ee];
+                Ap[tri(q) + p] = 0.0;
+            }
+            for (int it = tid; it < half * k; it += PIV_T) {  // V <- V J
+                const int ee = it / k, row = it - ee * k;
+                if (!ron[ee]) continue;
+                const int p = rp[ee], q = rq[ee];
+                const double c = rc[ee], s = rs[ee];
+                const double vp = V[row + (size_t)p * k], vq = V[row + (size_t)q * k];
+                V[row + (size_t)p * k] = c * vp - s * vq;
+                V[row + (size_t)q * k] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        const int cnt = s_cnt;
+        total_rot += cnt;
+        sweeps = sw + 1;
+        __syncthreads();
+        if (cnt == 0) break;
+    }
+
+    // ---- permutation Vhat <- Vhat P: eigenpair at position x moves to
+    // s_dest[x]; with order == 1 the non-padding positions receive their
+    // eigenvalues in descending order (ties by position), padding stays put.
+    if (tid == 0) {
+        int nr = 0;
+        for (int x = 0; x < k; ++x)
+            if (pair_map(I, J, b, x) < a.n_real) s_pos[nr++] = x;
+    }
+    __syncthreads();
+    for (int x = tid; x < k; x += PIV_T) {
+        int dest = x;
+        if (a.order == 1 && total_rot > 0 && pair_map(I, J, b, x) < a.n_real) {
+            const double dx = Ap[tri(x) + x];
+            int r = 0;
+            for (int y = 0; y < k; ++y) {
+                if (y == x || pair_map(I, J, b, y) >= a.n_real) continue;
+                const double dy = Ap[tri(y) + y];
+                r += (dy > dx) || (dy == dx && y < x);
+            }
+            dest = s_pos[r];
+        }
+        s_dest[x] = dest;
+    }
+    __syncthreads();
+
+    // ---- outputs: V and V^T, D into the next A, counters
+    double* Vo = a.V + (size_t)e * 2 * k * k;
+    for (int idx = tid; idx < k * k; idx += PIV_T) {
+        const int ii = idx % k, jj = idx / k;
+        const double v = V[idx];                 // V(ii, jj) -> column s_dest[jj]
+        Vo[ii + (size_t)k * s_dest[jj]] = v;
+        Vo[(size_t)k * k + s_dest[jj] + (size_t)k * ii] = v;
+    }
+    if (a.Aout) {
+        for (int idx = tid; idx < k * k; idx += PIV_T) {
+            const int ii = idx % k, jj = idx / k;
+            a.Aout[pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pair_map(I, J, b, s_dest[jj])] =
+                Ap[sidx(ii, jj)];
+        }
+    }
+    if (tid == 0) {
+        a.rot[e] = total_rot;
+        atomicAdd(&a.cnt->rotations, (unsigned long long)total_rot);
+        atomicAdd(&a.cnt->inner_sweeps, (unsigned long long)sweeps);
+        if (!frozen) atomicAdd(&a.cnt->pair_solves, 1ull);
+        // per applied rotation: its row pair in k/2-1 quads (12 flops each, as
+        // left and as right factor) and its column pair of V (6k flops)
+        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)(18 * k));
+    }
+}
+
+cudaError_t launch_pivot(const PivotArgs& a, cudaStream_t s)
+{
+    if (a.npairs <= 0) return cudaSuccess;
+    size_t smem = pivot_smem_bytes(a.k);
+    if (a.k <= 128) {
+        cudaError_t e = cudaFuncSetAttribute(k_pivot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_pivot<true><<<a.npairs, PIV_T, smem, s>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_pivot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_pivot<false><<<a.npairs, PIV_T, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// ======================================================================== GEMM tiles
+// C(M x 32) += Aop(M x K) Bop(K x 32) on 256 threads: thread (ty = tid % 32,
+// tx = tid / 32) owns rows ty + 32 i (i < MR) and columns tx + 8 j (j < 4).
+// K is streamed through shared memory in chunks of KC.
+constexpr int UPD_T = 256, KC = 16, TN = 32, T_LD = TN + 1;
+
+template <int MR>
+struct Tile {
+    double acc[MR][4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    }
+};
+
+// As: [KC][AS_LD], Bs: [KC][T_LD] (or B directly from a shared buffer).
+// fa(m, kk) loads Aop(m, kk); fb(kk, j) loads Bop(kk, j).  a_kfast / b_kfast
+// choose which index runs fastest across threads while loading (coalescing).
+template <int MR, bool A_KFAST, bool B_SMEM, bool B_KFAST, class FA, class FB>
+__device__ __forceinline__ void gemm_tile(Tile<MR>& t, int M, int K, int mr, FA fa, FB fb,
+                                          double* As, double* Bs, const double* Bsm)
+{
+    constexpr int AS_LD = 32 * MR + 1;
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const int kc = min(KC, K - k0);
+        if (A_KFAST) {
+            for (int idx = tid; idx < kc * M; idx += UPD_T) {
+                const int m = idx / kc, kk = idx - m * kc;
+                As[kk * AS_LD + m] = fa(m, k0 + kk);
+            }
+        } else {
+            for (int idx = tid; idx < kc * M; idx += UPD_T) {
+                const int kk = idx / M, m = idx - kk * M;
+                As[kk * AS_LD + m] = fa(m, k0 + kk);
+            }
+        }
+        if (!B_SMEM) {
+            if (B_KFAST) {
+                for (int idx = tid; idx < kc * TN; idx += UPD_T) {
+                    const int j = idx / kc, kk = idx - j * kc;
+                    Bs[kk * T_LD + j] = fb(k0 + kk, j);
+                }
+            } else {
+                for (int idx = tid; idx < kc * TN; idx += UPD_T) {
+                    const int kk = idx >> 5, j = idx & 31;
+                    Bs[kk * T_LD + j] = fb(k0 + kk, j);
+                }
+            }
+        }
+        __syncthreads();
+        const double* Bk = B_SMEM ? (Bsm + (size_t)k0 * T_LD) : Bs;
+        for (int kk = 0; kk < kc; ++kk) {
+            double bv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bk[kk * T_LD + tx + 8 * j];
+#pragma unroll
+            for (int i = 0; i < MR; ++i) {
+                if (i < mr) {
+                    const double av = As[kk * AS_LD + ty + 32 * i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) t.acc[i][j] = fma(av, bv[j], t.acc[i][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int MR>
+static size_t update_smem_bytes()
+{
+    return ((size_t)KC * (32 * MR + 1) + (size_t)KC * T_LD + (size_t)(32 * MR) * T_LD) *
+           sizeof(double);
+}
+
+// ======================================================================== EVD update
+__device__ __forceinline__ void decode_pairblock(int pb, int& e1, int& e2)
+{
+    int t = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)pb)) * 0.5f);
+    while (t * (t - 1) / 2 > pb) --t;
+    while ((t + 1) * t / 2 <= pb) ++t;
+    e2 = t;
+    e1 = pb - t * (t - 1) / 2;
+}
+
+template <int MR>
+__global__ void __launch_bounds__(UPD_T, 2) k_update_evd(UpdateArgs a, int n_sand, int nchunks)
+{
+    extern __shared__ __align__(16) double sm[];
+    constexpr int AS_LD = 32 * MR + 1;
+    double* As = sm;
+    double* Bs = As + KC * AS_LD;
+    double* Ts = Bs + KC * T_LD;  // [32*MR][T_LD]
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    const int k = a.k, b = a.b;
+    const int item = blockIdx.x;
+    Tile<MR> t;
+
+    if (item < n_sand) {
+        // ---------------- A'_{P1P2} (:, chunk) = V1^T (A_{P1P2} V2(:, chunk))
+        const int pbk = item / nchunks, c = item - pbk * nchunks;
+        int e1, e2;
+        decode_pairblock(pbk, e1, e2);
+        int I1, J1, I2, J2;
+        entry(a.pairs, e1, I1, J1);
+        entry(a.pairs, e2, I2, J2);
+        const int r1 = a.rot[e1], r2 = a.rot[e2];
+        const int c0 = c * TN, kw = min(TN, k - c0);
+        const int mr = (k + 31) >> 5;
+        const double* Ain = a.Ain;
+        const int lda = a.lda;
+        const double* V2 = a.V + (size_t)e2 * 2 * k * k;          // V2, column-major
+        const double* V1t = a.V + (size_t)e1 * 2 * k * k + (size_t)k * k;  // V1^T
+        // stage 1: T = A_blk V2(:, chunk)  (or the plain chunk when V2 == I)
+        if (r2) {
+            t.zero();
+            gemm_tile<MR, false, false, true>(
+                t, k, k, mr,
+                [&](int m, int kk) { return Ain[pair_map(I1, J1, b, m) + (size_t)lda * pair_map(I2, J2, b, kk)]; },
+                [&](int kk, int j) { return j < kw ? V2[kk + (size_t)k * (c0 + j)] : 0.0; }, As, Bs,
+                nullptr);
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i < mr) Ts[(ty + 32 * i) * T_LD + tx + 8 * j] = t.acc[i][j];
+        } else {
+            for (int idx = tid; idx < k * TN; idx += UPD_T) {
+                const int j = idx / k, m = idx - j * k;
+                Ts[m * T_LD + j] = j < kw ? Ain[pair_map(I1, J1, b, m) + (size_t)lda * pair_map(I2, J2, b, c0 + j)] : 0.0;
+            }
+        }
+        __syncthreads();
+        // stage 2: O = V1^T T
+        if (r1) {
+            t.zero();
+            gemm_tile<MR, false, true, false>(
+                t, k, k, mr, [&](int m, int kk) { return V1t[m + (size_t)k * kk]; },
+                [&](int, int) { return 0.0; }, As, Bs, Ts);
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = ty + 32 * i, jj = tx + 8 * j;
+                    if (i < mr && m < k && jj < kw) {
+                        const int gi = pair_map(I1, J1, b, m), gj = pair_map(I2, J2, b, c0 + jj);
+                        a.Aout[gi + (size_t)lda * gj] = t.acc[i][j];
+                        a.Aout[gj + (size_t)lda * gi] = t.acc[i][j];
+                    }
+                }
+        } else {
+            for (int idx = tid; idx < k * TN; idx += UPD_T) {
+                const int j = idx / k, m = idx - j * k;
+                if (j < kw) {
+                    const int gi = pair_map(I1, J1, b, m), gj = pair_map(I2, J2, b, c0 + j);
+                    const double v = Ts[m * T_LD + j];
+                    a.Aout[gi + (size_t)lda * gj] = v;
+                    a.Aout[gj + (size_t)lda * gi] = v;
+                }
+            }
+        }
+        if (tid == 0)
+            atomicAdd(&a.cnt->flops_fp64, (unsigned long long)(r1 ? 2ull * k * k * kw : 0) +
+                                              (unsigned long long)(r2 ? 2ull * k * k * kw : 0));
+    } else {
+        // ---------------- Q'(rows, P chunk) = Q(rows, P) V_P(:, chunk)
+        const int H = 32 * MR;
+        const int nrt = (a.qrows + H - 1) / H;
+        int rest = item - n_sand;
+        const int c = rest % nchunks;
+        rest /= nchunks;
+        const int rt = rest % nrt, e = rest / nrt;
+        int I, J;
+        entry(a.pairs, e, I, J);
+        const int r = a.rot[e];
+        const int c0 = c * TN, kw = min(TN, k - c0), r0 = rt * H, M = min(H, a.qrows - r0);
+        const int mr = (M + 31) >> 5;
+        const double* Qin = a.Qin;
+        const int ldq = a.ldq;
+        const double* Vp = a.V + (size_t)e * 2 * k * k;
+        if (r) {
+            t.zero();
+            gemm_tile<MR, false, false, true>(
+                t, M, k, mr, [&](int m, int kk) { return Qin[(r0 + m) + (size_t)ldq * pair_map(I, J, b, kk)]; },
+                [&](int kk, int j) { return j < kw ? Vp[kk + (size_t)k * (c0 + j)] : 0.0; }, As, Bs,
+                nullptr);
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = ty + 32 * i, jj = tx + 8 * j;
+                    if (i < mr && m < M && jj < kw)
+                        a.Qout[(r0 + m) + (size_t)ldq * pair_map(I, J, b, c0 + jj)] = t.acc[i][j];
+                }
+            if (tid == 0) atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+        } else {
+            for (int idx = tid; idx < M * kw; idx += UPD_T) {
+                const int j = idx / M, m = idx - j * M;
+                const size_t o = (r0 + m) + (size_t)ldq * pair_map(I, J, b, c0 + j);
+                a.Qout[o] = Qin[o];
+            }
+        }
+    }
+}
+
+template <int MR>
+static cudaError_t launch_update_evd_mr(const UpdateArgs& a, cudaStream_t s)
+{
+    const int nchunks = (a.k + TN - 1) / TN;
+    const int n_sand = a.npairs * (a.npairs - 1) / 2 * nchunks;
+    const int H = 32 * MR;
+    const int n_q = a.Qin ? a.npairs * ((a.qrows + H - 1) / H) * nchunks : 0;
+    const int items = n_sand + n_q;
+    if (items == 0) return cudaSuccess;
+    const size_t smem = update_smem_bytes<MR>();
+    cudaError_t e = cudaFuncSetAttribute(k_update_evd<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_update_evd<MR><<<items, UPD_T, smem, s>>>(a, n_sand, nchunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_evd(const UpdateArgs& a, cudaStream_t s)
+{
+    if (a.k <= 32) return launch_update_evd_mr<1>(a, s);
+    if (a.k <= 64) return launch_update_evd_mr<2>(a, s);
+    if (a.k <= 128) return launch_update_evd_mr<4>(a, s);
+    return launch_update_evd_mr<8>(a, s);
+}
+
+// ======================================================================== one-sided column update
+template <int MR>
+__global__ void __launch_bounds__(UPD_T, 2) k_update_cols(ColUpdateArgs a, int n_g, int nchunks)
+{
+    extern __shared__ __align__(16) double sm[];
+    constexpr int AS_LD = 32 * MR + 1;
+    double* As = sm;
+    double* Bs = As + KC * AS_LD;
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    const int k = a.k, b = a.b, H = 32 * MR;
+    int item = blockIdx.x;
+    const double* Min;
+    double* Mout;
+    int ld, rows;
+    if (item < n_g) {
+        Min = a.Gin; Mout = a.Gout; ld = a.ldg; rows = a.m;
+    } else {
+        item -= n_g;
+        Min = a.Vin; Mout = a.Vout; ld = a.ldv; rows = a.vrows;
+    }
+    const int nrt = (rows + H - 1) / H;
+    const int c = item % nchunks;
+    const int rest = item / nchunks;
+    const int rt = rest % nrt, e = rest / nrt;
+    int I, J;
+    entry(a.pairs, e, I, J);
+    const int r = a.rot[e];
+    const int c0 = c * TN, kw = min(TN, k - c0), r0 = rt * H, M = min(H, rows - r0);
+    const int mr = (M + 31) >> 5;
+    const double* Vp = a.Vh + (size_t)e * 2 * k * k;
+    if (r) {
+        Tile<MR> t;
+        t.zero();
+        gemm_tile<MR, false, false, true>(
+            t, M, k, mr, [&](int m, int kk) { return Min[(r0 + m) + (size_t)ld * pair_map(I, J, b, kk)]; },
+            [&](int kk, int j) { return j < kw ? Vp[kk + (size_t)k * (c0 + j)] : 0.0; }, As, Bs, nullptr);
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m = ty + 32 * i, jj = tx + 8 * j;
+                if (i < mr && m < M && jj < kw)
+                    Mout[(r0 + m) + (size_t)ld * pair_map(I, J, b, c0 + jj)] = t.acc[i][j];
+            }
+        if (tid == 0) atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+    } else {
+        for (int idx = tid; idx < M * kw; idx += UPD_T) {
+            const int j = idx / M, m = idx - j * M;
+            const size_t o = (r0 + m) + (size_t)ld * pair_map(I, J, b, c0 + j);
+            Mout[o] = Min[o];
+        }
+    }
+}
+
+template <int MR>
+static cudaError_t launch_update_cols_mr(const ColUpdateArgs& a, cudaStream_t s)
+{
+    const int nchunks = (a.k + TN - 1) / TN, H = 32 * MR;
+    const int n_g = a.npairs * ((a.m + H - 1) / H) * nchunks;
+    const int n_v = a.Vin ? a.npairs * ((a.vrows + H - 1) / H) * nchunks : 0;
+    if (n_g + n_v == 0) return cudaSuccess;
+    const size_t smem = ((size_t)KC * (32 * MR + 1) + (size_t)KC * T_LD) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_update_cols<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_update_cols<MR><<<n_g + n_v, UPD_T, smem, s>>>(a, n_g, nchunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_cols(const ColUpdateArgs& a, cudaStream_t s)
+{
+    // tiles of 128 rows: the inner dimension is k, so a 128 x 32 tile costs 2*128*32*k
+    return launch_update_cols_mr<4>(a, s);
+}
+
+// ======================================================================== Gram (split K over rows)
+constexpr int GRAM_ROWS = 512;
+int gram_panel_rows() { return GRAM_ROWS; }
+int gram_panels_for(int m) { return (m + GRAM_ROWS - 1) / GRAM_ROWS; }
+
+// Item (pair e, panel r, column chunk c): rows c0.. of the k x k Gram block
+// (lower triangle only: rows >= c0), K = the panel's rows of G.
+template <int MR>
+__global__ void __launch_bounds__(UPD_T, 2) k_gram(const double* __restrict__ G, int ldg, int m,
+                                                  const int2* __restrict__ pairs, int b, int k,
+                                                  int npanels, int nchunks, double* __restrict__ part,
+                                                  DevCounters* cnt)
+{
+    extern __shared__ __align__(16) double sm[];
+    constexpr int AS_LD = 32 * MR + 1;
+    double* As = sm;
+    double* Bs = As + KC * AS_LD;
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    const int item = blockIdx.x;
+    const int c = item % nchunks;
+    const int rest = item / nchunks;
+    const int pr = rest % npanels, e = rest / npanels;
+    int I, J;
+    entry(pairs, e, I, J);
+    const int c0 = c * TN, kw = min(TN, k - c0);
+    const int row0 = c0;  // lower triangle: output rows >= first column of the chunk
+    const int M = k - row0, mr = (M + 31) >> 5;
+    const int g0 = pr * GRAM_ROWS, K = min(GRAM_ROWS, m - g0);
+    Tile<MR> t;
+    t.zero();
+    gemm_tile<MR, true, false, true>(
+        t, M, K, mr,
+        [&](int mm, int kk) { return G[(g0 + kk) + (size_t)ldg * pair_map(I, J, b, row0 + mm)]; },
+        [&](int kk, int j) { return j < kw ? G[(g0 + kk) + (size_t)ldg * pair_map(I, J, b, c0 + j)] : 0.0; },
+        As, Bs, nullptr);
+    double* out = part + ((size_t)e * npanels + pr) * k * k;
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int mm = ty + 32 * i, jj = tx + 8 * j;
+            if (i < mr && mm < M && jj < kw) out[(row0 + mm) + (size_t)k * (c0 + jj)] = t.acc[i][j];
+        }
+    if (tid == 0) atomicAdd(&cnt->flops_fp64, 2ull * M * K * kw);
+}
+
+cudaError_t launch_gram(const double* G, int ldg, int m, const int2* pairs, int npairs, int b,
+                        int k, double* part, DevCounters* cnt, cudaStream_t s)
+{
+    const int nchunks = (k + TN - 1) / TN, npanels = gram_panels_for(m);
+    const int items = npairs * npanels * nchunks;
+    if (items == 0) return cudaSuccess;
+#define JAC_GRAM(MR)                                                                               \
+    do {                                                                                           \
+        const size_t smem = ((size_t)KC * (32 * MR + 1) + (size_t)KC * T_LD) * sizeof(double);     \
+        cudaError_t e = cudaFuncSetAttribute(k_gram<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                            \
+        k_gram<MR><<<items, UPD_T, smem, s>>>(G, ldg, m, pairs, b, k, npanels, nchunks, part, cnt); \
+    } while (0)
+    if (k <= 32) JAC_GRAM(1);
+    else if (k <= 64) JAC_GRAM(2);
+    else if (k <= 128) JAC_GRAM(4);
+    else JAC_GRAM(8);
+#undef JAC_GRAM
+    return cudaGetLastError();
+}
+
+// ======================================================================== finalisation
+// Stable rank of key[i] among key[0..n): ascending (asc) or descending.
+__global__ void k_rank(int n, const double* __restrict__ key, int stride, int asc,
+                       int* __restrict__ rank)
+{
+    __shared__ double tile[256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double ki = i < n ? key[(size_t)i * stride] : 0.0;
+    int r = 0;
+    for (int j0 = 0; j0 < n; j0 += 256) {
+        const int j = j0 + threadIdx.x;
+        tile[threadIdx.x] = j < n ? key[(size_t)j * stride] : 0.0;
+        __syncthreads();
+        const int lim = min(256, n - j0);
+        for (int u = 0; u < lim; ++u) {
+            const double kj = tile[u];
+            const int jj = j0 + u;
+            const bool before = asc ? (kj < ki || (kj == ki && jj < i)) : (kj > ki || (kj == ki && jj < i));
+            r += before;
+        }
+        __syncthreads();
+    }
+    if (i < n) rank[i] = r;
+}
+
+__global__ void k_finalize_evd(int n, int np, const double* __restrict__ Aw,
+                               const double* __restrict__ Qw, const int* __restrict__ rank,
+                               double* __restrict__ w, double* __restrict__ Q, int ldq,
+                               double* __restrict__ A, int lda)
+{
+    const long long total = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % n), j = (int)(idx / n);
+        if (Q) Q[i + (size_t)ldq * rank[j]] = Qw[i + (size_t)np * j];
+        if (A) A[rank[i] + (size_t)lda * rank[j]] = Aw[i + (size_t)np * j];
+        if (i == 0) w[rank[j]] = Aw[j + (size_t)np * j];
+    }
+}
+
+cudaError_t launch_finalize_evd(int n, int np, const double* Aw, const double* Qw, double* w,
+                                double* Q, int ldq, double* A, int lda, int* rank_ws,
+                                cudaStream_t s)
+{
+    k_rank<<<(n + 255) / 256, 256, 0, s>>>(n, Aw, np + 1, 1, rank_ws);
+    long long total = (long long)n * n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_finalize_evd<<<blocks, 256, 0, s>>>(n, np, Aw, Qw, rank_ws, w, Q, ldq, A, lda);
+    return cudaGetLastError();
+}
+
+__global__ void k_colnorm(int m, const double* __restrict__ Gw, int ld, double* __restrict__ norms)
+{
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int r = threadIdx.x; r < m; r += 256) {
+        const double v = Gw[r + (size_t)ld * j];
+        s = fma(v, v, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) norms[j] = sqrt(red[0]);
+}
+
+__global__ void k_finalize_svd(int m, int n, const double* __restrict__ Gw, int ldgw,
+                               const double* __restrict__ Vw, int ldvw,
+                               const double* __restrict__ norms, const int* __restrict__ rank,
+                               double* __restrict__ U, int ldu, double* __restrict__ sigma,
+                               double* __restrict__ V, int ldv)
+{
+    const long long totu = (long long)m * n, totv = V ? (long long)n * n : 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < totu + totv;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < totu) {
+            const int r = (int)(idx % m), j = (int)(idx / m);
+            const double nj = norms[j];
+            U[r + (size_t)ldu * rank[j]] = nj > 0.0 ? Gw[r + (size_t)ldgw * j] / nj : 0.0;
+            if (r == 0) sigma[rank[j]] = nj;
+        } else {
+            const long long t = idx - totu;
+            const int r = (int)(t % n), j = (int)(t / n);
+            V[r + (size_t)ldv * rank[j]] = Vw[r + (size_t)ldvw * j];
+        }
+    }
+}
+
+cudaError_t launch_finalize_svd(int m, int n, const double* Gw, int ldgw, const double* Vw,
+                                int ldvw, double* U, int ldu, double* sigma, double* V, int ldv,
+                                double* norms_ws, int* rank_ws, cudaStream_t s)
+{
+    k_colnorm<<<n, 256, 0, s>>>(m, Gw, ldgw, norms_ws);
+    k_rank<<<(n + 255) / 256, 256, 0, s>>>(n, norms_ws, 1, 0, rank_ws);
+    long long total = (long long)m * n + (V ? (long long)n * n : 0);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_finalize_svd<<<blocks, 256, 0, s>>>(m, n, Gw, ldgw, Vw, ldvw, norms_ws, rank_ws, U, ldu,
+                                          sigma, V, ldv);
+    return cudaGetLastError();
+}
+
+__global__ void k_max_into(const double* __restrict__ v, int n, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = *out;
+        for (int i = 0; i < n; ++i) m = fmax(m, v[i]);
+        *out = m;
+    }
+}
+
+cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaStream_t s)
+{
+    k_max_into<<<1, 32, 0, s>>>(relmax, npairs, out);
+    return cudaGetLastError();
+}
+
+}  // namespace jac

@@ -1,0 +1,77 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/jacobi.h declares, and its host-side logic (the pair schedule of
+Sec. 3 / Algorithm 3, parameter defaults, status strings) matches the oracle
+and the header."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(jacobi_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def jg():
+    from paper_2608_28952_gb300 import build
+    build.build()
+    import paper_2608_28952_gb300 as m
+    m.lib()
+    return m
+
+
+def test_every_declared_symbol_is_exported(jg):
+    names = _declared()
+    assert {"jacobi_syev", "jacobi_gesvd", "jacobi_params_default"} <= names
+    L = C.CDLL(jg.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names == set(jg.SIGNATURES), names ^ set(jg.SIGNATURES)
+
+
+def test_params_default_matches_header(jg):
+    p = jg.params()
+    assert p.b == 32 and p.max_sweeps == 30 and p.inner_max_sweeps == 30
+    assert p.tol == 1e-14 and p.inner_tol == 4 * 2.0 ** -53
+    assert p.precision == jg.PREC_FP64 and p.conv == jg.CONV_OFF_ABS
+    assert p.want_vectors == 1 and p.warm_start == 0
+
+
+def test_status_strings(jg):
+    assert jg.status_string(0) == "converged"
+    assert "max_sweeps" in jg.status_string(3)
+    assert "non-finite" in jg.status_string(jg.ERR_NONFINITE)
+    assert "invalid" in jg.status_string(-2)
+
+
+@pytest.mark.parametrize("kind", [oracle.ORDER_ROUND_ROBIN, oracle.ORDER_ANTI_DIAGONAL])
+def test_library_schedule_equals_oracle_schedule(jg, kind):
+    for N in range(2, 70):
+        if kind == oracle.ORDER_ROUND_ROBIN and N % 2:
+            with pytest.raises(ValueError):
+                jg.jacobi_ordering_table(kind, N)
+            continue
+        assert jg.jacobi_ordering_table(kind, N) == oracle.ordering(kind, N)
+
+
+def test_invalid_schedule_arguments(jg):
+    with pytest.raises(ValueError):
+        jg.jacobi_ordering_table(0, 1)
+    with pytest.raises(ValueError):
+        jg.jacobi_ordering_table(7, 8)

@@ -1,0 +1,297 @@
+"""GPU parity of the two-sided blocked Jacobi EVD against the CPU oracle.
+
+Element-wise parity of single steps (Algorithm 2: pivot solves + block-row /
+block-column updates), then full solves compared on what is unique
+(eigenvalues; eigenvectors through residual and orthogonality, since they are
+not unique).  Tolerances: |lambda - lambda_oracle| <= 1e-13 ||A||_2,
+||AQ - QD||_F <= 1e-12 ||A||_F, ||Q^T Q - I||_F <= 1e-13 n.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def jg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_28952_gb300 as m
+    m.lib()
+    return m
+
+
+def _dev(x):
+    import paper_2608_28952_gb300 as m
+    import torch
+    return m.colmajor(x, device="cuda", dtype=torch.float64)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def check(A, w, Q, w_ref, eig=1e-13, res=1e-12, orth=1e-13):
+    n = A.shape[0]
+    nrm2 = max(np.abs(w_ref).max(), 1e-300)
+    assert np.abs(w - w_ref).max() <= eig * nrm2, np.abs(w - w_ref).max() / nrm2
+    if Q is not None:
+        r = np.linalg.norm(A @ Q - Q * w[None, :])
+        assert r <= res * max(np.linalg.norm(A), 1e-300), r / np.linalg.norm(A)
+        o = np.linalg.norm(Q.T @ Q - np.eye(n))
+        assert o <= orth * n, o / n
+
+
+# ------------------------------------------------------------------ single steps
+STEP_CASES = [
+    (64, 8, 0, [0, 3, 6]),
+    (96, 16, 0, [0, 4]),          # k = 32
+    (256, 64, 0, [0, 1]),         # k = 128, shared-memory pivot at its limit
+    (512, 128, 0, [0]),           # k = 256, pivot in global scratch
+    (40, 5, 0, [0, 2]),           # odd b, ragged tiles
+    (80, 8, 1, [0, 1, 5]),        # Algorithm 3 with frozen blocks
+    (4, 1, 0, [0, 2]),            # b = 1: 2 x 2 pivots
+]
+
+
+def _step_pair(jg, A0, b, ordering, s):
+    np_ = A0.shape[0]
+    tab = oracle.ordering(ordering, np_ // b)
+    A_or, Q_or, _ = oracle.syev_step(A0, np.eye(np_), b, tab[s])
+    Ad, Qd = _dev(A0), _dev(np.eye(np_))
+    assert jg.jacobi_syev_step(Ad, Qd, s, jg.params(b=b, ordering=ordering)) == 0
+    Ag, Qg = _np(Ad), _np(Qd)
+    assert np.array_equal(Ag, Ag.T)  # mirrored writes keep exact symmetry
+    return Ag, Qg, A_or, Q_or, tab[s]
+
+
+@pytest.mark.parametrize("np_,b,ordering,steps", STEP_CASES)
+def test_step_parity_well_separated(jg, np_, b, ordering, steps):
+    """Pivots with well separated eigenvalues (A = diag(1..2np) + 0.05 G):
+    the step is well conditioned, so GPU and oracle agree to rounding."""
+    d = np.linspace(1.0, 2.0 * np_, np_)
+    A0 = np.asfortranarray(np.diag(d) + 0.05 * gen.sym_gaussian(np_, 900 + np_ + b))
+    for s in steps:
+        Ag, Qg, A_or, Q_or, _ = _step_pair(jg, A0, b, ordering, s)
+        scale = np.abs(A0).max()
+        assert np.abs(Ag - A_or).max() <= 1e-13 * scale, np.abs(Ag - A_or).max() / scale
+        assert np.abs(Qg - Q_or).max() <= 1e-13, np.abs(Qg - Q_or).max()
+
+
+def pivot_vector_tol(A0, b, pairs):
+    """Bound on the difference of two correctly rounded eigenvector bases of
+    the step's pivots: 32 k u ||Ahat|| / gap, gap = the smallest eigenvalue
+    gap of a pivot (LAPACK on the pivot, independent of both sides)."""
+    cond = 1.0
+    for (I, J) in pairs:
+        idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+        ev = np.linalg.eigvalsh(A0[np.ix_(idx, idx)])
+        gap = max(np.diff(ev).min(), 1e-300) if len(ev) > 1 else 1.0
+        cond = max(cond, np.abs(ev).max() / gap)
+    return 32 * (2 * b) * U * cond
+
+
+@pytest.mark.parametrize("np_,b,ordering,steps", STEP_CASES)
+def test_step_parity_random(jg, np_, b, ordering, steps):
+    """Gaussian pivots: eigenvectors of a pivot with close eigenvalues are
+    determined only to u ||Ahat|| / gap, so the tolerance is that bound."""
+    A0 = gen.sym_gaussian(np_, 1000 + np_ + b)
+    for s in steps:
+        Ag, Qg, A_or, Q_or, pairs = _step_pair(jg, A0, b, ordering, s)
+        tol_v = pivot_vector_tol(A0, b, pairs)
+        nrm2 = np.linalg.norm(A0, 2)
+        assert np.abs(Qg - Q_or).max() <= max(1e-13, tol_v), (np.abs(Qg - Q_or).max(), tol_v)
+        assert np.abs(Ag - A_or).max() <= max(1e-13, 4 * tol_v) * nrm2
+
+
+def test_step_without_permutation(jg):
+    """pivot_order = 0 (eigenpairs as solved, the paper's pseudocode)."""
+    np_, b = 96, 16
+    d = np.linspace(1.0, 2.0 * np_, np_)
+    A0 = np.asfortranarray(np.diag(d) + 0.05 * gen.sym_gaussian(np_, 1900))
+    tab = oracle.ordering(0, np_ // b)
+    A_or, Q_or, _ = oracle.syev_step(A0, np.eye(np_), b, tab[2], pivot_order=0)
+    Ad, Qd = _dev(A0), _dev(np.eye(np_))
+    assert jg.jacobi_syev_step(Ad, Qd, 2, jg.params(b=b, pivot_order=0)) == 0
+    assert np.abs(_np(Ad) - A_or).max() <= 1e-13 * np.abs(A0).max()
+    assert np.abs(_np(Qd) - Q_or).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ full solves
+def test_config1_n256_b16(jg):
+    """n = 256, b = 16, lambda ~ U[-1,1], round-robin, off(A) <= 1e-14 ||A||_F."""
+    A, lam = gen.sym_known(256, "uniform", seed=gen.SEEDS["c1"])
+    w_or, Q_or, _, st_or, s_or = oracle.syev(A, b=16)
+    w, Q, D, st = jg.syev(A, b=16)
+    w, Q, D = _np(w), _np(Q), _np(D)
+    assert st.status == 0 and s_or == 0
+    check(A, w, Q, w_or)
+    assert np.abs(w - np.sort(lam)).max() <= 1e-13 * np.abs(lam).max()
+    assert abs(st.sweeps - st_or.sweeps) <= 1
+    assert st.off_final <= 1e-14 * st.norm_fro or st.stalled
+    # on exit (D, Q) is a consistent state: A = Q D Q^T, diag(D) = w
+    assert np.array_equal(np.diag(D), w)
+    assert np.abs(Q @ D @ Q.T - A).max() <= 1e-13 * np.abs(A).max() * 16
+
+
+@pytest.mark.parametrize("n,b,ordering", [
+    (200, 16, 0), (77, 8, 0), (130, 64, 0), (300, 128, 0), (50, 5, 0), (20, 1, 0),
+    (100, 8, 1), (99, 7, 1), (33, 64, 0),
+])
+def test_ragged_and_orderings(jg, n, b, ordering):
+    A = gen.sym_gaussian(n, 2000 + n)
+    w_or, _, _, _, s_or = oracle.syev(A, b=b, ordering=ordering)
+    w, Q, _, st = jg.syev(A, b=b, ordering=ordering)
+    assert st.status == 0 and s_or == 0
+    check(A, _np(w), _np(Q), w_or)
+
+
+def test_full_solve_without_permutation(jg):
+    A, lam = gen.sym_known(192, "uniform", seed=1950)
+    w_or, *_ , s_or = oracle.syev(A, b=16, pivot_order=0)
+    w, Q, _, st = jg.syev(A, b=16, pivot_order=0)
+    assert st.status == 0 and s_or == 0
+    check(A, _np(w), _np(Q), w_or)
+
+
+def test_graded_spectrum_absolute_and_relative(jg):
+    """lambda_i = +-10^(-12 i/(n-1)); gate absolute 1e-13 ||A||_2 everywhere and
+    relative 1e-12 for |lambda| >= 1e-3 ||A||_2 (the stored entries do not fix
+    smaller eigenvalues to relative accuracy)."""
+    A, lam = gen.sym_known(256, "graded", seed=gen.SEEDS["c2g"])
+    w_or, *_ = oracle.syev(A, b=16)
+    w, Q, _, st = jg.syev(A, b=16)
+    w, Q = _np(w), _np(Q)
+    check(A, w, Q, w_or)
+    big = np.abs(w_or) >= 1e-3 * np.abs(w_or).max()
+    assert (np.abs(w - w_or)[big] / np.abs(w_or[big])).max() <= 1e-12
+
+
+def test_graded_dhd_relative_criterion(jg):
+    """A = D H D, kappa(H) <= 10: with the relative stop criterion every
+    eigenvalue agrees with the oracle to 1e-12 relative."""
+    A, d, H = gen.graded_dhd(128, seed=gen.SEEDS["c2dhd"])
+    w_or, *_ = oracle.syev(A, b=16, conv=oracle.CONV_REL, tol=4 * U)
+    w, Q, _, st = jg.syev(A, b=16, conv=jg.CONV_REL, tol=4 * U)
+    w = _np(w)
+    assert st.status == 0
+    assert (np.abs(w - w_or) / np.abs(w_or)).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ edge cases
+def test_diagonal_input_no_rotation(jg):
+    d = np.linspace(-2, 3, 40)
+    w, Q, D, st = jg.syev(np.diag(d), b=8)
+    assert st.status == 0 and st.sweeps == 0 and st.rotations == 0
+    assert np.array_equal(_np(w), d) and np.array_equal(_np(Q), np.eye(40))
+
+
+def test_tiny_orders(jg):
+    for n in (1, 2, 3):
+        A = gen.sym_gaussian(n, 3000 + n)
+        w, Q, _, st = jg.syev(A, b=1)
+        check(A, _np(w), _np(Q), np.linalg.eigvalsh(A))
+    w, Q, _, st = jg.syev(np.array([[5.0]]), b=4)
+    assert _np(w)[0] == 5.0 and _np(Q)[0, 0] == 1.0
+
+
+def test_zero_and_identity(jg):
+    w, Q, _, st = jg.syev(np.zeros((24, 24)), b=4)
+    assert st.status == 0 and np.all(_np(w) == 0)
+    w, Q, _, st = jg.syev(np.eye(24) * 3.0, b=4)
+    assert np.all(_np(w) == 3.0) and np.array_equal(_np(Q), np.eye(24))
+
+
+def test_nonfinite_and_bad_arguments(jg):
+    import torch
+    A = gen.sym_gaussian(16, 3100)
+    A[5, 2] = np.nan
+    Ad = _dev(A)
+    w = torch.empty(16, dtype=torch.float64, device="cuda")
+    Q = jg.colmajor_empty(16, 16, torch.float64, "cuda")
+    rc, _ = jg.jacobi_syev(Ad, w, Q, jg.params(b=4))
+    assert rc == jg.ERR_NONFINITE
+    A[5, 2] = 0.0
+    A[2, 5] = np.inf  # upper triangle is not read
+    rc, _ = jg.jacobi_syev(_dev(A), w, Q, jg.params(b=4))
+    assert rc == 0
+    assert jg.jacobi_syev(_dev(A), w, Q, jg.params(b=0))[0] == -7
+    assert jg.jacobi_syev(_dev(A), w, Q, jg.params(b=129))[0] == jg.ERR_UNSUPPORTED
+    assert jg.jacobi_syev(_dev(A), w, Q, jg.params(ordering=5))[0] == -7
+
+
+def test_leading_dimension_and_no_vectors(jg):
+    import torch
+    n, ld = 50, 64
+    A = gen.sym_gaussian(n, 3200)
+    big = torch.zeros((n, ld), dtype=torch.float64, device="cuda").t()  # ld x n storage
+    Ad = big[:n, :]
+    Ad.copy_(torch.from_numpy(A))
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    rc, st = jg.jacobi_syev(Ad, w, None, jg.params(b=8, want_vectors=0))
+    assert rc == 0
+    check(A, _np(w), None, np.linalg.eigvalsh(A))
+    assert torch.all(big[n:, :] == 0)  # rows past n untouched
+
+
+def test_max_sweeps_reports_nonconvergence(jg):
+    A = gen.sym_gaussian(64, 3300)
+    w, Q, _, st = jg.syev(A, b=8, max_sweeps=1)
+    assert st.status == 1 and st.sweeps == 1
+
+
+def test_deterministic(jg):
+    A = gen.sym_gaussian(160, 3400)
+    w1, Q1, _, _ = jg.syev(A, b=16)
+    w2, Q2, _, _ = jg.syev(A, b=16)
+    assert np.array_equal(_np(w1), _np(w2)) and np.array_equal(_np(Q1), _np(Q2))
+
+
+def test_warm_start_resume(jg):
+    import torch
+    A, lam = gen.sym_known(128, "uniform", seed=3500)
+    w, Q, D, st = jg.syev(A, b=16, max_sweeps=2)
+    assert st.status == 2
+    w2 = torch.empty_like(w)
+    rc, st2 = jg.jacobi_syev(D, w2, Q, jg.params(b=16, warm_start=1))
+    assert rc == 0
+    check(A, _np(w2), _np(Q), np.sort(lam))
+
+
+def test_host_buffers_match_device(jg):
+    import torch
+    A = gen.sym_gaussian(96, 3600)
+    w, Q, _, _ = jg.syev(A, b=16)
+    Ah = jg.colmajor(A, dtype=torch.float64).pin_memory()
+    wh = torch.empty(96, dtype=torch.float64).pin_memory()
+    Qh = jg.colmajor_empty(96, 96, torch.float64, "cpu")
+    rc, st = jg.jacobi_syev_h(Ah, wh, Qh, jg.params(b=16))
+    assert rc == 0
+    assert np.array_equal(wh.numpy(), _np(w)) and np.array_equal(Qh.numpy(), _np(Q))
+
+
+# ------------------------------------------------------------------ full size (n = 4096, b = 64)
+def test_full_size_n4096_b64(jg):
+    """The benchmark workload: first step element-wise against the oracle at
+    full size, then the converged solve against the constructed spectrum and
+    the residual / orthogonality bounds."""
+    n, b = 4096, 64
+    A, lam = gen.sym_known(n, "uniform", seed=gen.SEEDS["c2u"])
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, n // b)
+    A_or, _, _ = oracle.syev_step(A, None, b, tab[0])
+    Ad = _dev(A)
+    assert jg.jacobi_syev_step(Ad, None, 0, jg.params(b=b)) == 0
+    tol_v = pivot_vector_tol(A, b, tab[0])
+    assert np.abs(_np(Ad) - A_or).max() <= max(1e-13, 4 * tol_v) * np.abs(lam).max()
+    del Ad
+    w, Q, _, st = jg.syev(A, b=b)
+    w, Q = _np(w), _np(Q)
+    assert st.status == 0
+    check(A, w, Q, np.sort(lam))

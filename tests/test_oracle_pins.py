@@ -164,19 +164,25 @@ def test_block_off2_identity_over_one_step():
     assert abs(_offsq(A2) - (_offsq(A) - drop)) <= 1e-12 * np.sum(A * A)
 
 
-def test_step_pivot_blocks_hold_dhat_and_match_explicit_product():
+@pytest.mark.parametrize("order", [0, 1])
+def test_step_pivot_blocks_hold_dhat_and_match_explicit_product(order):
     """The update formulas of Algorithm 2 applied to the pivot itself give
-    Vhat^T Ahat Vhat = Dhat, and the step writes Dhat there."""
+    Vhat^T Ahat Vhat = Dhat, and the step writes Dhat there; with pivot_order 1
+    the eigenpairs are first permuted (Qhat <- Qhat P) so diag(Dhat) descends."""
     n, b = 32, 4
     A = gen.sym_gaussian(n, 33)
     N = oracle.padded_blocks(n, b)
     step = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)[0]
-    A2, _, _ = oracle.syev_step(A, None, b, step)
+    A2, _, _ = oracle.syev_step(A, None, b, step, pivot_order=order)
     W = np.eye(n)
     for (I, J) in step:
         idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
         Ah = A[np.ix_(idx, idx)]
         D, V, rot, sw = oracle.pivot_solve(Ah)
+        if order == 1:
+            perm = np.argsort(-np.diag(D), kind="stable")
+            D, V = D[np.ix_(perm, perm)], V[:, perm]
+            assert np.all(np.diff(np.diag(A2[np.ix_(idx, idx)])) <= 0)
         assert np.abs(V.T @ Ah @ V - D).max() <= 1e-14 * np.abs(Ah).max() * 2 * b
         assert np.array_equal(A2[np.ix_(idx, idx)], D)
         W[np.ix_(idx, idx)] = V
@@ -307,6 +313,17 @@ def test_blocked_and_scalar_agree_and_sweep_history_decreases():
     assert all(h[i + 1] < h[i] for i in range(len(h) - 1))
 
 
+def test_pivot_order_sorting_keeps_the_answer_and_saves_sweeps():
+    """The permutation after each pivot solve changes the iterates, not the
+    eigenvalues; on a graded spectrum it shortens the iteration."""
+    A, lam = gen.sym_known(96, "graded", seed=63)
+    w0, Q0, _, st0, s0 = oracle.syev(A, b=8, pivot_order=0)
+    w1, Q1, _, st1, s1 = oracle.syev(A, b=8, pivot_order=1)
+    assert s0 == 0 and s1 == 0
+    assert np.abs(w0 - w1).max() <= 1e-13 * np.abs(lam).max()
+    assert st1.sweeps < st0.sweeps
+
+
 def test_max_sweeps_reports_nonconvergence():
     A = gen.sym_gaussian(40, 62)
     w, Q, Af, st, status = oracle.syev(A, b=4, max_sweeps=1)
@@ -316,13 +333,14 @@ def test_max_sweeps_reports_nonconvergence():
 # ------------------------------------------------------------------ padding
 def test_padding_is_exact():
     """b that does not divide n: zero rows/columns stay exactly zero, so the
-    ragged run equals the run on the explicitly zero-padded matrix."""
+    ragged run equals the run on the explicitly zero-padded matrix (without
+    the pivot permutation, which treats explicit zeros as real rows)."""
     n, b = 10, 4
     A = gen.sym_gaussian(n, 70)
     Ap = np.zeros((12, 12), order="F")
     Ap[:n, :n] = A
-    w, Q, Af, st, s1 = oracle.syev(A, b=b)
-    wp, Qp, Afp, stp, s2 = oracle.syev(Ap, b=b)
+    w, Q, Af, st, s1 = oracle.syev(A, b=b, pivot_order=0)
+    wp, Qp, Afp, stp, s2 = oracle.syev(Ap, b=b, pivot_order=0)
     assert st.rotations == stp.rotations and st.sweeps == stp.sweeps
     # the padded run has two extra exact zero eigenvalues; removing them gives w
     z = np.where(wp == 0.0)[0]
@@ -331,6 +349,10 @@ def test_padding_is_exact():
     keep[z[:2]] = False
     assert np.array_equal(wp[keep], w)
     assert np.all(Afp[n:, :] == 0.0) and np.all(Afp[:, n:] == 0.0)
+    # with the permutation the padding positions stay fixed: same eigenvalues
+    w1, Q1, *_ = oracle.syev(A, b=b, pivot_order=1)
+    assert np.abs(w1 - np.linalg.eigvalsh(A)).max() <= 1e-13 * np.abs(w1).max()
+    assert np.linalg.norm(A @ Q1 - Q1 * w1[None, :]) <= 1e-12 * np.linalg.norm(A)
 
 
 def test_padding_inside_a_step():
@@ -340,7 +362,7 @@ def test_padding_inside_a_step():
     tab = oracle.ordering(oracle.ORDER_ANTI_DIAGONAL, 3)
     Ak = A
     for step in tab:
-        Ak, _, _ = oracle.syev_step(Ak, None, b, step)
+        Ak, _, _ = oracle.syev_step(Ak, None, b, step, pivot_order=0)
         assert np.all(Ak[10:, :] == 0.0) and np.all(Ak[:, 10:] == 0.0)
 
 
