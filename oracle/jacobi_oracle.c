@@ -52,6 +52,22 @@
  *     criterion, max |a_ij|/sqrt|a_ii a_jj| <= tol), or when the measure is
  *     already <= 100*tol and did not halve over the last sweep (stall).
  *
+ * Applying a rotation: with tau = s/(1+c) the pair (x, y) becomes
+ * (x - s(y + tau x), y + s(x - tau y)), algebraically (c x - s y, s x + c y).
+ * This is Rutishauser's form of the update; its rounding error is relative to
+ * the correction s(...), so the rotated vectors keep their length even for
+ * the small angles of late sweeps, where the computed (c, s) satisfy
+ * c^2 + s^2 = 1 + u on average and the plain form would let every column
+ * grow by about one unit roundoff per rotation.
+ *
+ * Diagonal of a pivot during its solve: each entry is carried as an unevaluated
+ * sum hi + lo (hi is what the rotation tests read).  A rotation's diagonal
+ * change -/+ t a_pq is formed exactly (fma) and added with an error-free
+ * two-sum, and the output Dhat gets hi + lo rounded once.  In the last inner
+ * sweeps t a_pq is below half an ulp of a_pp while the zeroed a_pq is not
+ * negligible; without the lo part that energy is lost on every rotation, in
+ * the same direction, and the spectrum shrinks by O(n u) over a solve.
+ *
  * Numbers: everything is IEEE binary64, round-to-nearest, built with
  * -ffp-contract=off so that no fused multiply-add changes a rounding, which
  * makes x86-64 and AArch64 builds give identical bits.
@@ -180,6 +196,31 @@ void oracle_rotation(double app, double aqq, double apq, double *c, double *s, d
     *s = tt * cc;
 }
 
+/* (hi, lo) <- (hi, lo) + d * sgn for the diagonal update, with d = t * apq
+ * formed exactly as dh + dl (fma) and the sum by an error-free two-sum. */
+static void dd_add_prod(double *hi, double *lo, double t, double apq, double sgn)
+{
+    double dh = t * apq;
+    double dl = fma(t, apq, -dh);
+    dh *= sgn;
+    dl *= sgn;
+    double a = *hi, sum = a + dh;
+    double bb = sum - a;
+    double err = (a - (sum - bb)) + (dh - bb);
+    err += *lo + dl;
+    double h2 = sum + err;
+    *lo = err - (h2 - sum);
+    *hi = h2;
+}
+
+/* The pair (x, y) <- (c x - s y, s x + c y) in Rutishauser's form. */
+static void rot_apply(double s, double tau, double *x, double *y)
+{
+    double a = *x, b = *y;
+    *x = a - s * (b + tau * a);
+    *y = b + s * (a - tau * b);
+}
+
 static int rotation_wanted(double app, double aqq, double apq, double tol_rel)
 {
     if (apq == 0.0) return 0;
@@ -244,26 +285,17 @@ int oracle_rotate(int n, double *A, int lda, double *Q, int ldq, int p, int q)
     double app = AT(A, lda, p, p), aqq = AT(A, lda, q, q);
     double c, s, t;
     oracle_rotation(app, aqq, apq, &c, &s, &t);
-    for (int j = 0; j < n; j++) {          /* rows: A <- J^T A */
-        double x = AT(A, lda, p, j), y = AT(A, lda, q, j);
-        AT(A, lda, p, j) = c * x - s * y;
-        AT(A, lda, q, j) = s * x + c * y;
-    }
-    for (int i = 0; i < n; i++) {          /* columns: A <- A J */
-        double x = AT(A, lda, i, p), y = AT(A, lda, i, q);
-        AT(A, lda, i, p) = c * x - s * y;
-        AT(A, lda, i, q) = s * x + c * y;
-    }
+    double tau = s / (1.0 + c);
+    for (int j = 0; j < n; j++)            /* rows: A <- J^T A */
+        rot_apply(s, tau, &AT(A, lda, p, j), &AT(A, lda, q, j));
+    for (int i = 0; i < n; i++)            /* columns: A <- A J */
+        rot_apply(s, tau, &AT(A, lda, i, p), &AT(A, lda, i, q));
     AT(A, lda, p, p) = app - t * apq;
     AT(A, lda, q, q) = aqq + t * apq;
     AT(A, lda, p, q) = 0.0;
     AT(A, lda, q, p) = 0.0;
     if (Q)
-        for (int i = 0; i < n; i++) {
-            double x = AT(Q, ldq, i, p), y = AT(Q, ldq, i, q);
-            AT(Q, ldq, i, p) = c * x - s * y;
-            AT(Q, ldq, i, q) = s * x + c * y;
-        }
+        for (int i = 0; i < n; i++) rot_apply(s, tau, &AT(Q, ldq, i, p), &AT(Q, ldq, i, q));
     return 1;
 }
 
@@ -323,6 +355,8 @@ int oracle_pivot_solve(int k, double *Ah, double *V, double tol_rel, int max_swe
     int *tab = (int *)malloc(sizeof(int) * (size_t)(2 * half * (S > 0 ? S : 1)));
     double *cs = (double *)malloc(sizeof(double) * (size_t)(4 * half));
     int *on = (int *)malloc(sizeof(int) * (size_t)half);
+    double *dlo = (double *)calloc((size_t)k, sizeof(double)); /* low parts of the diagonal */
+    double *diag0 = (double *)malloc(sizeof(double) * (size_t)k); /* hi parts at round start */
     if (S > 0) rr_table(k, tab);
     for (int j = 0; j < k; j++)
         for (int i = 0; i < k; i++) AT(V, k, i, j) = (i == j) ? 1.0 : 0.0;
@@ -334,45 +368,42 @@ int oracle_pivot_solve(int k, double *Ah, double *V, double tol_rel, int max_swe
             for (int e = 0; e < half; e++) {
                 int p = pr[2 * e], q = pr[2 * e + 1];
                 double app = AT(Ah, k, p, p), aqq = AT(Ah, k, q, q), apq = AT(Ah, k, p, q);
+                diag0[p] = app;
+                diag0[q] = aqq;
                 on[e] = rotation_wanted(app, aqq, apq, tol_rel);
                 if (on[e]) {
                     double c, s, t;
                     oracle_rotation(app, aqq, apq, &c, &s, &t);
                     cs[4 * e + 0] = c;
                     cs[4 * e + 1] = s;
-                    cs[4 * e + 2] = app - t * apq;
-                    cs[4 * e + 3] = aqq + t * apq;
+                    cs[4 * e + 2] = t;
+                    cs[4 * e + 3] = apq;
                 }
             }
             for (int e = 0; e < half; e++) { /* rows */
                 if (!on[e]) continue;
                 int p = pr[2 * e], q = pr[2 * e + 1];
-                double c = cs[4 * e], s = cs[4 * e + 1];
-                for (int j = 0; j < k; j++) {
-                    double x = AT(Ah, k, p, j), y = AT(Ah, k, q, j);
-                    AT(Ah, k, p, j) = c * x - s * y;
-                    AT(Ah, k, q, j) = s * x + c * y;
-                }
+                double s = cs[4 * e + 1], tau = s / (1.0 + cs[4 * e]);
+                for (int j = 0; j < k; j++) rot_apply(s, tau, &AT(Ah, k, p, j), &AT(Ah, k, q, j));
             }
             for (int e = 0; e < half; e++) { /* columns of A and V */
                 if (!on[e]) continue;
                 int p = pr[2 * e], q = pr[2 * e + 1];
-                double c = cs[4 * e], s = cs[4 * e + 1];
+                double s = cs[4 * e + 1], tau = s / (1.0 + cs[4 * e]);
                 for (int i = 0; i < k; i++) {
-                    double x = AT(Ah, k, i, p), y = AT(Ah, k, i, q);
-                    AT(Ah, k, i, p) = c * x - s * y;
-                    AT(Ah, k, i, q) = s * x + c * y;
-                    x = AT(V, k, i, p);
-                    y = AT(V, k, i, q);
-                    AT(V, k, i, p) = c * x - s * y;
-                    AT(V, k, i, q) = s * x + c * y;
+                    rot_apply(s, tau, &AT(Ah, k, i, p), &AT(Ah, k, i, q));
+                    rot_apply(s, tau, &AT(V, k, i, p), &AT(V, k, i, q));
                 }
             }
             for (int e = 0; e < half; e++) { /* exact 2x2 diagonal form */
                 if (!on[e]) continue;
                 int p = pr[2 * e], q = pr[2 * e + 1];
-                AT(Ah, k, p, p) = cs[4 * e + 2];
-                AT(Ah, k, q, q) = cs[4 * e + 3];
+                double t = cs[4 * e + 2], apq = cs[4 * e + 3];
+                double hp = diag0[p], hq = diag0[q];
+                dd_add_prod(&hp, &dlo[p], t, apq, -1.0);
+                dd_add_prod(&hq, &dlo[q], t, apq, +1.0);
+                AT(Ah, k, p, p) = hp;
+                AT(Ah, k, q, q) = hq;
                 AT(Ah, k, p, q) = 0.0;
                 AT(Ah, k, q, p) = 0.0;
                 in_sweep++;
@@ -381,10 +412,13 @@ int oracle_pivot_solve(int k, double *Ah, double *V, double tol_rel, int max_swe
         total += in_sweep;
         if (in_sweep == 0) { sw++; break; }
     }
+    for (int i = 0; i < k; i++) AT(Ah, k, i, i) += dlo[i]; /* hi + lo, rounded once */
     if (sweeps_out) *sweeps_out = sw;
     free(tab);
     free(cs);
     free(on);
+    free(dlo);
+    free(diag0);
     return total;
 }
 
@@ -941,17 +975,11 @@ int oracle_gesvd_scalar(int m, int n, double *G, int ldg, double *sigma, double 
                 if (!rotation_wanted(al, be, ga, p->tol)) continue;
                 double c, sn, t;
                 oracle_rotation(al, be, ga, &c, &sn, &t);
-                for (int r = 0; r < m; r++) {
-                    double x = AT(Gw, m, r, pp), y = AT(Gw, m, r, q);
-                    AT(Gw, m, r, pp) = c * x - sn * y;
-                    AT(Gw, m, r, q) = sn * x + c * y;
-                }
+                double tau = sn / (1.0 + c);
+                for (int r = 0; r < m; r++) rot_apply(sn, tau, &AT(Gw, m, r, pp), &AT(Gw, m, r, q));
                 if (Vw)
-                    for (int r = 0; r < n; r++) {
-                        double x = AT(Vw, n, r, pp), y = AT(Vw, n, r, q);
-                        AT(Vw, n, r, pp) = c * x - sn * y;
-                        AT(Vw, n, r, q) = sn * x + c * y;
-                    }
+                    for (int r = 0; r < n; r++)
+                        rot_apply(sn, tau, &AT(Vw, n, r, pp), &AT(Vw, n, r, q));
                 in_sweep++;
             }
         s.rotations += in_sweep;
