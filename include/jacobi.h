@@ -111,6 +111,7 @@ typedef struct {
     long long pivot_launches;  /* of which pivot-solve kernels                 */
     long long update_launches; /* of which update kernels                      */
     double flops_fp64;       /* FP64 flops issued (updates + pivot solves)     */
+    double flops_update;     /* of which in the update / Gram kernels          */
     double flops_fp32;       /* FP32 flops issued                              */
     double flops_lowp;       /* bf16 / fp16 / tf32 tensor flops issued         */
 } jacobi_stats;
@@ -197,6 +198,64 @@ int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq, const jacob
  */
 int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, int ldv,
                       const jacobi_params* p, int step, double* relmax_out, void* stream);
+
+/* ------------------------------------------------------------ batched forms
+ * Thousands of independent matrices in one persistent launch (not in the
+ * paper, whose subject is one matrix on P processors; the per-matrix method is
+ * the same Jacobi iteration).  Each matrix is solved by one CTA with the
+ * scalar parallel-ordered Jacobi of the pivot solve (Algorithm 2 applied with
+ * b = 1, i.e. the blocked method with a single pair covering the matrix);
+ * the matrices are taken longest first from an atomic queue.  A matrix of
+ * order n (1 <= n <= 512) is solved in shared memory when it fits, else in a
+ * per-CTA slot of global scratch.  Stop: a sweep applies no rotation
+ * (relative threshold p->inner_tol; the default becomes 4 * 2^-24 for FP32),
+ * or p->max_sweeps.
+ *
+ * Pointer arguments named without h_ are HOST arrays of DEVICE pointers, one
+ * per matrix; h_* arrays are host arrays of sizes / leading dimensions (NULL
+ * = tight).  info: DEVICE array of batch ints: 0 converged, >0 sweeps run
+ * without converging, -100 non-finite input.  A is read only (lower
+ * triangle); w ascending; Q (or NULL when p->want_vectors == 0) eigenvectors.
+ */
+int jacobi_syev_batched(int batch, const int* h_n, double* const* A, const int* h_lda,
+                        double* const* w, double* const* Q, const int* h_ldq,
+                        const jacobi_params* p, int* info, jacobi_stats* st, void* stream);
+int jacobi_syev_batched_f32(int batch, const int* h_n, float* const* A, const int* h_lda,
+                            float* const* w, float* const* Q, const int* h_ldq,
+                            const jacobi_params* p, int* info, jacobi_stats* st, void* stream);
+
+/* Batched one-sided SVD (Algorithm 6 with a single column-block pair): each
+ * sweep forms the n x n Gram block of G (m x n, m >= n, n <= 64 for the
+ * shared-memory path on GB300), solves it with the FP32 Jacobi core, sorts its
+ * eigenpairs descending and rotates G's columns and V.  Stop: the Gram's
+ * largest normalised off-diagonal <= max(p->tol, sqrt(m) 2^-24), or a sweep
+ * without rotation.  G is overwritten by U; sigma descending. */
+int jacobi_gesvd_batched_f32(int batch, const int* h_m, const int* h_n, float* const* G,
+                             const int* h_ldg, float* const* sigma, float* const* V,
+                             const int* h_ldv, const jacobi_params* p, int* info,
+                             jacobi_stats* st, void* stream);
+
+/* Plan API: validation, longest-first order, workspace and the launch shape
+ * are set up once; the first execute captures [pointer upload, queue reset,
+ * persistent kernel] into a CUDA graph that later executes replay.
+ *   kind: 0 = symmetric EVD, 1 = one-sided SVD;  precision: JACOBI_PREC_FP64
+ *   or JACOBI_PREC_FP32 (kind 1: FP32 only).  h_m may be NULL for kind 0.
+ * jacobi_plan_autotune times each candidate launch shape (threads per CTA,
+ * largest order kept in shared memory) on a sample of the batch, keeps the
+ * fastest, and records it in an in-process cache keyed by kind, precision,
+ * vectors and the size mix (also written to the file named by the
+ * environment variable JACOBI_TUNE_CACHE, if set, and read back by later
+ * plans).  Plans are not thread-safe; one plan per stream. */
+typedef struct jacobi_plan jacobi_plan;
+int jacobi_plan_create_batched(jacobi_plan** out, int kind, int precision, int batch,
+                               const int* h_m, const int* h_n, const int* h_lda,
+                               const int* h_ldq, const jacobi_params* p, void* stream);
+int jacobi_plan_autotune(jacobi_plan* plan, void* const* A_or_G, void* const* w_or_sigma,
+                         void* const* Q_or_V, int* info, void* stream);
+int jacobi_plan_execute(jacobi_plan* plan, void* const* A_or_G, void* const* w_or_sigma,
+                        void* const* Q_or_V, int* info, jacobi_stats* st, void* stream);
+int jacobi_plan_shape(const jacobi_plan* plan, int* threads, int* smem_kmax, int* grid);
+void jacobi_plan_destroy(jacobi_plan* plan);
 
 /*
  * jacobi_ordering_table -- the library's pair schedule for N blocks

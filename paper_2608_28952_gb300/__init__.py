@@ -52,8 +52,8 @@ class jacobi_stats(C.Structure):
                 ("ms_pivot", C.c_double), ("ms_update", C.c_double),
                 ("launches", C.c_longlong), ("pivot_launches", C.c_longlong),
                 ("update_launches", C.c_longlong),
-                ("flops_fp64", C.c_double), ("flops_fp32", C.c_double),
-                ("flops_lowp", C.c_double)]
+                ("flops_fp64", C.c_double), ("flops_update", C.c_double),
+                ("flops_fp32", C.c_double), ("flops_lowp", C.c_double)]
 
 
 @dataclass
@@ -76,6 +76,7 @@ class Stats:
     pivot_launches: int
     update_launches: int
     flops_fp64: float
+    flops_update: float
     flops_fp32: float
     flops_lowp: float
     off_hist: list = field(default_factory=list)
@@ -85,7 +86,7 @@ def _stats(s: jacobi_stats) -> Stats:
     return Stats(s.status, s.sweeps, s.sweeps_lowp, s.stalled, s.steps, s.pair_solves,
                  s.rotations, s.inner_sweeps, s.norm_fro, s.off_initial, s.off_final,
                  s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
-                 s.update_launches, s.flops_fp64, s.flops_fp32, s.flops_lowp,
+                 s.update_launches, s.flops_fp64, s.flops_update, s.flops_fp32, s.flops_lowp,
                  list(s.off_hist)[: max(0, min(64, s.sweeps))])
 
 
@@ -103,6 +104,14 @@ SIGNATURES = {
     "jacobi_ordering_table": (_I, [_I, _I, _P, _P]),
     "jacobi_syev_step": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_gesvd_step": (_I, [_I, _I, _P, _I, _P, _I, _PP, _I, C.POINTER(C.c_double), _P]),
+    "jacobi_syev_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _PP, _P, _SP, _P]),
+    "jacobi_syev_batched_f32": (_I, [_I, _P, _P, _P, _P, _P, _P, _PP, _P, _SP, _P]),
+    "jacobi_gesvd_batched_f32": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _PP, _P, _SP, _P]),
+    "jacobi_plan_create_batched": (_I, [C.POINTER(_P), _I, _I, _I, _P, _P, _P, _P, _PP, _P]),
+    "jacobi_plan_autotune": (_I, [_P, _P, _P, _P, _P, _P]),
+    "jacobi_plan_execute": (_I, [_P, _P, _P, _P, _P, _SP, _P]),
+    "jacobi_plan_shape": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "jacobi_plan_destroy": (None, [_P]),
 }
 
 _LIB = None
@@ -286,3 +295,89 @@ def gesvd(G, b: int = 32, *, want_vectors: bool = True, stream=None, **kw):
     if rc < 0:
         raise RuntimeError(f"jacobi_gesvd: {rc} ({status_string(rc)})")
     return Gd, s, V, st
+
+
+# ------------------------------------------------------------------ batched forms
+def _ptr_array(tensors):
+    """Host array of device pointers (None -> NULL array)."""
+    if tensors is None:
+        return None
+    arr = (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+    return arr
+
+
+def _int_array(vals):
+    return (C.c_int * len(vals))(*[int(v) for v in vals])
+
+
+class Plan:
+    """Batched plan (jacobi_plan_*): kind 0 EVD, 1 one-sided SVD."""
+
+    def __init__(self, kind, precision, n, m=None, lda=None, ldq=None, p=None, stream=None):
+        self.kind, self.batch = kind, len(n)
+        self._h = C.c_void_p()
+        self._keep = [_int_array(n), _int_array(m) if m is not None else None,
+                      _int_array(lda) if lda is not None else None,
+                      _int_array(ldq) if ldq is not None else None]
+        rc = lib().jacobi_plan_create_batched(C.byref(self._h), kind, precision, len(n),
+                                              self._keep[1], self._keep[0], self._keep[2],
+                                              self._keep[3], C.byref(p) if p is not None else None,
+                                              _stream_ptr(stream))
+        if rc != 0:
+            raise RuntimeError(f"jacobi_plan_create_batched: {rc} ({status_string(rc)})")
+
+    def autotune(self, X, y, Z, info, stream=None):
+        rc = lib().jacobi_plan_autotune(self._h, _ptr_array(X), _ptr_array(y), _ptr_array(Z),
+                                        C.c_void_p(info.data_ptr()), _stream_ptr(stream))
+        if rc != 0:
+            raise RuntimeError(f"jacobi_plan_autotune: {rc}")
+
+    def execute(self, X, y, Z, info, stream=None):
+        st = jacobi_stats()
+        rc = lib().jacobi_plan_execute(self._h, _ptr_array(X), _ptr_array(y), _ptr_array(Z),
+                                       C.c_void_p(info.data_ptr()), C.byref(st),
+                                       _stream_ptr(stream))
+        return rc, _stats(st)
+
+    def shape(self):
+        t, k, g = C.c_int(), C.c_int(), C.c_int()
+        lib().jacobi_plan_shape(self._h, C.byref(t), C.byref(k), C.byref(g))
+        return t.value, k.value, g.value
+
+    def close(self):
+        if self._h:
+            lib().jacobi_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jacobi_syev_batched(As, ws, Qs, info, p=None, stream=None, f32=False):
+    """C ``jacobi_syev_batched`` / ``_f32`` on lists of column-major CUDA tensors."""
+    n = [a.shape[0] for a in As]
+    st = jacobi_stats()
+    f = lib().jacobi_syev_batched_f32 if f32 else lib().jacobi_syev_batched
+    rc = f(len(As), _int_array(n), _ptr_array(As), _int_array([_colmajor_ld(a) for a in As]),
+           _ptr_array(ws), _ptr_array(Qs),
+           _int_array([_colmajor_ld(q) for q in Qs]) if Qs is not None else None,
+           C.byref(p) if p is not None else None, C.c_void_p(info.data_ptr()), C.byref(st),
+           _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_gesvd_batched_f32(Gs, sigmas, Vs, info, p=None, stream=None):
+    """C ``jacobi_gesvd_batched_f32`` on lists of column-major CUDA tensors."""
+    m = [g.shape[0] for g in Gs]
+    n = [g.shape[1] for g in Gs]
+    st = jacobi_stats()
+    rc = lib().jacobi_gesvd_batched_f32(
+        len(Gs), _int_array(m), _int_array(n), _ptr_array(Gs),
+        _int_array([_colmajor_ld(g) for g in Gs]), _ptr_array(sigmas), _ptr_array(Vs),
+        _int_array([_colmajor_ld(v) for v in Vs]) if Vs is not None else None,
+        C.byref(p) if p is not None else None, C.c_void_p(info.data_ptr()), C.byref(st),
+        _stream_ptr(stream))
+    return rc, _stats(st)

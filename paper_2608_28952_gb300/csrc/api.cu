@@ -149,6 +149,7 @@ void fill_counters(jacobi_stats* st, const DevCounters& c)
     st->inner_sweeps = (long long)c.inner_sweeps;
     st->pair_solves = (long long)c.pair_solves;
     st->flops_fp64 = (double)c.flops_fp64;
+    st->flops_update = (double)c.flops_update;
     st->flops_fp32 = (double)c.flops_fp32;
     st->flops_lowp = (double)c.flops_lowp;
 }
@@ -237,7 +238,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     pa.cnt = E.cnt;
     cudaError_t e = launch_pivot(pa, cs);
     if (e != cudaSuccess) return e;
-    if (mid && (e = cudaEventRecord(mid, cs)) != cudaSuccess) return e;
+    if (mid && (e = cudaEventRecordWithFlags(mid, cs, cudaEventRecordExternal)) != cudaSuccess) return e;
     UpdateArgs ua{};
     ua.Ain = E.Aw[cur];
     ua.Aout = E.Aw[cur ^ 1];
@@ -275,12 +276,12 @@ SweepResult run_evd_sweeps(EvdState& E, const jacobi_params& p, int& cur, double
         const int start = cur;
         auto body = [&](cudaStream_t cs) -> bool {
             int c = start;
-            if (cudaEventRecord(pe.ev[0], cs) != cudaSuccess) return false;
+            if (cudaEventRecordWithFlags(pe.ev[0], cs, cudaEventRecordExternal) != cudaSuccess) return false;
             for (int si = 0; si < E.ord.S; ++si) {
                 if (launch_step(E, si, c, cs, p.inner_tol, p.inner_max_sweeps, p.pivot_order,
                                 pe.ev[2 * si + 1]) != cudaSuccess)
                     return false;
-                if (cudaEventRecord(pe.ev[2 * si + 2], cs) != cudaSuccess) return false;
+                if (cudaEventRecordWithFlags(pe.ev[2 * si + 2], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                 c ^= 1;
             }
             return launch_offnorm(E.np, E.Aw[c], E.partial, E.ticket, E.result, use_rel, cs) ==
@@ -480,12 +481,12 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
             const int start = cur;
             auto body = [&](cudaStream_t cs) -> bool {
                 if (cudaMemsetAsync(sweepmax, 0, sizeof(double), cs) != cudaSuccess) return false;
-                if (cudaEventRecord(pe.ev[0], cs) != cudaSuccess) return false;
+                if (cudaEventRecordWithFlags(pe.ev[0], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                 int c = start;
                 for (int si = 0; si < ord.S; ++si) {
                     const int nps = ord.dev_per_step, p0 = si * nps;
                     if (launch_gram(Gw[c], m, m, dpairs + p0, nps, b, k, part, cnt, cs) != cudaSuccess) return false;
-                    if (cudaEventRecord(pe.ev[3 * si + 1], cs) != cudaSuccess) return false;
+                    if (cudaEventRecordWithFlags(pe.ev[3 * si + 1], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     PivotArgs pa{};
                     pa.ld = np;
                     pa.gram = part;
@@ -505,7 +506,7 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                     pa.cnt = cnt;
                     if (launch_pivot(pa, cs) != cudaSuccess) return false;
                     if (launch_max_into(relmax, nps, sweepmax, cs) != cudaSuccess) return false;
-                    if (cudaEventRecord(pe.ev[3 * si + 2], cs) != cudaSuccess) return false;
+                    if (cudaEventRecordWithFlags(pe.ev[3 * si + 2], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     ColUpdateArgs ca{};
                     ca.Gin = Gw[c];
                     ca.Gout = Gw[c ^ 1];
@@ -523,7 +524,7 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                     ca.rot = rot;
                     ca.cnt = cnt;
                     if (launch_update_cols(ca, cs) != cudaSuccess) return false;
-                    if (cudaEventRecord(pe.ev[3 * si + 3], cs) != cudaSuccess) return false;
+                    if (cudaEventRecordWithFlags(pe.ev[3 * si + 3], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     c ^= 1;
                 }
                 return true;

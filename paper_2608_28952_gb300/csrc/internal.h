@@ -34,6 +34,7 @@ struct DevCounters {
     unsigned long long inner_sweeps;
     unsigned long long pair_solves;
     unsigned long long flops_fp64;   // issued update + pivot flops
+    unsigned long long flops_update; // of which in the update (and Gram) kernels
     unsigned long long flops_fp32;
     unsigned long long flops_lowp;
     int nonfinite;                   // input scan flag

@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "jacobi_core.cuh"
 
 namespace jac {
 
@@ -44,39 +45,6 @@ __device__ __forceinline__ bool entry(const int2* pairs, int e, int& I, int& J)
     I = frozen ? -1 - pr.x : pr.x;
     J = frozen ? -1 - pr.y : pr.y;
     return frozen;
-}
-
-// Packed lower-triangular index of symmetric entry (i, j).
-__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
-__device__ __forceinline__ int sidx(int i, int j) { return i >= j ? tri(i) + j : tri(j) + i; }
-
-// The textbook 2x2 symmetric Schur rotation: zeta = (aqq - app)/(2 apq),
-// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)) with sgn(0) = +1, c = 1/sqrt(1+t^2),
-// s = t c; J = [[c, s], [-s, c]] makes J^T [[app, apq], [apq, aqq]] J diagonal
-// with diagonal (app - t apq, aqq + t apq).  Every operation is rounded
-// separately (no contraction) so that the decision and the angle are the
-// correctly rounded values of these formulas.
-__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& c, double& s,
-                                       double& dp, double& dq)
-{
-    double zeta = __ddiv_rn(__dsub_rn(aqq, app), __dmul_rn(2.0, apq));
-    double t;
-    if (fabs(zeta) > 1e150) {
-        t = __ddiv_rn(0.5, zeta);
-    } else {
-        double r = __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(zeta, zeta)));
-        t = __ddiv_rn(zeta >= 0.0 ? 1.0 : -1.0, __dadd_rn(fabs(zeta), r));
-    }
-    c = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(t, t))));
-    s = __dmul_rn(t, c);
-    dp = __dsub_rn(app, __dmul_rn(t, apq));
-    dq = __dadd_rn(aqq, __dmul_rn(t, apq));
-}
-
-__device__ __forceinline__ bool rotation_wanted(double app, double aqq, double apq, double tol)
-{
-    if (apq == 0.0) return false;
-    return fabs(apq) > __dmul_rn(__dmul_rn(tol, __dsqrt_rn(fabs(app))), __dsqrt_rn(fabs(aqq)));
 }
 
 // ======================================================================== load
@@ -233,8 +201,8 @@ size_t pivot_gscratch_doubles(int k) { return k <= 128 ? 0 : tri_pad(k) + (size_
 static size_t pivot_smem_bytes(int k)
 {
     const int half = k / 2, nq = half * (half - 1) / 2;
-    size_t small = (size_t)4 * half * sizeof(double) + (size_t)3 * half * sizeof(int) +
-                   (size_t)nq * sizeof(unsigned) + 64;
+    size_t small = (size_t)4 * half * sizeof(double) + (size_t)k * sizeof(double) +
+                   (size_t)3 * half * sizeof(int) + (size_t)nq * sizeof(unsigned) + 64;
     if (k <= 128) small += (tri_pad(k) + (size_t)k * k) * sizeof(double);
     return small;
 }
@@ -259,15 +227,18 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
         V = Ap + ntp;
         tail = smem;
     }
-    double* rc = tail;
-    double* rs = rc + half;
-    double* rdp = rs + half;
-    double* rdq = rdp + half;
-    int* rp = (int*)(rdq + half);
-    int* rq = rp + half;
-    int* ron = rq + half;
-    unsigned* quad = (unsigned*)(ron + half);
+    CoreSmem<double> cs;
+    cs.tau = tail;
+    cs.s = cs.tau + half;
+    cs.t = cs.s + half;
+    cs.apq = cs.t + half;
+    cs.dlo = cs.apq + half;
+    cs.p = (int*)(cs.dlo + k);
+    cs.q = cs.p + half;
+    cs.on = cs.q + half;
+    unsigned* quad = (unsigned*)(cs.on + half);
     __shared__ int s_cnt;
+    cs.cnt = &s_cnt;
     __shared__ double s_red[PIV_T / 32];
     __shared__ int s_dest[256];   // output slot of each eigenpair (k <= 256)
     __shared__ int s_pos[256];    // the pivot's non-padding positions, ascending
@@ -291,8 +262,8 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
         }
     }
     for (int idx = tid; idx < k * k; idx += PIV_T) V[idx] = (idx % k == idx / k) ? 1.0 : 0.0;
-    for (int e2 = 1 + tid; e2 < half; e2 += PIV_T)
-        for (int e1 = 0; e1 < e2; ++e1) quad[(e2 * (e2 - 1) >> 1) + e1] = (unsigned)e1 | ((unsigned)e2 << 16);
+    for (int x = tid; x < k; x += PIV_T) cs.dlo[x] = 0.0;
+    build_quad_table(quad, half);
     __syncthreads();
 
     // ---- one-sided stop statistic: max_{i != j} |a_ij| / sqrt(a_ii a_jj) before rotating
@@ -316,82 +287,9 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
     }
 
     // ---- inner sweeps: round-robin over the k indices, k-1 rounds of k/2 rotations
-    const double tol = a.tol_rel;
-    int total_rot = 0, sweeps = 0;
-    const int max_sweeps = frozen ? 0 : a.max_sweeps;
-    for (int sw = 0; sw < max_sweeps; ++sw) {
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
-        for (int r = 0; r < k - 1; ++r) {
-            for (int ee = tid; ee < half; ee += PIV_T) {
-                const int pa = ee, pb = k - 1 - ee;
-                const int ia = pa == 0 ? 0 : 1 + (pa - 1 + r) % (k - 1);
-                const int ib = 1 + (pb - 1 + r) % (k - 1);
-                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
-                const double app = Ap[tri(p) + p], aqq = Ap[tri(q) + q], apq = Ap[tri(q) + p];
-                const bool on = rotation_wanted(app, aqq, apq, tol);
-                rp[ee] = p;
-                rq[ee] = q;
-                ron[ee] = on;
-                if (on) {
-                    double c, s, dp, dq;
-                    schur2(app, aqq, apq, c, s, dp, dq);
-                    rc[ee] = c;
-                    rs[ee] = s;
-                    rdp[ee] = dp;
-                    rdq[ee] = dq;
-                    atomicAdd(&s_cnt, 1);
-                }
-            }
-            __syncthreads();
-            // both-sided rotation of every 2x2 quad (rows of pair e1, columns of pair e2)
-            for (int qi = tid; qi < nq; qi += PIV_T) {
-                const unsigned qq = quad[qi];
-                const int e1 = qq & 0xffff, e2 = qq >> 16;
-                const int on1 = ron[e1], on2 = ron[e2];
-                if (!(on1 | on2)) continue;
-                const int p1 = rp[e1], q1 = rq[e1], p2 = rp[e2], q2 = rq[e2];
-                const int i00 = sidx(p1, p2), i01 = sidx(p1, q2), i10 = sidx(q1, p2),
-                          i11 = sidx(q1, q2);
-                double x00 = Ap[i00], x01 = Ap[i01], x10 = Ap[i10], x11 = Ap[i11];
-                if (on1) {  // rows: J1^T X
-                    const double c = rc[e1], s = rs[e1];
-                    double y00 = c * x00 - s * x10, y10 = s * x00 + c * x10;
-                    double y01 = c * x01 - s * x11, y11 = s * x01 + c * x11;
-                    x00 = y00; x10 = y10; x01 = y01; x11 = y11;
-                }
-                if (on2) {  // columns: X J2
-                    const double c = rc[e2], s = rs[e2];
-                    double y00 = c * x00 - s * x01, y01 = s * x00 + c * x01;
-                    double y10 = c * x10 - s * x11, y11 = s * x10 + c * x11;
-                    x00 = y00; x01 = y01; x10 = y10; x11 = y11;
-                }
-                Ap[i00] = x00; Ap[i01] = x01; Ap[i10] = x10; Ap[i11] = x11;
-            }
-            for (int ee = tid; ee < half; ee += PIV_T) {
-                if (!ron[ee]) continue;
-                const int p = rp[ee], q = rq[ee];
-                Ap[tri(p) + p] = rdp[ee];
-                Ap[tri(q) + q] = rdq[ee];
-                Ap[tri(q) + p] = 0.0;
-            }
-            for (int it = tid; it < half * k; it += PIV_T) {  // V <- V J
-                const int ee = it / k, row = it - ee * k;
-                if (!ron[ee]) continue;
-                const int p = rp[ee], q = rq[ee];
-                const double c = rc[ee], s = rs[ee];
-                const double vp = V[row + (size_t)p * k], vq = V[row + (size_t)q * k];
-                V[row + (size_t)p * k] = c * vp - s * vq;
-                V[row + (size_t)q * k] = s * vp + c * vq;
-            }
-            __syncthreads();
-        }
-        const int cnt = s_cnt;
-        total_rot += cnt;
-        sweeps = sw + 1;
-        __syncthreads();
-        if (cnt == 0) break;
-    }
+    int sweeps = 0;
+    const int total_rot =
+        jacobi_solve<double>(Ap, V, k, a.tol_rel, frozen ? 0 : a.max_sweeps, quad, cs, &sweeps);
 
     // ---- permutation Vhat <- Vhat P: eigenpair at position x moves to
     // s_dest[x]; with order == 1 the non-padding positions receive their
@@ -625,9 +523,12 @@ __global__ void __launch_bounds__(UPD_T, 2) k_update_evd(UpdateArgs a, int n_san
                 }
             }
         }
-        if (tid == 0)
-            atomicAdd(&a.cnt->flops_fp64, (unsigned long long)(r1 ? 2ull * k * k * kw : 0) +
-                                              (unsigned long long)(r2 ? 2ull * k * k * kw : 0));
+        if (tid == 0) {
+            const unsigned long long f = (unsigned long long)(r1 ? 2ull * k * k * kw : 0) +
+                                         (unsigned long long)(r2 ? 2ull * k * k * kw : 0);
+            atomicAdd(&a.cnt->flops_fp64, f);
+            atomicAdd(&a.cnt->flops_update, f);
+        }
     } else {
         // ---------------- Q'(rows, P chunk) = Q(rows, P) V_P(:, chunk)
         const int H = 32 * MR;
@@ -658,7 +559,10 @@ __global__ void __launch_bounds__(UPD_T, 2) k_update_evd(UpdateArgs a, int n_san
                     if (i < mr && m < M && jj < kw)
                         a.Qout[(r0 + m) + (size_t)ldq * pair_map(I, J, b, c0 + jj)] = t.acc[i][j];
                 }
-            if (tid == 0) atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+            if (tid == 0) {
+                atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+                atomicAdd(&a.cnt->flops_update, 2ull * M * k * kw);
+            }
         } else {
             for (int idx = tid; idx < M * kw; idx += UPD_T) {
                 const int j = idx / M, m = idx - j * M;
@@ -737,7 +641,10 @@ __global__ void __launch_bounds__(UPD_T, 2) k_update_cols(ColUpdateArgs a, int n
                 if (i < mr && m < M && jj < kw)
                     Mout[(r0 + m) + (size_t)ld * pair_map(I, J, b, c0 + jj)] = t.acc[i][j];
             }
-        if (tid == 0) atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+        if (tid == 0) {
+            atomicAdd(&a.cnt->flops_fp64, 2ull * M * k * kw);
+            atomicAdd(&a.cnt->flops_update, 2ull * M * k * kw);
+        }
     } else {
         for (int idx = tid; idx < M * kw; idx += UPD_T) {
             const int j = idx / M, m = idx - j * M;
@@ -810,7 +717,10 @@ __global__ void __launch_bounds__(UPD_T, 2) k_gram(const double* __restrict__ G,
             const int mm = ty + 32 * i, jj = tx + 8 * j;
             if (i < mr && mm < M && jj < kw) out[(row0 + mm) + (size_t)k * (c0 + jj)] = t.acc[i][j];
         }
-    if (tid == 0) atomicAdd(&cnt->flops_fp64, 2ull * M * K * kw);
+    if (tid == 0) {
+        atomicAdd(&cnt->flops_fp64, 2ull * M * K * kw);
+        atomicAdd(&cnt->flops_update, 2ull * M * K * kw);
+    }
 }
 
 cudaError_t launch_gram(const double* G, int ldg, int m, const int2* pairs, int npairs, int b,

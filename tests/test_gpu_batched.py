@@ -1,0 +1,142 @@
+"""GPU parity of the batched forms against the CPU oracle.
+
+Each matrix of a batch is solved by the scalar parallel-ordered Jacobi of the
+pivot solve (Algorithm 2 applied with b = 1 to the whole matrix); the oracle
+for one matrix is therefore ``oracle.pivot_solve`` on it (zero-padded to an
+even order: the padding row is never rotated and keeps the eigenvalue 0 at its
+position).  FP64 batches are gated like the single-matrix path; FP32 batches
+against the FP64 oracle with the FP64 bounds scaled by u32/u64 = 2^29
+(eigenvalues 5.4e-5 ||A||_2, residual 5.4e-4 ||A||_F, orthogonality 5.4e-5 n).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+SCALE32 = 2.0 ** 29
+
+
+@pytest.fixture(scope="module")
+def jg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_28952_gb300 as m
+    m.lib()
+    return m
+
+
+def oracle_eig(A):
+    n = A.shape[0]
+    k = n + (n & 1)
+    Ap = np.zeros((k, k))
+    Ap[:n, :n] = A
+    D, V, rot, sw = oracle.pivot_solve(Ap)
+    return np.sort(np.diag(D)[:n])
+
+
+def _mk(jg, mats, dtype):
+    import torch
+    As = [jg.colmajor(a, device="cuda", dtype=dtype) for a in mats]
+    ws = [torch.empty(a.shape[0], dtype=dtype, device="cuda") for a in mats]
+    Qs = [jg.colmajor_empty(a.shape[0], a.shape[0], dtype, "cuda") for a in mats]
+    info = torch.full((len(mats),), -7, dtype=torch.int32, device="cuda")
+    return As, ws, Qs, info
+
+
+SIZES = [1, 2, 3, 8, 17, 31, 64, 65, 100, 127, 128, 129, 130, 190, 255, 300, 384, 511, 512]
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_batched_evd_against_oracle(jg, f32):
+    import torch
+    r = np.random.default_rng(5)
+    sizes = SIZES + list(r.integers(1, 200, 20))
+    mats = [gen.sym_gaussian(int(n), 7, i) for i, n in enumerate(sizes)]
+    dtype = torch.float32 if f32 else torch.float64
+    As, ws, Qs, info = _mk(jg, mats, dtype)
+    rc, st = jg.jacobi_syev_batched(As, ws, Qs, info, jg.params(), f32=f32)
+    assert rc == 0
+    assert torch.all(info == 0), info
+    sc = SCALE32 if f32 else 1.0
+    for A, w, Q in zip(mats, ws, Qs):
+        n = A.shape[0]
+        w = w.double().cpu().numpy()
+        Q = Q.double().cpu().numpy()
+        w_or = oracle_eig(A)
+        nrm2 = max(np.abs(w_or).max(), 1e-300)
+        assert np.abs(w - w_or).max() <= 1e-13 * sc * nrm2, (n, np.abs(w - w_or).max() / nrm2)
+        assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * sc * np.linalg.norm(A)
+        assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * sc * n
+        assert np.all(np.diff(w) >= 0)
+
+
+def test_batched_evd_no_vectors_and_nonfinite(jg):
+    import torch
+    mats = [gen.sym_gaussian(n, 71, n) for n in (40, 90, 200)]
+    mats[1][3, 2] = np.nan
+    As, ws, _, info = _mk(jg, mats, torch.float64)
+    rc, st = jg.jacobi_syev_batched(As, ws, None, info, jg.params(want_vectors=0))
+    assert rc == 0
+    assert info.cpu().tolist() == [0, -100, 0]
+    for i in (0, 2):
+        assert np.abs(ws[i].cpu().numpy() - oracle_eig(mats[i])).max() <= 1e-13 * 30
+
+
+def test_batched_evd_deterministic_and_matches_single_pivot_path(jg):
+    import torch
+    mats = [gen.sym_gaussian(n, 72, n) for n in (64, 128, 200)]
+    As, ws, Qs, info = _mk(jg, mats, torch.float64)
+    jg.jacobi_syev_batched(As, ws, Qs, info, jg.params())
+    w1 = [w.clone() for w in ws]
+    jg.jacobi_syev_batched(As, ws, Qs, info, jg.params())
+    assert all(torch.equal(a, b) for a, b in zip(w1, ws))
+
+
+def test_plan_autotune_and_replay(jg):
+    import torch
+    r = np.random.default_rng(6)
+    sizes = [int(x) for x in r.integers(8, 257, 300)]
+    mats = [gen.sym_gaussian(n, 73, i) for i, n in enumerate(sizes)]
+    As, ws, Qs, info = _mk(jg, mats, torch.float32)
+    plan = jg.Plan(0, jg.PREC_FP32, sizes, p=jg.params())
+    plan.autotune(As, ws, Qs, info)
+    th, smk, grid = plan.shape()
+    assert th in (128, 256, 512) and grid >= 152
+    rc, st = plan.execute(As, ws, Qs, info)
+    assert rc == 0 and torch.all(info == 0)
+    w1 = [w.clone() for w in ws]
+    rc, st2 = plan.execute(As, ws, Qs, info)   # graph replay
+    assert rc == 0 and all(torch.equal(a, b) for a, b in zip(w1, ws))
+    for i in (0, 17, 299):
+        w_or = oracle_eig(mats[i])
+        assert np.abs(ws[i].double().cpu().numpy() - w_or).max() <= 1e-13 * SCALE32 * np.abs(w_or).max()
+    plan.close()
+
+
+def test_batched_tall_svd_f32(jg):
+    import torch
+    shapes = [(1024, 64)] * 12 + [(300, 40), (100, 100), (64, 1), (77, 33), (2, 2)]
+    mats = [gen.tall_gaussian(m, n, 74, i, dtype=np.float64) for i, (m, n) in enumerate(shapes)]
+    mats[13] = gen.svd_known(100, 100, seed=75, decades=3.0)[0]
+    Gs = [jg.colmajor(g, device="cuda", dtype=torch.float32) for g in mats]
+    ss = [torch.empty(g.shape[1], dtype=torch.float32, device="cuda") for g in mats]
+    Vs = [jg.colmajor_empty(g.shape[1], g.shape[1], torch.float32, "cuda") for g in mats]
+    info = torch.full((len(mats),), -7, dtype=torch.int32, device="cuda")
+    rc, st = jg.jacobi_gesvd_batched_f32(Gs, ss, Vs, info, jg.params())
+    assert rc == 0 and torch.all(info == 0), info
+    for G, U, s, V in zip(mats, Gs, ss, Vs):
+        n = G.shape[1]
+        U = U.double().cpu().numpy()
+        s = s.double().cpu().numpy()
+        V = V.double().cpu().numpy()
+        _, s_or, _, _, rc_or = oracle.gesvd(G, b=max(1, n // 2) if n > 1 else 1)
+        assert np.abs(s - s_or).max() <= 1e-13 * SCALE32 * s_or[0]
+        assert np.all(np.diff(s) <= 0)
+        assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * SCALE32 * n
+        assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-13 * SCALE32 * n
+        assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-12 * SCALE32 * np.linalg.norm(G)
