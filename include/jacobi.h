@@ -258,6 +258,27 @@ int jacobi_plan_shape(const jacobi_plan* plan, int* threads, int* smem_kmax, int
 void jacobi_plan_destroy(jacobi_plan* plan);
 
 /*
+ * jacobi_syev_step_noalloc -- jacobi_syev_step without any allocation.  The
+ * paper has no counterpart: it exists for callers that cannot allocate, such
+ * as code inside a framework that owns all device memory through its own pool
+ * (a cudaMalloc from outside the pool fails or fragments it) and
+ * latency-critical loops that cannot take an allocation's implicit
+ * synchronisation.  Same arguments, semantics and results as
+ * jacobi_syev_step; every buffer besides A and Q lives in a fixed array in
+ * device global memory, so the call makes no cudaMalloc / cudaFree and no host
+ * heap allocation.
+ *   Limits: np <= 768 and 1 <= p->b <= 128, else JACOBI_ERR_UNSUPPORTED.  The
+ *   array (about 24 MB) stays resident on every GPU the process uses until
+ *   the process exits.
+ *   The first call on a device looks up the array's address on that device;
+ *   make that first call before any stream capture.
+ *   All calls share the array: calls whose work overlaps on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller.
+ */
+int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
+                             const jacobi_params* p, int step, void* stream);
+
+/*
  * jacobi_ordering_table -- the library's pair schedule for N blocks
  * (host-side logic, no GPU needed): kind is JACOBI_ORDER_*; pairs receives
  * 2 ints (I < J, 0-based) per pair, step after step (room for N*(N-1) ints);

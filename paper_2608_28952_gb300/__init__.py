@@ -112,6 +112,7 @@ SIGNATURES = {
     "jacobi_plan_execute": (_I, [_P, _P, _P, _P, _P, _SP, _P]),
     "jacobi_plan_shape": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "jacobi_plan_destroy": (None, [_P]),
+    "jacobi_syev_step_noalloc": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
 }
 
 _LIB = None
@@ -238,6 +239,17 @@ def jacobi_syev_step(A, Q, step: int, p: jacobi_params | None = None, stream=Non
                                   _colmajor_ld(Q) if Q is not None else np_,
                                   C.byref(p) if p is not None else None, step,
                                   _stream_ptr(stream))
+
+
+def jacobi_syev_step_noalloc(A, Q, step: int, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev_step_noalloc``: ``jacobi_syev_step`` for callers that
+    cannot allocate device memory (np <= 768, b <= 128); the library keeps its
+    working buffers in one fixed device array instead."""
+    np_ = A.shape[0]
+    return lib().jacobi_syev_step_noalloc(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
+                                          _colmajor_ld(Q) if Q is not None else np_,
+                                          C.byref(p) if p is not None else None, step,
+                                          _stream_ptr(stream))
 
 
 def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=None):
