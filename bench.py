@@ -468,8 +468,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="evd4096", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--inner-max-sweeps", type=int, default=30,
-                    help="cap on the sweeps of one pivot solve (approximate solves)")
+    ap.add_argument("--inner-max-sweeps", type=int, default=0,
+                    help="cap on the sweeps of one pivot solve (0 = the library's automatic choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true")
     args = ap.parse_args(argv)

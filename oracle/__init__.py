@@ -187,7 +187,7 @@ def _params(b, ordering, max_sweeps, inner_max_sweeps, conv, tol, inner_tol, wan
 
 
 def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U64,
-              inner_max=30, pivot_order=1):
+              inner_max=1, pivot_order=1):
     """One parallel step (Algorithm 2 structure) on a full np x np matrix;
     pivot_order 1 sorts each pivot's eigenpairs descending (Qhat <- Qhat P).
 
@@ -203,7 +203,7 @@ def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U6
 
 
 def syev(A: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float = 1e-14,
-         ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 30,
+         ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 1,
          conv: int = CONV_OFF_ABS, inner_tol: float = 4 * U64, want_vectors: bool = True,
          threads: int = 0, pivot_order: int = 1):
     """Blocked (Algorithm 1 in the parallel order of Algorithm 2) or scalar

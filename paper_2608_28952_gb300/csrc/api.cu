@@ -136,7 +136,7 @@ int check_params(const jacobi_params& p)
     if (p.b < 1) return -7;
     if (p.b > 128) return JACOBI_ERR_UNSUPPORTED;
     if (p.ordering != JACOBI_ORDER_ROUND_ROBIN && p.ordering != JACOBI_ORDER_ANTI_DIAGONAL) return -7;
-    if (p.max_sweeps < 0 || p.max_sweeps > 1000 || p.inner_max_sweeps < 1) return -7;
+    if (p.max_sweeps < 0 || p.max_sweeps > 1000 || p.inner_max_sweeps < 0) return -7;
     if (!(p.tol >= 0.0) || !(p.inner_tol >= 0.0)) return -7;
     if (p.conv != JACOBI_CONV_OFF_ABS && p.conv != JACOBI_CONV_REL) return -7;
     if (p.pivot_order != 0 && p.pivot_order != 1) return -7;
@@ -163,7 +163,7 @@ extern "C" int jacobi_params_default(jacobi_params* p)
     p->b = 32;
     p->ordering = JACOBI_ORDER_ROUND_ROBIN;
     p->max_sweeps = 30;
-    p->inner_max_sweeps = 30;
+    p->inner_max_sweeps = 0;
     p->tol = 1e-14;
     p->inner_tol = 4.0 * U64;
     p->precision = JACOBI_PREC_FP64;
@@ -415,6 +415,7 @@ extern "C" int jacobi_syev(int n, double* A, int lda, double* w, double* Q, int 
     if (p.want_vectors && ldq < n) return -6;
     int e = check_params(p);
     if (e) return e;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;
     jacobi_stats st;
     memset(&st, 0, sizeof(st));
     cudaStream_t s = (cudaStream_t)stream;
@@ -590,6 +591,7 @@ extern "C" int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, dou
     if (p.want_vectors && ldv < n) return -7;
     int e = check_params(p);
     if (e) return e == -7 ? -8 : e;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;
     jacobi_stats st;
     memset(&st, 0, sizeof(st));
     int rc = gesvd_fp64(m, n, G, ldg, sigma, V, ldv, p, &st, (cudaStream_t)stream);
@@ -686,6 +688,7 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
     if (pin) p = *pin; else jacobi_params_default(&p);
     int e = check_params(p);
     if (e) return e == -7 ? -6 : e;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2) return -1;
     if (!A) return -2;
     if (lda < np) return -3;
@@ -744,6 +747,7 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
     if (pin) p = *pin; else jacobi_params_default(&p);
     int e = check_params(p);
     if (e) return e == -7 ? -7 : e;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;
     if (m < 1) return -1;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2 || np > m) return -2;
     if (!G) return -3;

@@ -28,10 +28,6 @@ constexpr double U32 = 5.9604644775390625e-08;
 struct Shape {
     int threads = 256;
     int smem_kmax = 0;   // EVD: even orders up to this are solved in shared memory
-    bool operator<(const Shape& o) const
-    {
-        return threads != o.threads ? threads < o.threads : smem_kmax < o.smem_kmax;
-    }
 };
 
 std::mutex g_tune_mu;
@@ -239,6 +235,7 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
     if (!h_n) return -6;
     jacobi_params p;
     if (pin) p = *pin; else jacobi_params_default(&p);
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;  // one-sided: full pivot solves
     if (p.max_sweeps < 1 || p.inner_max_sweeps < 1 || !(p.tol >= 0) || !(p.inner_tol >= 0)) return -10;
     cudaStream_t s = (cudaStream_t)stream;
     auto* pl = new jacobi_plan();

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
 {
     extern __shared__ __align__(16) double smem[];
     const int e = blockIdx.x, tid = threadIdx.x;
-    const int k = a.k, b = a.b, half = k >> 1, nq = half * (half - 1) / 2;
+    const int k = a.k, b = a.b, half = k >> 1;
     int I, J;
     const bool frozen = entry(a.pairs, e, I, J);
     const size_t ntp = tri_pad(k);

@@ -111,6 +111,7 @@ extern "C" int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, i
     if (pin) p = *pin; else jacobi_params_default(&p);
     if (p.b < 1 || p.b > kNoAllocMaxB) return p.b < 1 ? -6 : JACOBI_ERR_UNSUPPORTED;
     if (p.ordering != JACOBI_ORDER_ROUND_ROBIN && p.ordering != JACOBI_ORDER_ANTI_DIAGONAL) return -6;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;  // automatic, as in jacobi_syev_step
     if (p.inner_max_sweeps < 1 || !(p.inner_tol >= 0.0) || (p.pivot_order != 0 && p.pivot_order != 1)) return -6;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2) return -1;
     if (np > kNoAllocMaxN) return JACOBI_ERR_UNSUPPORTED;

@@ -160,7 +160,7 @@ def test_block_off2_identity_over_one_step():
         Ah = A[np.ix_(idx, idx)]
         D, V, rot, sw = oracle.pivot_solve(Ah)
         drop += _offsq(Ah) - _offsq(D)
-    A2, _, _ = oracle.syev_step(A, None, b, step)
+    A2, _, _ = oracle.syev_step(A, None, b, step, inner_max=30)
     assert abs(_offsq(A2) - (_offsq(A) - drop)) <= 1e-12 * np.sum(A * A)
 
 
@@ -173,7 +173,7 @@ def test_step_pivot_blocks_hold_dhat_and_match_explicit_product(order):
     A = gen.sym_gaussian(n, 33)
     N = oracle.padded_blocks(n, b)
     step = oracle.ordering(oracle.ORDER_ROUND_ROBIN, N)[0]
-    A2, _, _ = oracle.syev_step(A, None, b, step, pivot_order=order)
+    A2, _, _ = oracle.syev_step(A, None, b, step, inner_max=30, pivot_order=order)
     W = np.eye(n)
     for (I, J) in step:
         idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
