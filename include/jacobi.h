@@ -21,7 +21,11 @@
  *   - nothing is printed, nothing throws, nothing exits;
  *   - return value: 0 converged, >0 the sweep count when max_sweeps ran out
  *     (outputs then hold the current iterate), <0 an error (JACOBI_ERR_* or
- *     -k for an invalid k-th argument).
+ *     -k for an invalid k-th argument);
+ *   - the pivot solves of a step with few pairs run with a thread-block
+ *     cluster of up to 8 CTAs per pair (chosen automatically); the
+ *     environment variable JACOBI_PIVOT_CLUSTER=1 forces one CTA per pair,
+ *     =2/4/8 that cluster size where it fits.
  */
 #ifndef JACOBI_GB300_H
 #define JACOBI_GB300_H

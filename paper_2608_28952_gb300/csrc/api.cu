@@ -9,6 +9,7 @@
 // the only device->host traffic per sweep is the stop statistic.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -131,6 +132,26 @@ bool capture(SweepGraph& g, F body)
     return ok;
 }
 
+// Cluster size for the pivot solves of a step with npairs pairs of order k:
+// automatic unless JACOBI_PIVOT_CLUSTER is set ("1" = one CTA per pair, a
+// power of two <= 8 = that size when it fits).
+int choose_pivot_cluster(int k, int npairs)
+{
+    int dev = 0, sms = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int C = pivot_cluster_size(k, npairs, sms, (size_t)smem);
+    if (const char* env = getenv("JACOBI_PIVOT_CLUSTER")) {
+        const int want = atoi(env);
+        if (want == 1) C = 1;
+        else if (want == 2 || want == 4 || want == 8) {
+            if (k % want == 0 && k / want >= 8 && pivot_cluster_smem(k, want) + 4096 <= (size_t)smem) C = want;
+        }
+    }
+    return C;
+}
+
 int check_params(const jacobi_params& p)
 {
     if (p.b < 1) return -7;
@@ -200,6 +221,8 @@ namespace jac {
 struct EvdState {
     int np, b, k;
     int n_real;   // rows/columns >= n_real are zero padding
+    int pcl = 1;  // pivot cluster size (1: one CTA per pair)
+    unsigned* qtab = nullptr;
     Ordering ord;
     int2* dpairs;
     double* Aw[2];
@@ -236,7 +259,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     pa.n_real = E.n_real;
     pa.gscratch = E.gscratch;
     pa.cnt = E.cnt;
-    cudaError_t e = launch_pivot(pa, cs);
+    cudaError_t e = E.pcl > 1 ? launch_pivot_cluster(pa, E.pcl, E.qtab, cs) : launch_pivot(pa, cs);
     if (e != cudaSuccess) return e;
     if (mid && (e = cudaEventRecordWithFlags(mid, cs, cudaEventRecordExternal)) != cudaSuccess) return e;
     UpdateArgs ua{};
@@ -354,7 +377,10 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         E.result = ws.get<double>(3);
         E.cnt = ws.get<DevCounters>(1);
         int* rank = ws.get<int>(n);
+        E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
+        E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(E.dpairs, E.ord.dev_pairs.data(), E.ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(E.cnt, 0, sizeof(DevCounters), s) != cudaSuccess ||
@@ -459,7 +485,10 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
         double* norms = ws.get<double>(n);
         int* rank = ws.get<int>(n);
         DevCounters* cnt = ws.get<DevCounters>(1);
+        const int pcl = choose_pivot_cluster(k, ord.dev_per_step);
+        unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (qtab && launch_quad_table(qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(dpairs, ord.dev_pairs.data(), ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s) != cudaSuccess)
@@ -505,7 +534,8 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                     pa.n_real = n;
                     pa.gscratch = gscr;
                     pa.cnt = cnt;
-                    if (launch_pivot(pa, cs) != cudaSuccess) return false;
+                    if ((pcl > 1 ? launch_pivot_cluster(pa, pcl, qtab, cs) : launch_pivot(pa, cs)) != cudaSuccess)
+                        return false;
                     if (launch_max_into(relmax, nps, sweepmax, cs) != cudaSuccess) return false;
                     if (cudaEventRecordWithFlags(pe.ev[3 * si + 2], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     ColUpdateArgs ca{};
@@ -714,7 +744,10 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         E.gscratch = gsz ? ws.get<double>(gsz * E.ord.max_pairs) : nullptr;
         E.dpairs = ws.get<int2>(E.ord.dev_pairs.size() / 2);
         E.cnt = ws.get<DevCounters>(1);
+        E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
+        E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(E.dpairs, E.ord.dev_pairs.data(), E.ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(E.cnt, 0, sizeof(DevCounters), s) != cudaSuccess ||
@@ -775,7 +808,10 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         int2* dpairs = ws.get<int2>(ord.dev_pairs.size() / 2);
         double* smax = ws.get<double>(1);
         DevCounters* cnt = ws.get<DevCounters>(1);
+        const int pcl = choose_pivot_cluster(k, nps);
+        unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (qtab && launch_quad_table(qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(dpairs, ord.dev_pairs.data(), ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s) != cudaSuccess ||
@@ -805,7 +841,8 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         pa.n_real = np;
         pa.gscratch = gscr;
         pa.cnt = cnt;
-        if (launch_pivot(pa, s) != cudaSuccess || launch_max_into(relmax, nps, smax, s) != cudaSuccess)
+        if ((pcl > 1 ? launch_pivot_cluster(pa, pcl, qtab, s) : launch_pivot(pa, s)) != cudaSuccess ||
+            launch_max_into(relmax, nps, smax, s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
         ColUpdateArgs ca{};
         ca.Gin = Gw[0];

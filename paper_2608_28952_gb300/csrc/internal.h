@@ -83,6 +83,13 @@ struct PivotArgs {
     DevCounters* cnt;
 };
 cudaError_t launch_pivot(const PivotArgs& a, cudaStream_t s);
+// The same pivot solves with a cluster of C CTAs per pair (C from
+// pivot_cluster_size; C == 1 means: use launch_pivot).  qtab: quad table
+// for half = 128 (device, from launch_quad_table).
+int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap);
+size_t pivot_cluster_smem(int k, int C);
+cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab, cudaStream_t s);
+cudaError_t launch_quad_table(unsigned* qtab, int h, cudaStream_t s);
 size_t pivot_gscratch_doubles(int k);   // per pair, 0 when shared memory suffices
 
 // Update of one step (EVD): sandwich items A'_{P1P2} = V1^T A_{P1P2} V2 for

@@ -1,0 +1,378 @@
+// k_pivot_cluster.cu -- the pivot solves of one step with a thread-block
+// cluster of C CTAs per pair, so that a step's few pairs (n/(2b) of them)
+// keep all SMs busy: at n = 4096, b = 64 a step has 32 pairs; with C = 4 they
+// occupy 128 SMs instead of 32.
+//
+// Same computation as k_pivot (Algorithm 2 applied with b = 1 to each 2b x 2b
+// pivot, rotations in Rutishauser's form, diagonal carried as hi + lo), laid
+// out over the cluster's distributed shared memory:
+//   * the packed lower triangle of the pivot is split by row ranges over the
+//     C CTAs (entry (i, j), i >= j, lives in the CTA that owns row i) and is
+//     read and written through DSMEM addresses;
+//   * V is split by rows (CTA r owns rows [r k/C, (r+1) k/C)), so rotating
+//     its column pairs is local;
+//   * every CTA keeps its own copy of the diagonal (hi and lo) and computes
+//     every rotation of a round itself from that copy and the (shared) a_pq,
+//     so the copies stay identical.  A split cluster barrier (arrive after
+//     choosing the rotations, wait before the rotated a_pq entries are
+//     zeroed) keeps those zeroes from racing a slower CTA's reads without
+//     stalling the rotation work; a full cluster barrier ends each round.
+// Quads (2x2 cross-pair blocks) are spread over all C * blockDim threads.
+// Every loop runs the same trip count in all CTAs of a cluster, so the
+// cluster barriers always match.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "jacobi_core.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace jac {
+
+constexpr int PC_T = 512;
+constexpr int PC_MAXC = 8;
+
+__device__ __forceinline__ int pc_pair_map(int I, int J, int b, int x)
+{
+    return x < b ? I * b + x : J * b + (x - b);
+}
+
+// Row ranges: CTA r owns rows [row0[r], row0[r+1]) of the packed triangle,
+// chosen so the entry counts are as equal as possible.
+struct Split {
+    int C;
+    int row0[PC_MAXC + 1];
+    int base[PC_MAXC + 1];  // packed index of the first entry of row0[r]
+};
+
+__host__ __device__ inline void make_split(int k, int C, Split& s)
+{
+    s.C = C;
+    const long long total = (long long)k * (k + 1) / 2;
+    int row = 0;
+    s.row0[0] = 0;
+    s.base[0] = 0;
+    for (int r = 1; r < C; ++r) {
+        const long long target = total * r / C;
+        while (row < k && (long long)(row + 1) * (row + 2) / 2 <= target) ++row;
+        s.row0[r] = row;
+        s.base[r] = row * (row + 1) / 2;
+    }
+    s.row0[C] = k;
+    s.base[C] = (int)total;
+}
+
+__host__ inline int split_max_chunk(int k, int C)
+{
+    Split s;
+    make_split(k, C, s);
+    int m = 0;
+    for (int r = 0; r < C; ++r) m = s.base[r + 1] - s.base[r] > m ? s.base[r + 1] - s.base[r] : m;
+    return m;
+}
+
+struct DistPacked {
+    double* ptr[PC_MAXC];   // each CTA's chunk, as generic (DSMEM) addresses
+    Split sp;
+    __device__ __forceinline__ double* at(int i, int j) const
+    {
+        if (i < j) { const int t = i; i = j; j = t; }
+        int r = 0;
+#pragma unroll
+        for (int u = 1; u < PC_MAXC; ++u)
+            if (u < sp.C && i >= sp.row0[u]) r = u;
+        return ptr[r] + (tri(i) + j - sp.base[r]);
+    }
+};
+
+size_t pivot_cluster_smem(int k, int C)
+{
+    const int half = k / 2;
+    const size_t chunk = (size_t)split_max_chunk(k, C);
+    const size_t vrows = (size_t)(k / C) * k;
+    return (chunk + vrows + 2 * (size_t)k + 4 * (size_t)half) * sizeof(double) +
+           3 * (size_t)half * sizeof(int) + 64;
+}
+
+__global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, const unsigned* qtab)
+{
+    extern __shared__ __align__(16) double csm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = (int)cluster.block_rank();
+    const int e = blockIdx.x / C;
+    const int tid = threadIdx.x, nt = blockDim.x, gtid = r * nt + tid, gnt = C * nt;
+    const int k = a.k, b = a.b, half = k >> 1, nq = half * (half - 1) / 2;
+    const int rows = k / C, r_lo = r * rows;
+    int I, J;
+    {
+        const int2 pr = a.pairs[e];
+        const bool fz = pr.x < 0;
+        I = fz ? -1 - pr.x : pr.x;
+        J = fz ? -1 - pr.y : pr.y;
+    }
+    const bool frozen = a.pairs[e].x < 0;
+
+    DistPacked ap;
+    make_split(k, C, ap.sp);
+    const int chunk_max = [&] {
+        int m = 0;
+        for (int u = 0; u < C; ++u) m = max(m, ap.sp.base[u + 1] - ap.sp.base[u]);
+        return m;
+    }();
+    double* my_chunk = csm;
+    double* Vl = my_chunk + chunk_max;       // rows x k (ld rows): V(r_lo + i, j) at Vl[i + rows j]
+    double* dhi = Vl + (size_t)rows * k;     // diagonal replica
+    double* dlo = dhi + k;
+    double* rtau = dlo + k;
+    double* rs = rtau + half;
+    double* rt = rs + half;
+    double* rapq = rt + half;
+    int* rp = (int*)(rapq + half);
+    int* rq = rp + half;
+    int* ron = rq + half;
+    __shared__ int s_cnt;
+    __shared__ double s_red[PC_T / 32];
+    __shared__ double s_part[PC_MAXC];
+    __shared__ int s_dest[256];
+    __shared__ int s_pos[256];
+    for (int u = 0; u < C; ++u) ap.ptr[u] = cluster.map_shared_rank(my_chunk, u);
+
+    // ---- load: the entries this CTA owns, V rows = identity rows
+    const int my_lo = ap.sp.row0[r], my_hi = ap.sp.row0[r + 1];
+    if (a.gram == nullptr) {
+        for (int idx = tid; idx < k * k; idx += nt) {
+            const int ii = idx % k, jj = idx / k;
+            if (ii < jj || ii < my_lo || ii >= my_hi) continue;
+            my_chunk[tri(ii) + jj - ap.sp.base[r]] =
+                a.Ain[pc_pair_map(I, J, b, ii) + (size_t)a.ld * pc_pair_map(I, J, b, jj)];
+        }
+    } else {
+        const double* g = a.gram + (size_t)e * a.npanels * k * k;
+        for (int idx = tid; idx < k * k; idx += nt) {
+            const int ii = idx % k, jj = idx / k;
+            if (ii < jj || ii < my_lo || ii >= my_hi) continue;
+            double s = 0.0;
+            for (int p = 0; p < a.npanels; ++p) s += g[(size_t)p * k * k + idx];  // fixed order
+            my_chunk[tri(ii) + jj - ap.sp.base[r]] = s;
+        }
+    }
+    for (int idx = tid; idx < rows * k; idx += nt) {
+        const int i = idx % rows, j = idx / rows;
+        Vl[idx] = (r_lo + i == j) ? 1.0 : 0.0;
+    }
+    cluster.sync();
+    for (int x = tid; x < k; x += nt) {
+        dhi[x] = *ap.at(x, x);
+        dlo[x] = 0.0;
+    }
+
+    // ---- one-sided stop statistic (Gram pivots), max over the cluster
+    if (a.relmax) {
+        __syncthreads();
+        double mx = 0.0;
+        if (!frozen)
+            for (int idx = tid; idx < k * k; idx += nt) {
+                const int ii = idx % k, jj = idx / k;
+                if (ii <= jj || ii < my_lo || ii >= my_hi) continue;
+                const double d = sqrt(dhi[ii]) * sqrt(dhi[jj]);
+                if (d > 0.0) mx = fmax(mx, fabs(my_chunk[tri(ii) + jj - ap.sp.base[r]]) / d);
+            }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int w = 0; w < nt / 32; ++w) m = fmax(m, s_red[w]);
+            *cluster.map_shared_rank(&s_part[r], 0) = m;
+        }
+        cluster.sync();
+        if (r == 0 && tid == 0) {
+            double m = 0.0;
+            for (int u = 0; u < C; ++u) m = fmax(m, s_part[u]);
+            a.relmax[e] = m;
+        }
+    }
+    __syncthreads();
+
+    // ---- inner sweeps
+    const double tol = a.tol_rel;
+    const int max_sweeps = frozen ? 0 : a.max_sweeps;
+    int total_rot = 0, sweeps = 0;
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        if (tid == 0) s_cnt = 0;
+        __syncthreads();
+        for (int rd = 0; rd < k - 1; ++rd) {
+            // rotations of the round, from the local diagonal and the shared a_pq
+            for (int ee = tid; ee < half; ee += nt) {
+                const int pa = ee, pb = k - 1 - ee;
+                const int ia = pa == 0 ? 0 : 1 + (pa - 1 + rd) % (k - 1);
+                const int ib = 1 + (pb - 1 + rd) % (k - 1);
+                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+                const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
+                const bool on = rotation_wanted(app, aqq, apq, tol);
+                rp[ee] = p;
+                rq[ee] = q;
+                ron[ee] = on;
+                if (on) {
+                    double s, t, tau;
+                    schur2(app, aqq, apq, s, t, tau);
+                    rtau[ee] = tau;
+                    rs[ee] = s;
+                    rt[ee] = t;
+                    rapq[ee] = apq;
+                    atomicAdd(&s_cnt, 1);
+                }
+            }
+            __syncthreads();
+            asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+            // quads over the whole cluster
+            for (int qi = gtid; qi < nq; qi += gnt) {
+                int e1, e2;
+                quad_of(qtab, qi, e1, e2);
+                const int on1 = ron[e1], on2 = ron[e2];
+                if (!(on1 | on2)) continue;
+                const int p1 = rp[e1], q1 = rq[e1], p2 = rp[e2], q2 = rq[e2];
+                double* a00 = ap.at(p1, p2);
+                double* a01 = ap.at(p1, q2);
+                double* a10 = ap.at(q1, p2);
+                double* a11 = ap.at(q1, q2);
+                double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                if (on1) {
+                    const double s = rs[e1], tau = rtau[e1];
+                    rot2(s, tau, x00, x10);
+                    rot2(s, tau, x01, x11);
+                }
+                if (on2) {
+                    const double s = rs[e2], tau = rtau[e2];
+                    rot2(s, tau, x00, x01);
+                    rot2(s, tau, x10, x11);
+                }
+                *a00 = x00;
+                *a01 = x01;
+                *a10 = x10;
+                *a11 = x11;
+            }
+            // diagonal replica (every CTA)
+            for (int ee = tid; ee < half; ee += nt) {
+                if (!ron[ee]) continue;
+                const int p = rp[ee], q = rq[ee];
+                dd_add_prod(dhi[p], dlo[p], rt[ee], rapq[ee], -1.0);
+                dd_add_prod(dhi[q], dlo[q], rt[ee], rapq[ee], 1.0);
+            }
+            // local rows of V
+            for (int it = tid; it < half * rows; it += nt) {
+                const int ee = it / rows, i = it - ee * rows;
+                if (!ron[ee]) continue;
+                const int p = rp[ee], q = rq[ee];
+                double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                rot2(rs[ee], rtau[ee], vp, vq);
+                Vl[i + (size_t)rows * p] = vp;
+                Vl[i + (size_t)rows * q] = vq;
+            }
+            // every CTA has read this round's a_pq: rank 0 may zero them now
+            asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+            if (r == 0)
+                for (int ee = tid; ee < half; ee += nt)
+                    if (ron[ee]) *ap.at(rq[ee], rp[ee]) = 0.0;
+            cluster.sync();
+        }
+        const int cnt = s_cnt;
+        total_rot += cnt;
+        sweeps = sw + 1;
+        __syncthreads();
+        if (cnt == 0) break;
+    }
+    for (int x = tid; x < k; x += nt) dhi[x] += dlo[x];  // hi + lo, rounded once
+    __syncthreads();
+
+    // ---- permutation (identical in every CTA: same diagonal replica)
+    if (tid == 0) {
+        int nr = 0;
+        for (int x = 0; x < k; ++x)
+            if (pc_pair_map(I, J, b, x) < a.n_real) s_pos[nr++] = x;
+    }
+    __syncthreads();
+    for (int x = tid; x < k; x += nt) {
+        int dest = x;
+        if (a.order == 1 && total_rot > 0 && pc_pair_map(I, J, b, x) < a.n_real) {
+            const double dx = dhi[x];
+            int rr = 0;
+            for (int y = 0; y < k; ++y) {
+                if (y == x || pc_pair_map(I, J, b, y) >= a.n_real) continue;
+                const double dy = dhi[y];
+                rr += (dy > dx) || (dy == dx && y < x);
+            }
+            dest = s_pos[rr];
+        }
+        s_dest[x] = dest;
+    }
+    __syncthreads();
+
+    // ---- outputs: this CTA's rows of V (and the matching columns of V^T)
+    double* Vo = a.V + (size_t)e * 2 * k * k;
+    for (int idx = tid; idx < rows * k; idx += nt) {
+        const int i = idx % rows, j = idx / rows;
+        const double v = Vl[idx];  // V(r_lo + i, j) -> column s_dest[j]
+        Vo[(r_lo + i) + (size_t)k * s_dest[j]] = v;
+        Vo[(size_t)k * k + s_dest[j] + (size_t)k * (r_lo + i)] = v;
+    }
+    if (a.Aout) {
+        for (int idx = tid; idx < k * k; idx += nt) {
+            const int ii = idx % k, jj = idx / k;
+            const int hi_row = ii >= jj ? ii : jj;
+            if (hi_row < my_lo || hi_row >= my_hi) continue;
+            const double v = ii == jj ? dhi[ii] : my_chunk[tri(hi_row) + (ii >= jj ? jj : ii) - ap.sp.base[r]];
+            a.Aout[pc_pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pc_pair_map(I, J, b, s_dest[jj])] = v;
+        }
+    }
+    if (r == 0 && tid == 0) {
+        a.rot[e] = total_rot;
+        atomicAdd(&a.cnt->rotations, (unsigned long long)total_rot);
+        atomicAdd(&a.cnt->inner_sweeps, (unsigned long long)sweeps);
+        if (!frozen) atomicAdd(&a.cnt->pair_solves, 1ull);
+        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)(18 * k));
+    }
+    // no CTA may leave while others can still read its shared memory
+    cluster.sync();
+}
+
+// Cluster size for a step with npairs pairs on an sms-SM GPU: the largest
+// power of two C <= 8 with npairs * C <= sms whose per-CTA share fits the
+// shared-memory limit, or 1 (use the one-CTA kernel).
+int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
+{
+    int best = 1;
+    for (int C = 2; C <= PC_MAXC; C *= 2) {
+        if (k % C || k / C < 8 || npairs * C > sms) break;
+        if (pivot_cluster_smem(k, C) + 4096 <= smem_cap) best = C;
+    }
+    return best;
+}
+
+cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab, cudaStream_t s)
+{
+    if (a.npairs <= 0) return cudaSuccess;
+    const size_t smem = pivot_cluster_smem(a.k, C);
+    cudaError_t e = cudaFuncSetAttribute(k_pivot_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(k_pivot_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.npairs * C);
+    cfg.blockDim = dim3(PC_T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pivot_cluster, a, C, qtab);
+}
+
+}  // namespace jac

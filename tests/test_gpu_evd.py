@@ -111,6 +111,29 @@ def test_step_parity_random(jg, np_, b, ordering, steps):
         assert np.abs(Ag - A_or).max() <= max(1e-13, 4 * tol_v) * nrm2
 
 
+@pytest.mark.parametrize("cl", ["1", "2", "4", "8"])
+@pytest.mark.parametrize("np_,b", [(256, 32), (512, 128), (384, 64)])
+def test_step_parity_cluster_sizes(jg, monkeypatch, cl, np_, b):
+    """The pivot solves with 1 CTA per pair and with clusters of 2, 4, 8 CTAs
+    (distributed pivot in shared memory) give the oracle's step."""
+    monkeypatch.setenv("JACOBI_PIVOT_CLUSTER", cl)
+    d = np.linspace(1.0, 2.0 * np_, np_)
+    A0 = np.asfortranarray(np.diag(d) + 0.05 * gen.sym_gaussian(np_, 930 + np_ + b))
+    for s in (0, 2):
+        Ag, Qg, A_or, Q_or, _ = _step_pair(jg, A0, b, 0, s)
+        assert np.abs(Ag - A_or).max() <= 1e-13 * np.abs(A0).max()
+        assert np.abs(Qg - Q_or).max() <= 1e-13
+
+
+@pytest.mark.parametrize("cl", ["1", "4"])
+def test_full_solve_cluster_sizes(jg, monkeypatch, cl):
+    monkeypatch.setenv("JACOBI_PIVOT_CLUSTER", cl)
+    A, lam = gen.sym_known(512, "uniform", seed=1960)
+    w, Q, _, st = jg.syev(A, b=64)
+    assert st.status == 0
+    check(A, _np(w), _np(Q), np.sort(lam))
+
+
 def test_step_without_permutation(jg):
     """pivot_order = 0 (eigenpairs as solved, the paper's pseudocode)."""
     np_, b = 96, 16

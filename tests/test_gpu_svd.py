@@ -54,7 +54,7 @@ def test_step_parity_elementwise(jg, m, np_, b, ordering):
     tab = oracle.ordering(ordering, np_ // b)
     p = jg.params(b=b, ordering=ordering, tol=1e-15)
     for s in (0, len(tab) - 1):
-        G_or, V_or, r_or = oracle.gesvd_step(G0, np.eye(np_), b, tab[s], tol_rel=tol)
+        G_or, V_or, r_or = oracle.gesvd_step(G0, np.eye(np_), b, tab[s], tol_rel=tol, inner_max=30)
         Gd, Vd = _dev(G0), _dev(np.eye(np_))
         rc, r = jg.jacobi_gesvd_step(Gd, Vd, s, p)
         assert rc == 0
@@ -73,6 +73,21 @@ def test_known_singular_values(jg, m, n, b):
     assert st.status == 0 and rc_or == 0
     check_svd(G, U, s, V, s_or)
     assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+
+
+@pytest.mark.parametrize("cl", ["1", "4"])
+def test_step_parity_cluster_sizes(jg, monkeypatch, cl):
+    monkeypatch.setenv("JACOBI_PIVOT_CLUSTER", cl)
+    m, np_, b = 900, 256, 32
+    G0 = gen.tall_gaussian(m, np_, 4450, dtype=np.float64)
+    tab = oracle.ordering(0, np_ // b)
+    G_or, V_or, r_or = oracle.gesvd_step(G0, np.eye(np_), b, tab[1], tol_rel=oracle.svd_tol(m),
+                                         inner_max=30)
+    Gd, Vd = _dev(G0), _dev(np.eye(np_))
+    rc, r = jg.jacobi_gesvd_step(Gd, Vd, 1, jg.params(b=b, tol=1e-15))
+    assert rc == 0 and abs(r - r_or) <= 1e-13
+    assert np.abs(_np(Gd) - G_or).max() <= 1e-12 * np.abs(G0).max()
+    assert np.abs(_np(Vd) - V_or).max() <= 1e-12
 
 
 def test_without_permutation(jg):
