@@ -286,6 +286,20 @@ int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
                              const jacobi_params* p, int step, void* stream);
 
 /*
+ * jacobi_lowp_gemm -- the split-precision tensor-core product used by the
+ * mixed-precision sweeps, as a primitive: C = op(A) B in FP32 where every
+ * operand value x enters as hi = bf16(x), lo = bf16(x - hi) and each product
+ * as hi*hi + hi*lo + lo*hi, accumulated in FP32 by tcgen05.mma (kind::f16)
+ * in tensor memory.  All matrices column-major FP32 on the device: A is
+ * M x K (transA = 0, lda >= M) or K x M (transA = 1, lda >= K), B K x N
+ * (ldb >= K), C M x N (ldc >= M).  Returns 0, -k for an invalid argument,
+ * JACOBI_ERR_TIMEOUT if a bounded wait on the tensor cores ran out.
+ * (The paper names variable precision as future work, Sec. 7.)
+ */
+int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, const float* B,
+                     int ldb, float* C, int ldc, void* stream);
+
+/*
  * jacobi_ordering_table -- the library's pair schedule for N blocks
  * (host-side logic, no GPU needed): kind is JACOBI_ORDER_*; pairs receives
  * 2 ints (I < J, 0-based) per pair, step after step (room for N*(N-1) ints);

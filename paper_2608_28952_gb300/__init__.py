@@ -113,6 +113,7 @@ SIGNATURES = {
     "jacobi_plan_shape": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "jacobi_plan_destroy": (None, [_P]),
     "jacobi_syev_step_noalloc": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
+    "jacobi_lowp_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
 }
 
 _LIB = None
@@ -262,6 +263,15 @@ def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=No
                                  C.byref(p) if p is not None else None, step, C.byref(r),
                                  _stream_ptr(stream))
     return rc, r.value
+
+
+def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
+    """C ``jacobi_lowp_gemm``: C = op(A) B (FP32, column-major CUDA tensors)
+    on the tensor cores with bf16 hi/lo operand splits."""
+    K, N = B.shape
+    M = C.shape[0]
+    return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
+                                  _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
 
 
 def jacobi_ordering_table(kind: int, N: int):
