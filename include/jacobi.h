@@ -121,6 +121,10 @@ typedef struct {
     double flops_update;     /* of which in the update / Gram kernels          */
     double flops_fp32;       /* FP32 flops issued                              */
     double flops_lowp;       /* bf16 / fp16 / tf32 tensor flops issued         */
+    double ms_lowp;          /* mixed forms: device time of the low-precision
+                                sweeps (pivot solves included)                 */
+    double ms_refine;        /* mixed forms: device time of the return to FP64
+                                (re-orthogonalisation, refinement, S = X^T A X) */
 } jacobi_stats;
 
 /* Fill *p with the defaults above.  Returns 0. */
@@ -298,6 +302,25 @@ int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
  */
 int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, const float* B,
                      int ldb, float* C, int ldc, void* stream);
+
+/*
+ * jacobi_syev_step_lowp -- one step of the mixed form's low-precision phase
+ * (Algorithm 2's step with the updates on the tensor cores): the pivot
+ * blocks of step `step` are promoted to FP64 and solved in FP64 (as in
+ * jacobi_syev_step), D is written back rounded to FP32, and every
+ * block-row/column update of A (A'_{P1P2} = V1^T A_{P1P2} V2, mirrored) and
+ * column update of Q (Q'(:,P) = Q(:,P) V_P) is formed from V rounded to FP32
+ * by the split-precision product of jacobi_lowp_gemm.  A is a full
+ * symmetric np x np FP32 matrix (exactly symmetric), np = N * p->b with N
+ * even for round-robin; Q is np x np FP32 or NULL; both device, column-major,
+ * updated in place.  p->precision must be JACOBI_PREC_MIXED_BF16X3.
+ * Returns 0, -k for an invalid argument, JACOBI_ERR_UNSUPPORTED for another
+ * precision, JACOBI_ERR_TIMEOUT if a bounded tensor-core wait ran out,
+ * JACOBI_ERR_CUDA / JACOBI_ERR_ALLOC.  Allocates its workspace
+ * stream-ordered and blocks until done.
+ */
+int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ldq, const jacobi_params* p,
+                          int step, void* stream);
 
 /*
  * jacobi_ordering_table -- the library's pair schedule for N blocks

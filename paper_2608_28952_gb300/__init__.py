@@ -53,7 +53,8 @@ class jacobi_stats(C.Structure):
                 ("launches", C.c_longlong), ("pivot_launches", C.c_longlong),
                 ("update_launches", C.c_longlong),
                 ("flops_fp64", C.c_double), ("flops_update", C.c_double),
-                ("flops_fp32", C.c_double), ("flops_lowp", C.c_double)]
+                ("flops_fp32", C.c_double), ("flops_lowp", C.c_double),
+                ("ms_lowp", C.c_double), ("ms_refine", C.c_double)]
 
 
 @dataclass
@@ -79,6 +80,8 @@ class Stats:
     flops_update: float
     flops_fp32: float
     flops_lowp: float
+    ms_lowp: float
+    ms_refine: float
     off_hist: list = field(default_factory=list)
 
 
@@ -87,6 +90,7 @@ def _stats(s: jacobi_stats) -> Stats:
                  s.rotations, s.inner_sweeps, s.norm_fro, s.off_initial, s.off_final,
                  s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
                  s.update_launches, s.flops_fp64, s.flops_update, s.flops_fp32, s.flops_lowp,
+                 s.ms_lowp, s.ms_refine,
                  list(s.off_hist)[: max(0, min(64, s.sweeps))])
 
 
@@ -114,6 +118,7 @@ SIGNATURES = {
     "jacobi_plan_destroy": (None, [_P]),
     "jacobi_syev_step_noalloc": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_lowp_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
+    "jacobi_syev_step_lowp": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
 }
 
 _LIB = None
@@ -272,6 +277,17 @@ def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
     M = C.shape[0]
     return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
                                   _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
+
+
+def jacobi_syev_step_lowp(A, Q, step: int, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev_step_lowp``: one low-precision step of the mixed form
+    in place on FP32 column-major CUDA tensors A (np x np, symmetric) and Q
+    (or None); p.precision must be JACOBI_PREC_MIXED_BF16X3."""
+    np_ = A.shape[0]
+    return lib().jacobi_syev_step_lowp(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
+                                       _colmajor_ld(Q) if Q is not None else np_,
+                                       C.byref(p) if p is not None else None, step,
+                                       _stream_ptr(stream))
 
 
 def jacobi_ordering_table(kind: int, N: int):

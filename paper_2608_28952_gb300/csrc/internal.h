@@ -66,6 +66,8 @@ cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned i
 struct PivotArgs {
     const double* Ain;         // EVD: working A (np x np, ld np); SVD: null
     double* Aout;              // EVD: next working A (pivot blocks written)
+    const float* Ain32;        // mixed form: FP32 working A instead of Ain
+    float* Aout32;             // mixed form: FP32 next A instead of Aout
     int ld;                    // np
     const double* gram;        // SVD: Gram partials [pair][panel][k*k] or null
     int npanels;
@@ -137,5 +139,35 @@ cudaError_t launch_load_svd(int m, int n, int np, const double* G, int ldg, doub
                             double* Vw, DevCounters* cnt, cudaStream_t s);
 // Max over pairs of relmax[0..npairs) into *out (max with its prior value).
 cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaStream_t s);
+
+// ----------------------------------------------------------------- mixed form (tensor cores)
+// One low-precision step's updates on FP32 working copies: stage 1
+// T_pb = A_{P1P2} V2 (all pair-blocks P1 < P2) and Q'(:,P) = Q(:,P) V_P,
+// stage 2 A'_{P1P2} = V1^T T_pb with its mirror; products from bf16 hi/lo
+// splits on tcgen05.  The pivot blocks are written by the pivot kernel.
+struct TcUpdArgs {
+    const float* Ain; float* Aout; int lda;     // np x np FP32, double-buffered
+    const float* Qin; float* Qout; int ldq; int qrows;
+    float* T;                                   // [npb][k*k] stage-1 products
+    const int2* pairs; int npairs; int b, k;
+    const double* V; const int* rot;            // pivot kernel outputs (FP64 V, V^T)
+    int* err;                                   // set on a timed-out tensor-core wait
+    DevCounters* cnt;
+};
+cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s);
+size_t tc_update_tbuf_floats(int npairs, int k);
+
+cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
+                             double* result, cudaStream_t s);
+cudaError_t launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int transA,
+                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
+cudaError_t launch_load_sym32(int n, int np, const double* A, int lda, float* A32, float* Q32,
+                              DevCounters* cnt, cudaStream_t s);
+cudaError_t launch_pad_sym64(int n, int np, const double* A, int lda, double* A0p, cudaStream_t s);
+cudaError_t launch_f32_to_f64(long long count, const float* x, double* y, cudaStream_t s);
+cudaError_t launch_oa_step_elementwise(int np, const double* S, double* G, double* lam, double eta,
+                                       cudaStream_t s);
+cudaError_t launch_symmetrize(int np, const double* S, double* B, cudaStream_t s);
+cudaError_t launch_ns_halfres(int np, double* G, cudaStream_t s);
 
 }  // namespace jac

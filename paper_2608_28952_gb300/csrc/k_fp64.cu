@@ -123,7 +123,8 @@ int reduce_blocks_for(int np)
     return g < 1 ? 1 : g;
 }
 
-__global__ void __launch_bounds__(RED_T) k_offnorm(int np, const double* __restrict__ Aw,
+template <typename TA>
+__global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict__ Aw,
                                                    double* partial, unsigned int* ticket,
                                                    double* result, int want_rel)
 {
@@ -132,16 +133,16 @@ __global__ void __launch_bounds__(RED_T) k_offnorm(int np, const double* __restr
     const int tid = threadIdx.x, G = gridDim.x;
     double off = 0.0, all = 0.0, rel = 0.0;
     for (int j = blockIdx.x; j < np; j += G) {
-        const double* col = Aw + (size_t)np * j;
-        const double ajj = fabs(col[j]);
+        const TA* col = Aw + (size_t)np * j;
+        const double ajj = fabs((double)col[j]);
         for (int i = tid; i < np; i += RED_T) {
-            double v = col[i];
+            double v = (double)col[i];
             double v2 = v * v;
             all += v2;
             if (i != j) {
                 off += v2;
                 if (want_rel && v != 0.0) {
-                    double d = fabs(Aw[(size_t)np * i + i]) * ajj;
+                    double d = fabs((double)Aw[(size_t)np * i + i]) * ajj;
                     double r = d > 0.0 ? v2 / d : INFINITY;
                     rel = fmax(rel, r);
                 }
@@ -187,7 +188,14 @@ __global__ void __launch_bounds__(RED_T) k_offnorm(int np, const double* __restr
 cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned int* ticket,
                            double* result, bool want_rel, cudaStream_t s)
 {
-    k_offnorm<<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, want_rel);
+    k_offnorm<double><<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, want_rel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
+                             double* result, cudaStream_t s)
+{
+    k_offnorm<float><<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, 0);
     return cudaGetLastError();
 }
 
@@ -247,9 +255,10 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
     if (a.gram == nullptr) {
         for (int idx = tid; idx < k * k; idx += PIV_T) {
             int ii = idx % k, jj = idx / k;
-            if (ii >= jj)
-                Ap[tri(ii) + jj] =
-                    a.Ain[pair_map(I, J, b, ii) + (size_t)a.ld * pair_map(I, J, b, jj)];
+            if (ii >= jj) {
+                const size_t g = pair_map(I, J, b, ii) + (size_t)a.ld * pair_map(I, J, b, jj);
+                Ap[tri(ii) + jj] = a.Ain32 ? (double)a.Ain32[g] : a.Ain[g];
+            }
         }
     } else {
         const double* g = a.gram + (size_t)e * a.npanels * k * k;
@@ -324,11 +333,12 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
         Vo[ii + (size_t)k * s_dest[jj]] = v;
         Vo[(size_t)k * k + s_dest[jj] + (size_t)k * ii] = v;
     }
-    if (a.Aout) {
+    if (a.Aout || a.Aout32) {
         for (int idx = tid; idx < k * k; idx += PIV_T) {
             const int ii = idx % k, jj = idx / k;
-            a.Aout[pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pair_map(I, J, b, s_dest[jj])] =
-                Ap[sidx(ii, jj)];
+            const size_t g = pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pair_map(I, J, b, s_dest[jj]);
+            if (a.Aout32) a.Aout32[g] = (float)Ap[sidx(ii, jj)];
+            else a.Aout[g] = Ap[sidx(ii, jj)];
         }
     }
     if (tid == 0) {
@@ -741,6 +751,57 @@ cudaError_t launch_gram(const double* G, int ldg, int m, const int2* pairs, int 
     else if (k <= 128) JAC_GRAM(4);
     else JAC_GRAM(8);
 #undef JAC_GRAM
+    return cudaGetLastError();
+}
+
+// ======================================================================== general FP64 GEMM
+// C (M x N) = alpha op(A) B + beta C, column-major; op(A) = A (M x K) or A^T
+// (A stored K x M).  Tiles of 128 x 32 on 256 threads (the update kernels'
+// register tiling).
+template <bool TRANS>
+__global__ void __launch_bounds__(UPD_T, 2) k_gemm64(int M, int N, int K, double alpha,
+                                                     const double* __restrict__ A, int lda,
+                                                     const double* __restrict__ B, int ldb, double beta,
+                                                     double* __restrict__ C, int ldc)
+{
+    extern __shared__ __align__(16) double sm[];
+    constexpr int MR = 4, AS_LD = 32 * MR + 1;
+    double* As = sm;
+    double* Bs = As + KC * AS_LD;
+    const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * TN;
+    const int Mt = min(128, M - m0), mr = (Mt + 31) >> 5;
+    Tile<MR> t;
+    t.zero();
+    gemm_tile<MR, TRANS, false, true>(
+        t, Mt, K, mr,
+        [&](int m, int kk) { return TRANS ? A[kk + (size_t)lda * (m0 + m)] : A[(m0 + m) + (size_t)lda * kk]; },
+        [&](int kk, int j) { return n0 + j < N ? B[kk + (size_t)ldb * (n0 + j)] : 0.0; }, As, Bs, nullptr);
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = ty + 32 * i, jj = tx + 8 * j;
+            if (i < mr && m < Mt && n0 + jj < N) {
+                double* c = C + (m0 + m) + (size_t)ldc * (n0 + jj);
+                *c = beta == 0.0 ? alpha * t.acc[i][j] : fma(alpha, t.acc[i][j], beta * *c);
+            }
+        }
+}
+
+cudaError_t launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int transA,
+                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s)
+{
+    const size_t smem = ((size_t)KC * (32 * 4 + 1) + (size_t)KC * T_LD) * sizeof(double);
+    dim3 grid((M + 127) / 128, (N + TN - 1) / TN);
+    cudaError_t e;
+    if (transA) {
+        if ((e = cudaFuncSetAttribute(k_gemm64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k_gemm64<true><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_gemm64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k_gemm64<false><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
     return cudaGetLastError();
 }
 

@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
         for (int idx = tid; idx < k * k; idx += nt) {
             const int ii = idx % k, jj = idx / k;
             if (ii < jj || ii < my_lo || ii >= my_hi) continue;
-            my_chunk[tri(ii) + jj - ap.sp.base[r]] =
-                a.Ain[pc_pair_map(I, J, b, ii) + (size_t)a.ld * pc_pair_map(I, J, b, jj)];
+            const size_t gi = pc_pair_map(I, J, b, ii) + (size_t)a.ld * pc_pair_map(I, J, b, jj);
+            my_chunk[tri(ii) + jj - ap.sp.base[r]] = a.Ain32 ? (double)a.Ain32[gi] : a.Ain[gi];
         }
     } else {
         const double* g = a.gram + (size_t)e * a.npanels * k * k;
@@ -317,13 +317,15 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
         Vo[(r_lo + i) + (size_t)k * s_dest[j]] = v;
         Vo[(size_t)k * k + s_dest[j] + (size_t)k * (r_lo + i)] = v;
     }
-    if (a.Aout) {
+    if (a.Aout || a.Aout32) {
         for (int idx = tid; idx < k * k; idx += nt) {
             const int ii = idx % k, jj = idx / k;
             const int hi_row = ii >= jj ? ii : jj;
             if (hi_row < my_lo || hi_row >= my_hi) continue;
             const double v = ii == jj ? dhi[ii] : my_chunk[tri(hi_row) + (ii >= jj ? jj : ii) - ap.sp.base[r]];
-            a.Aout[pc_pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pc_pair_map(I, J, b, s_dest[jj])] = v;
+            const size_t g = pc_pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pc_pair_map(I, J, b, s_dest[jj]);
+            if (a.Aout32) a.Aout32[g] = (float)v;
+            else a.Aout[g] = v;
         }
     }
     if (r == 0 && tid == 0) {
