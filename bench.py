@@ -5,17 +5,26 @@ Default workload: plain FP64 two-sided blocked Jacobi EVD of a dense
 symmetric n = 4096 matrix, b = 64, round-robin ordering, eigenvalues plus the
 full eigenvector matrix, stop at off(A) <= 1e-14 ||A||_F.  Input: A = Q diag(lam)
 Q^T, lam ~ U[-1, 1], Q Haar (Householder QR of a seeded Gaussian), seed 2.
+Other workloads (--workload): the n = 256 case, the graded spectrum, the
+one-sided SVD, the mixed-precision form at n = 4096 and n = 8192 (with the
+plain FP64 solve of the same n = 8192 matrix beside it), and the batched forms
+(20000 symmetric matrices, n ~ U{8..512}, FP32 or FP64; 4096 tall 1024 x 64
+FP32 SVDs).
 
-One step = one complete jacobi_syev call (every sweep to convergence plus
-the finalisation) on the resident input.  Prints ONE JSON line (rank 0).
+One step = one complete call (every sweep to convergence plus the
+finalisation) on the resident input: jacobi_syev / jacobi_gesvd for a single
+matrix, one plan execution over the whole batch for the batched forms.
+Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on the same workload
   python bench.py --ncu-case             # a few single steps, for ncu captures
 
 Under torchrun (N > 1) every rank solves its own replica of the workload
-(the single-matrix path has no data-parallel split: replicas only); the
-value is the matrices solved by all ranks over the slowest rank's time.
+(the single-matrix path has no data-parallel split: replicas only; a batch
+is independent problems, so each rank takes a full batch of its own: weak
+scaling with no collective on the data path); the value is the matrices
+solved by all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -38,19 +47,58 @@ METRIC = "Jacobi matrices/s & eff. TFLOP/s: mixed+batched vs plain FP64, same er
 U64 = 2.0 ** -53
 
 # FP64 pipe of GB300: 2 DFMA per clock per SM, 152 SMs, 2070 MHz maximum
-# clock (nominal 1.25 TFLOP/s); a DFMA counts 2 flops.
+# clock (nominal 1.25 TFLOP/s); a DFMA counts 2 flops.  FP32 pipe: 128 FFMA
+# per clock per SM.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_BASIS = ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; "
+              "measured DFMA loop 1.197 TFLOP/s on this pool)")
+FP32_BASIS = "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (FP32 pipe)"
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 WORKLOADS = {
-    "evd4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2,
+    "evd4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, ref_sweeps=13,
                     desc="plain FP64 two-sided block Jacobi EVD, n=4096, b=64, round-robin, "
                          "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
     "evd256": dict(kind="evd", n=256, b=16, spectrum="uniform", seed=1,
                    desc="plain FP64 two-sided block Jacobi EVD, n=256, b=16, round-robin, "
                         "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
+    "evd4096g": dict(kind="evd", n=4096, b=64, spectrum="graded", seed=3, ref_sweeps=13,
+                     desc="plain FP64 two-sided block Jacobi EVD, n=4096, b=64, round-robin, "
+                          "graded lam_i = +-10^(-12 i/(n-1)), eigenvalues + full Q, "
+                          "off(A) <= 1e-14 ||A||_F"),
     "svd16384x2048": dict(kind="svd", m=16384, n=2048, b=64, seed=5,
                           desc="plain FP64 one-sided block Jacobi SVD, 16384 x 2048, b=64, "
                                "sigma_i = 10^(-10 i/(n-1)), U, sigma, V"),
+    "mixed4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=13,
+                      refine_steps=2,
+                      desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
+                           "updates, FP64 pivots, FP64 refinement + closing sweeps), n=4096, "
+                           "b=64, lam ~ U[-1,1], eigenvalues + full Q, off <= 1e-14 ||A||_F"),
+    "mixed8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14,
+                      refine_steps=1,
+                      desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
+                           "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, "
+                           "b=128, lam ~ U[-1,1], eigenvalues + full Q, off <= 1e-14 ||A||_F"),
+    "evd8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, ref_sweeps=14,
+                    desc="plain FP64 two-sided block Jacobi EVD, n=8192, b=128, round-robin, "
+                         "lam ~ U[-1,1], eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
+    "batched_f32": dict(kind="batched_evd", count=20000, lo=8, hi=512, seed=7, f32=True,
+                        desc="batched FP32 EVD: 20000 symmetric (M+M^T)/2, M_ij ~ N(0,1), "
+                             "n ~ U{8..512}, eigenvalues + Q, one plan execution per batch"),
+    "batched_f64": dict(kind="batched_evd", count=20000, lo=8, hi=512, seed=7, f32=False,
+                        desc="batched FP64 EVD: 20000 symmetric (M+M^T)/2, M_ij ~ N(0,1), "
+                             "n ~ U{8..512}, eigenvalues + Q, one plan execution per batch"),
+    "batched_svd_f32": dict(kind="batched_svd", count=4096, m=1024, n=64, seed=7, f32=True,
+                            desc="batched FP32 one-sided Jacobi SVD: 4096 tall 1024 x 64, "
+                                 "G_ij ~ N(0,1), U, sigma, V, one plan execution per batch"),
 }
 
 
@@ -232,9 +280,41 @@ def cpu_baseline(wl, sweeps: int, budget_s: float = 12.0):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def run_reference_batched(args, wl):
+    shapes = batch_shapes(wl)
+    B = len(shapes)
+    mats = batched_host_sample(wl, shapes, 256)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=6.0)
+        mats = mats[done:] + mats[:done]  # the next step starts where this one ended
+        rates.append(secs / frac)
+    t_batch = sum(rates[args.warmup:]) / args.steps
+    value = B / t_batch
+    evd = wl["kind"] == "batched_evd"
+    sample = (f"each step = the FP64 oracle (scalar parallel-ordered Jacobi per matrix, one "
+              f"thread) on consecutive matrices of the batch for 6 s, extrapolated by "
+              f"{'n^3' if evd else 'm n^2'} work to all {B} matrices")
+    return value, 1e3 * t_batch, sample
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
+        return 0
+    if wl["kind"] in ("batched_evd", "batched_svd"):
+        value, ms_step, sample = run_reference_batched(args, wl)
+        cores = len(os.sched_getaffinity(0))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["desc"]},
+                "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
         return 0
     sweeps = wl.get("ref_sweeps", 9)
     times, S = cpu_oracle_sample(wl, sweeps, budget_s=1e9, max_steps=args.warmup + args.steps)
@@ -258,7 +338,59 @@ def run_reference(args, wl):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def padded_np(n, b):
+    N = (n + b - 1) // b
+    N += N & 1
+    return N * b
+
+
+def evd_kernel_classes(stats, wl, peaks):
+    """Device time, launches and issued flops per kernel class of the
+    two-sided solve (summed over the timed steps), each with its roofline."""
+    b = wl["b"]
+    npd = padded_np(wl["n"], b)
+    S = npd // b - 1
+    lowp_steps = sum(st.sweeps_lowp for st in stats) * S
+    tot = lambda f: sum(getattr(st, f) for st in stats)
+    bf16 = peaks.get("bf16_tflops_sustained")
+    cls = {
+        "pivot": dict(kernel="k_pivot / k_pivot_cluster", ms=tot("ms_pivot"),
+                      launches=tot("pivot_launches"),
+                      flops=tot("flops_fp64") - tot("flops_update") - tot("flops_refine"),
+                      bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS),
+        "update_fp64": dict(kernel="k_update_evd", ms=tot("ms_update") - tot("ms_update_lowp"),
+                            launches=tot("update_launches") - 2 * lowp_steps,
+                            flops=tot("flops_update"), bound="alu", peak=FP64_PEAK_TFLOPS,
+                            peak_basis=FP64_BASIS),
+    }
+    if tot("sweeps_lowp") > 0:
+        cls["update_lowp"] = dict(kernel="k_tc_upd1 + k_tc_upd2 (tcgen05)", ms=tot("ms_update_lowp"),
+                                  launches=2 * lowp_steps, flops=tot("flops_lowp"), bound="tensor",
+                                  peak=bf16, peak_basis="measured bf16 dense, sustained "
+                                  "(MEASURED_PEAKS.json); flops = the three bf16 products issued")
+        cls["refine"] = dict(kernel="k_gemm64 (+ elementwise)", ms=tot("ms_refine"),
+                             launches=None, flops=tot("flops_refine"), bound="alu",
+                             peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS)
+    for c in cls.values():
+        c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
+        c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
+        c["unit"] = "TFLOP/s"
+    if "update_lowp" in cls:
+        # HBM view of the tensor-core update: per step A, Q (FP32) read and
+        # written once, the stage-1 products T written and read once
+        k = 2 * b
+        P = npd // k
+        per_step = 4 * (4 * npd * npd) + 2 * 4 * (P * (P - 1) // 2) * k * k
+        c = cls["update_lowp"]
+        c["hbm_bytes_per_step"] = per_step
+        c["hbm_gbs"] = per_step * lowp_steps / (c["ms"] / 1e3) / 1e9 if c["ms"] > 0 else None
+        c["hbm_peak_gbs"] = peaks.get("hbm_gbs")
+    return cls
+
+
 def run_gpu(args, wl):
+    if wl["kind"] in ("batched_evd", "batched_svd"):
+        return run_batched(args, wl)
     import numpy as np
     import torch
 
@@ -271,10 +403,13 @@ def run_gpu(args, wl):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     jg.lib()
+    peaks = measured_peaks()
     stream = torch.cuda.current_stream(dev)
     X, ref = make_input(wl)
     b = wl["b"]
-    p = jg.params(b=b, inner_max_sweeps=args.inner_max_sweeps)
+    prec = wl.get("precision", 0)
+    extra = {"refine_steps": wl["refine_steps"]} if "refine_steps" in wl else {}
+    p = jg.params(b=b, inner_max_sweeps=args.inner_max_sweeps, precision=prec, **extra)
     Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
     Wd = torch.empty_like(Xd.t()).t()  # column-major work copy
     if wl["kind"] == "evd":
@@ -299,14 +434,7 @@ def run_gpu(args, wl):
         step()
     torch.cuda.synchronize(dev)
     barrier(world)
-    gpu_id = None
-    try:
-        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
-        if not gpu_id.startswith("GPU-"):
-            gpu_id = "GPU-" + gpu_id
-    except Exception:
-        gpu_id = None
-    sampler = ClockSampler(gpu_id)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -327,6 +455,8 @@ def run_gpu(args, wl):
         w = out.cpu().numpy()
         lam = np.sort(ref)
         acc["max_abs_eig_err_over_norm2"] = float(np.abs(w - lam).max() / np.abs(lam).max())
+        big = np.abs(lam) >= 1e-3 * np.abs(lam).max()
+        acc["max_rel_eig_err_abs_ge_1e-3"] = float((np.abs(w - lam)[big] / np.abs(lam[big])).max())
         A64 = torch.from_numpy(np.asarray(X)).to(dev)
         R = A64 @ V - V * out[None, :]
         acc["residual_fro_over_normA"] = float(torch.linalg.norm(R) / torch.linalg.norm(A64))
@@ -341,26 +471,38 @@ def run_gpu(args, wl):
 
     sweeps = stats[-1].sweeps
     flops_issued = sum(st.flops_fp64 for st in stats)
-    ms_update = sum(st.ms_update for st in stats)
-    ms_pivot = sum(st.ms_pivot for st in stats)
-    n_upd = sum(st.update_launches for st in stats)
-    n_piv = sum(st.pivot_launches for st in stats)
     launches = int(sum(st.launches for st in stats))
 
-    # roofline of the dominant kernel (FP64 pipe: plain ALU arithmetic)
-    kernels = {"update": {"ms": ms_update, "launches": n_upd},
-               "pivot": {"ms": ms_pivot, "launches": n_piv}}
-    upd_flops = sum(st.flops_update for st in stats)
+    # roofline of the dominant kernel class
     if wl["kind"] == "evd":
-        npd = ((wl["n"] + b - 1) // b + 1) // 2 * 2 * b
-        alg = evd_update_flops(npd, b)
-        avg_ms = ms_update / max(n_upd, 1)
-        # issued work: pair-blocks whose two pivots did not rotate are copies
-        alg_issued = upd_flops / max(n_upd, 1)
-        achieved = alg_issued / (avg_ms / 1e3) / 1e12
-        traffic, prof = profile_traffic("update_evd_n4096_b64") if wl["n"] == 4096 else (None, None)
-        kname = "k_update_evd"
+        kernels = evd_kernel_classes(stats, wl, peaks)
+        dom = max(kernels, key=lambda c: kernels[c]["ms"])
+        kc = kernels[dom]
+        if dom in ("update_fp64", "pivot") and kc["launches"]:
+            avg_ms = kc["ms"] / kc["launches"]
+            per_launch = kc["flops"] / kc["launches"]
+        else:
+            avg_ms, per_launch = kc["ms"], kc["flops"]
+        npd = padded_np(wl["n"], b)
+        prof_name = {"update_fp64": f"update_evd_n{wl['n']}_b{b}",
+                     "pivot": f"pivot_n{wl['n']}_b{b}",
+                     "refine": f"gemm64_n{wl['n']}",
+                     "update_lowp": f"tc_update_n{wl['n']}_b{b}"}[dom]
+        traffic, prof = profile_traffic(prof_name)
+        roofline = {"kernel": kc["kernel"], "class": dom, "bound": kc["bound"],
+                    "achieved": kc["achieved"], "peak": kc["peak"], "unit": "TFLOP/s",
+                    "frac": kc["frac"], "traffic": traffic, "peak_basis": kc["peak_basis"],
+                    "flops_per_launch_issued": per_launch, "avg_launch_ms": avg_ms,
+                    "alg_update_flops_per_step_full": evd_update_flops(npd, b),
+                    "share_of_step": kc["ms"] / ms if ms else None,
+                    "profile": os.path.relpath(prof, ROOT) if prof else None}
     else:
+        ms_update = sum(st.ms_update for st in stats)
+        n_upd = sum(st.update_launches for st in stats)
+        upd_flops = sum(st.flops_update for st in stats)
+        kernels = {"update": {"ms": ms_update, "launches": n_upd},
+                   "pivot": {"ms": sum(st.ms_pivot for st in stats),
+                             "launches": sum(st.pivot_launches for st in stats)}}
         m, n_ = wl["m"], wl["n"]
         k = 2 * b
         P = ((n_ + b - 1) // b + 1) // 2
@@ -370,17 +512,12 @@ def run_gpu(args, wl):
         avg_ms = ms_update / max(n_upd // 2, 1)
         alg_issued = upd_flops / max(n_upd // 2, 1)
         achieved = alg_issued / (avg_ms / 1e3) / 1e12
-        traffic, prof = (None, None)
-        kname = "k_gram + k_update_cols"
-    sm_mhz = clocks.get("sm_mhz")
-    roofline = {"kernel": kname, "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic,
-                "peak_basis": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; "
-                              "measured DFMA loop 1.197 TFLOP/s on this pool)",
-                "alg_flops_per_launch_full": alg, "flops_per_launch_issued": alg_issued,
-                "avg_launch_ms": avg_ms,
-                "share_of_step": ms_update / ms if ms else None}
+        roofline = {"kernel": "k_gram + k_update_cols", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_basis": FP64_BASIS, "alg_flops_per_launch_full": alg,
+                    "flops_per_launch_issued": alg_issued, "avg_launch_ms": avg_ms,
+                    "share_of_step": ms_update / ms if ms else None}
 
     # end to end: the same calls with host buffers, copies inside the timing
     e2e = None
@@ -414,20 +551,29 @@ def run_gpu(args, wl):
         cpu = cpu_baseline(wl, sweeps)
 
     if rank == 0:
+        st = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == 0 else "bf16x3+f32+f64",
                 "data": "synthetic (seeded; see config)",
                 "config": {"workload": wl["desc"], "b": b,
                            "n": wl["n"], **({"m": wl["m"]} if "m" in wl else {}),
                            "seed": wl["seed"], "parallelism": f"replicas x{world}",
+                           **({"precision": "mixed bf16x3", "refine_steps": wl.get("refine_steps")}
+                              if prec else {}),
                            "l2": "inputs larger than L2 (working A, Q double-buffered: "
                                  "4 x n^2 x 8 B)"},
-                "eff_tflops_issued": flops_issued / (sum(st.ms_total for st in stats) / 1e3) / 1e12,
-                "sweeps": sweeps, "inner_max_sweeps": args.inner_max_sweeps,
-                "pivot_stats": {"pair_solves": stats[-1].pair_solves,
-                                "inner_sweeps_per_solve": stats[-1].inner_sweeps / max(1, stats[-1].pair_solves),
-                                "rotations": stats[-1].rotations},
+                "eff_tflops_issued": (sum(st_.flops_fp64 + st_.flops_lowp for st_ in stats)
+                                      / (sum(st_.ms_total for st_ in stats) / 1e3) / 1e12),
+                "sweeps": sweeps, "sweeps_lowp": st.sweeps_lowp,
+                "inner_max_sweeps": args.inner_max_sweeps,
+                "phases_ms_last_step": {"lowp": st.ms_lowp, "refine": st.ms_refine,
+                                        "pivot": st.ms_pivot, "update": st.ms_update,
+                                        "total": st.ms_total},
+                "pivot_stats": {"pair_solves": st.pair_solves,
+                                "inner_sweeps_per_solve": st.inner_sweeps / max(1, st.pair_solves),
+                                "rotations": st.rotations},
                 "accuracy": acc, "kernels": kernels,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
@@ -439,19 +585,255 @@ def run_gpu(args, wl):
     return 0
 
 
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- batched forms
+def batch_shapes(wl):
+    import jacobi_inputs as gen
+    if wl["kind"] == "batched_evd":
+        return [(int(n), int(n)) for n in gen.batch_sizes(wl["count"], wl["lo"], wl["hi"], wl["seed"])]
+    return [(wl["m"], wl["n"])] * wl["count"]
+
+
+def batched_cpu_sample(wl, shapes, mats_host, budget_s: float, max_items: int | None = None):
+    """The oracle on consecutive matrices of the batch (LPT order is not
+    used: matrices are taken as listed) until budget_s has passed.  Returns
+    (seconds, matrices done, work done / work of the whole batch)."""
+    import numpy as np
+    import oracle
+    evd = wl["kind"] == "batched_evd"
+    work = lambda mn: mn[1] ** 3 if evd else mn[0] * mn[1] ** 2
+    total_work = sum(work(x) for x in shapes)
+    t0, done, w = time.perf_counter(), 0, 0
+    for i, A in enumerate(mats_host):
+        if evd:
+            n = A.shape[0]
+            k = n + (n & 1)
+            Ap = np.zeros((k, k))
+            Ap[:n, :n] = A
+            oracle.pivot_solve(Ap)
+        else:
+            n = A.shape[1]
+            oracle.gesvd(A, b=max(1, n // 2))
+        done += 1
+        w += work(shapes[i])
+        if time.perf_counter() - t0 >= budget_s or (max_items and done >= max_items):
+            break
+    return time.perf_counter() - t0, done, w / total_work
+
+
+def batched_host_sample(wl, shapes, count: int):
+    """The first `count` matrices of the batch as float64 numpy arrays.  They
+    are drawn on the CUDA device when there is one, which reproduces the GPU
+    run's matrices exactly (same seeded generator, same draws); without a
+    GPU, torch's CPU generator gives other draws of the same distribution."""
+    import torch
+    import jacobi_inputs as gen
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    flat, views, _ = gen.batch_flat_torch(shapes[:count], wl["seed"], dev, torch.float64,
+                                          symmetric=wl["kind"] == "batched_evd")
+    out = [v.cpu().numpy() for v in views]
+    del flat, views
+    return out
+
+
+def run_batched(args, wl):
+    import numpy as np
+    import torch
+
+    import jacobi_inputs as gen
+    import paper_2608_28952_gb300 as jg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    jg.lib()
+    stream = torch.cuda.current_stream(dev)
+    evd = wl["kind"] == "batched_evd"
+    dtype = torch.float32 if wl["f32"] else torch.float64
+    shapes = batch_shapes(wl)
+    B = len(shapes)
+    flat0, views0, offs = gen.batch_flat_torch(shapes, wl["seed"], dev, dtype, symmetric=evd)
+    flat = flat0.clone()
+    X = [flat[o:o + m * n].view(n, m).t() for (m, n), o in zip(shapes, offs)]
+    ncols = [n for _, n in shapes]
+    y_off = np.concatenate([[0], np.cumsum(ncols)]).astype(np.int64)
+    z_off = np.concatenate([[0], np.cumsum([n * n for n in ncols])]).astype(np.int64)
+    yflat = torch.empty(int(y_off[-1]), dtype=dtype, device=dev)
+    zflat = torch.empty(int(z_off[-1]), dtype=dtype, device=dev)
+    Y = [yflat[int(y_off[i]):int(y_off[i + 1])] for i in range(B)]
+    Z = [zflat[int(z_off[i]):int(z_off[i + 1])].view(n, n).t() for i, n in enumerate(ncols)]
+    info = torch.full((B,), -7, dtype=torch.int32, device=dev)
+    prec = jg.PREC_FP32 if wl["f32"] else jg.PREC_FP64
+    plan = jg.Plan(0 if evd else 1, prec, ncols, m=None if evd else [m for m, _ in shapes],
+                   p=jg.params(), stream=stream)
+    t0 = time.perf_counter()
+    if wl["f32"] and evd:
+        plan.autotune(X, Y, Z, info, stream)
+    tune_s = time.perf_counter() - t0
+    shape = plan.shape()
+
+    def step():
+        flat.copy_(flat0)
+        rc, st = plan.execute(X, Y, Z, info, stream)
+        if rc != 0:
+            raise RuntimeError(f"status {rc} ({jg.status_string(rc)})")
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if int((info != 0).sum()) != 0:
+        raise RuntimeError(f"{int((info != 0).sum())} matrices did not converge")
+    barrier(world)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = aggregate_max(ms, world, dev)
+    total = aggregate_sum(float(args.steps * B), world, dev)
+    value = total / (ms_max / 1e3)
+    bad = int((info != 0).sum())
+
+    # accuracy on a spread sample (LAPACK on the host as the witness)
+    acc = {"matrices_not_converged": bad}
+    idx = list(range(0, B, max(1, B // 16)))[:16]
+    e_eig = e_res = e_orth = 0.0
+    for i in idx:
+        A = views0[i].double().cpu().numpy()
+        y = Y[i].double().cpu().numpy()
+        Zi = Z[i].double().cpu().numpy()
+        n = A.shape[1]
+        if evd:
+            ref = np.linalg.eigvalsh(A)
+            e_eig = max(e_eig, float(np.abs(y - ref).max() / max(np.abs(ref).max(), 1e-300)))
+            e_res = max(e_res, float(np.linalg.norm(A @ Zi - Zi * y[None, :]) / np.linalg.norm(A)))
+        else:
+            ref = np.linalg.svd(A, compute_uv=False)
+            e_eig = max(e_eig, float(np.abs(y - ref).max() / ref[0]))
+            U = X[i].double().cpu().numpy()
+            e_res = max(e_res, float(np.linalg.norm(A @ Zi - U * y[None, :]) / np.linalg.norm(A)))
+        e_orth = max(e_orth, float(np.linalg.norm(Zi.T @ Zi - np.eye(n)) / n))
+    acc.update({"sample": len(idx), "max_abs_err_over_norm2": e_eig,
+                "max_residual_fro_over_normA": e_res, "max_orth_fro_over_n": e_orth,
+                "witness": "numpy.linalg (LAPACK) on the sampled matrices"})
+
+    st = stats[-1]
+    f_issued = (st.flops_fp32 if wl["f32"] else st.flops_fp64)
+    peak = FP32_PEAK_TFLOPS if wl["f32"] else FP64_PEAK_TFLOPS
+    achieved = f_issued / (st.ms_total / 1e3) / 1e12
+    kname = "k_batched_evd" if evd else "k_batched_svd"
+    traffic, prof = profile_traffic(f"{kname}_{'f32' if wl['f32'] else 'f64'}_{B}")
+    roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_basis": FP32_BASIS if wl["f32"] else FP64_BASIS,
+                "flops_per_launch_issued": f_issued, "avg_launch_ms": st.ms_total,
+                "launches_per_step": st.launches,
+                "profile": os.path.relpath(prof, ROOT) if prof else None}
+
+    e2e = None
+    if args.e2e_steps > 0:
+        hx = flat0.cpu().pin_memory()
+        hy = torch.empty_like(yflat, device="cpu").pin_memory()
+        hz = torch.empty_like(zflat, device="cpu").pin_memory()
+        hu = torch.empty_like(flat, device="cpu").pin_memory() if not evd else None
+        tt = 0.0
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            flat.copy_(hx, non_blocking=True)
+            rc, _ = plan.execute(X, Y, Z, info, stream)
+            hy.copy_(yflat, non_blocking=True)
+            hz.copy_(zflat, non_blocking=True)
+            if hu is not None:
+                hu.copy_(flat, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            if rc != 0:
+                raise RuntimeError(f"e2e status {rc}")
+            if i > 0:
+                tt += t1 - t0
+        tt_max = aggregate_max(tt, world, dev)
+        e_total = aggregate_sum(float(args.e2e_steps * B), world, dev)
+        esz = flat.element_size()
+        e2e = {"value": e_total / tt_max, "unit": "matrices/s",
+               "h2d_bytes_per_step": flat.numel() * esz,
+               "d2h_bytes_per_step": (yflat.numel() + zflat.numel()
+                                      + (flat.numel() if hu is not None else 0)) * esz,
+               "steps": args.e2e_steps,
+               "timing": "wall clock: pinned host -> device copy of the batch, plan "
+                         "execution, device -> pinned host copy of the results"}
+        del hx, hy, hz, hu
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mats = batched_host_sample(wl, shapes, 64)
+        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=12.0)
+        cpu = {"value": B / (secs / frac), "unit": "matrices/s",
+               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"the first {done} matrices of the batch ({frac:.2e} of its "
+                         f"{'n^3' if evd else 'm n^2'} work), {secs:.1f} s, extrapolated "
+                         f"by work to all {B}; FP64 oracle (scalar parallel-ordered "
+                         f"Jacobi per matrix), one thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if wl["f32"] else "f64", "data": "synthetic (seeded; see config)",
+                "config": {"workload": wl["desc"], "count": B, "seed": wl["seed"],
+                           **({"n_range": [wl["lo"], wl["hi"]]} if evd else
+                              {"m": wl["m"], "n": wl["n"]}),
+                           "plan_shape": {"threads": shape[0], "smem_kmax": shape[1],
+                                          "grid": shape[2]},
+                           "autotune_s": tune_s, "parallelism": f"one batch per rank x{world}",
+                           "l2": "inputs larger than L2 (the batch: "
+                                 f"{flat.numel() * flat.element_size() / 1e9:.1f} GB)"},
+                "eff_tflops_issued": achieved, "accuracy": acc,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(s_.launches for s_ in stats)), "clocks": clocks,
+                "source_sha256": source_hash()}
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ncu_case(args, wl):
-    """A handful of single steps of the workload (for ncu captures)."""
+    """A handful of single steps of the workload (for ncu captures): FP64
+    steps, or low-precision steps for the mixed workloads."""
     import torch
 
     import paper_2608_28952_gb300 as jg
     X, _ = make_input(wl)
     dev = torch.device("cuda", 0)
-    Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
-    Qd = jg.colmajor(torch.eye(X.shape[0], dtype=torch.float64), device=dev)
-    p = jg.params(b=wl["b"])
+    mixed = wl.get("precision", 0) != 0
+    dt = torch.float32 if mixed else torch.float64
+    Xd = jg.colmajor(X, device=dev, dtype=dt)
+    Qd = jg.colmajor(torch.eye(X.shape[0], dtype=dt), device=dev)
+    p = jg.params(b=wl["b"], precision=wl.get("precision", 0))
     for s in range(args.warmup + args.steps):
         if wl["kind"] == "evd":
-            rc = jg.jacobi_syev_step(Xd, Qd, s % (X.shape[0] // wl["b"] - 1), p)
+            f = jg.jacobi_syev_step_lowp if mixed else jg.jacobi_syev_step
+            rc = f(Xd, Qd, s % (X.shape[0] // wl["b"] - 1), p)
         else:
             rc, _ = jg.jacobi_gesvd_step(Xd, None, s % (X.shape[1] // wl["b"] - 1), p)
         assert rc == 0, rc

@@ -14,6 +14,9 @@ Recipes (seed per workload is fixed by the caller):
   * ``sym_gaussian(n)``           (M + M^T)/2, M_ij ~ N(0, 1)
   * ``batch_sizes(count, lo, hi)``n ~ U{lo..hi} (inclusive)
   * ``tall_gaussian(m, n)``       G_ij ~ N(0, 1)
+  * ``batch_flat_torch(...)``     the batched workloads drawn on the device (torch's
+                                   Philox generator, seeded): many matrices packed
+                                   into one flat column-major buffer
 Q, U, V come from the Householder QR of a seeded N(0,1) matrix with the signs
 fixed so that diag(R) > 0.
 """
@@ -102,3 +105,28 @@ def batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
 
 def tall_gaussian(m: int, n: int, seed: int, *more, dtype=np.float32) -> np.ndarray:
     return np.asfortranarray(rng(seed, *more).standard_normal((m, n)).astype(dtype))
+
+
+def batch_flat_torch(shapes, seed: int, device, dtype, symmetric: bool = True):
+    """Many matrices drawn on the device, packed into one flat buffer.
+
+    shapes: list of (m, n).  Each matrix is M_ij ~ N(0, 1) (torch's seeded
+    device generator), symmetrised as (M + M^T)/2 when ``symmetric`` (m == n).
+    Returns (flat, views, offsets): ``views[i]`` is matrix i as a column-major
+    (m, n) view into ``flat`` (leading dimension m), offsets in elements.
+    Drawn in float64 and rounded once to ``dtype``."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    offs, tot = [], 0
+    for m, n in shapes:
+        offs.append(tot)
+        tot += m * n
+    flat = torch.empty(tot, dtype=dtype, device=device)
+    views = []
+    for (m, n), o in zip(shapes, offs):
+        M = torch.randn(n, m, generator=g, device=device, dtype=torch.float64)  # row-major n x m = col-major m x n
+        if symmetric and m == n:
+            M = 0.5 * (M + M.t())
+        flat[o:o + m * n].copy_(M.reshape(-1))
+        views.append(flat[o:o + m * n].view(n, m).t())
+    return flat, views, offs

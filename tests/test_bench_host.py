@@ -1,0 +1,121 @@
+"""Host-side logic of bench.py: the cross-rank aggregation of the N-GPU
+launch (run here as two gloo ranks on the CPU), the workload table, the
+algorithmic work counts and the kernel-class roofline bookkeeping."""
+from __future__ import annotations
+
+import os
+import socket
+import sys
+from types import SimpleNamespace
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # each rank measured its own replica: time differs, matrices add up
+    t = bench.aggregate_max(10.0 + rank, world)
+    n = bench.aggregate_sum(3.0, world)
+    bench.barrier(world)
+    dist.destroy_process_group()
+    q.put((rank, t, n))
+
+
+def test_aggregation_over_two_gloo_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # every rank sees the slowest rank's time and the total work
+    assert out == [(0, 11.0, 6.0), (1, 11.0, 6.0)]
+
+
+def test_single_rank_aggregation_is_identity():
+    assert bench.aggregate_max(2.5, 1) == 2.5
+    assert bench.aggregate_sum(4.0, 1) == 4.0
+
+
+def test_workloads_are_complete():
+    for name, wl in bench.WORKLOADS.items():
+        assert wl["kind"] in ("evd", "svd", "batched_evd", "batched_svd"), name
+        assert "desc" in wl and "seed" in wl
+    # the five configurations of the workload description are all present
+    assert bench.WORKLOADS["evd256"]["n"] == 256 and bench.WORKLOADS["evd256"]["b"] == 16
+    assert bench.WORKLOADS["evd4096"]["n"] == 4096 and bench.WORKLOADS["evd4096"]["b"] == 64
+    assert bench.WORKLOADS["svd16384x2048"]["m"] == 16384
+    assert bench.WORKLOADS["mixed8192"]["n"] == 8192 and bench.WORKLOADS["mixed8192"]["b"] == 128
+    assert bench.WORKLOADS["batched_f64"]["count"] == 20000
+    assert bench.WORKLOADS["batched_svd_f32"]["count"] == 4096
+
+
+def test_padding_and_update_flops():
+    assert bench.padded_np(4096, 64) == 4096
+    assert bench.padded_np(100, 16) == 128       # 7 blocks -> 8
+    assert bench.padded_np(96, 16) == 96
+    # one step at np = 4096, b = 64: 32 pairs, 496 pair-blocks of 4 k^3 plus Q
+    k = 128
+    assert bench.evd_update_flops(4096, 64) == 496 * 4 * k ** 3 + 32 * 2 * 4096 * k * k
+
+
+def _stats(**kw):
+    base = dict(sweeps_lowp=0, ms_pivot=0.0, pivot_launches=0, flops_fp64=0.0, flops_update=0.0,
+                flops_refine=0.0, ms_update=0.0, ms_update_lowp=0.0, update_launches=0,
+                flops_lowp=0.0, ms_refine=0.0)
+    base.update(kw)
+    return SimpleNamespace(**base)
+
+
+def test_kernel_classes_plain_fp64():
+    wl = dict(n=4096, b=64)
+    st = _stats(ms_pivot=1000.0, pivot_launches=819, flops_fp64=8e12, flops_update=7e12,
+                ms_update=5500.0, update_launches=819)
+    cls = bench.evd_kernel_classes([st], wl, {})
+    assert set(cls) == {"pivot", "update_fp64"}
+    assert cls["update_fp64"]["launches"] == 819
+    assert cls["update_fp64"]["achieved"] == pytest.approx(7e12 / 5.5 / 1e12)
+    assert cls["pivot"]["flops"] == pytest.approx(1e12)
+
+
+def test_kernel_classes_mixed_split_the_phases():
+    wl = dict(n=4096, b=64)
+    S = 63
+    st = _stats(sweeps_lowp=11, ms_pivot=1100.0, pivot_launches=13 * S, flops_fp64=2.5e12,
+                flops_update=1.0e12, flops_refine=1.2e12, ms_update=1300.0, ms_update_lowp=500.0,
+                update_launches=2 * 11 * S + 2 * S, flops_lowp=1.75e13, ms_refine=1000.0)
+    cls = bench.evd_kernel_classes([st], wl, {"bf16_tflops_sustained": 1688.5, "hbm_gbs": 6777.0})
+    assert cls["update_lowp"]["launches"] == 2 * 11 * S
+    assert cls["update_fp64"]["launches"] == 2 * S
+    assert cls["update_fp64"]["ms"] == pytest.approx(800.0)
+    assert cls["update_lowp"]["bound"] == "tensor" and cls["update_lowp"]["peak"] == 1688.5
+    assert cls["pivot"]["flops"] == pytest.approx(2.5e12 - 1.0e12 - 1.2e12)
+    assert cls["update_lowp"]["hbm_gbs"] > 0
+
+
+def test_batch_shapes_follow_the_recipe():
+    wl = bench.WORKLOADS["batched_f32"]
+    sh = bench.batch_shapes(wl)
+    assert len(sh) == 20000 and all(m == n and 8 <= n <= 512 for m, n in sh)
+    sv = bench.batch_shapes(bench.WORKLOADS["batched_svd_f32"])
+    assert sv == [(1024, 64)] * 4096
