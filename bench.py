@@ -359,13 +359,13 @@ def evd_kernel_classes(stats, wl, peaks):
                       flops=tot("flops_fp64") - tot("flops_update") - tot("flops_refine"),
                       bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS),
         "update_fp64": dict(kernel="k_update_evd", ms=tot("ms_update") - tot("ms_update_lowp"),
-                            launches=tot("update_launches") - 2 * lowp_steps,
+                            launches=tot("update_launches") - 3 * lowp_steps,
                             flops=tot("flops_update"), bound="alu", peak=FP64_PEAK_TFLOPS,
                             peak_basis=FP64_BASIS),
     }
     if tot("sweeps_lowp") > 0:
-        cls["update_lowp"] = dict(kernel="k_tc_upd1 + k_tc_upd2 (tcgen05)", ms=tot("ms_update_lowp"),
-                                  launches=2 * lowp_steps, flops=tot("flops_lowp"), bound="tensor",
+        cls["update_lowp"] = dict(kernel="k_tc_split_v + k_tc_upd1 + k_tc_upd2 (tcgen05)",
+                                  ms=tot("ms_update_lowp"), launches=3 * lowp_steps, flops=tot("flops_lowp"), bound="tensor",
                                   peak=bf16, peak_basis="measured bf16 dense, sustained "
                                   "(MEASURED_PEAKS.json); flops = the three bf16 products issued")
         cls["refine"] = dict(kernel="k_gemm64 (+ elementwise)", ms=tot("ms_refine"),

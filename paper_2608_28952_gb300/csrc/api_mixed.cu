@@ -39,6 +39,7 @@ struct LowpState {
     float* Aw[2];
     float* Qw[2];
     float* T;
+    unsigned char* vimg;
     double* Vb;
     int* rot;
     double* gscratch;
@@ -81,6 +82,7 @@ cudaError_t launch_step32(const LowpState& L, int s, int cur, cudaStream_t cs, d
     ua.ldq = L.np;
     ua.qrows = L.np;
     ua.T = L.T;
+    ua.vimg = L.vimg;
     ua.pairs = L.dpairs + p0;
     ua.npairs = nps;
     ua.b = L.b;
@@ -100,6 +102,9 @@ int run_lowp_sweeps(LowpState& L, const jacobi_params& p, int& cur, double targe
     SweepGraph graphs[2];
     bool tried[2] = {false, false}, have[2] = {false, false};
     PhaseEvents pe(2 * (size_t)L.ord->S + 1);
+    // A rotation whose a_pq is below the FP32 rounding of the pivot's diagonal
+    // changes nothing the FP32 working copy can hold: skip it in this phase.
+    const double inner_tol = p.inner_tol > U32 ? p.inner_tol : U32;
     double prev = INFINITY;
     int sw = 0;
     for (; sw < p.max_sweeps; ++sw) {
@@ -108,7 +113,7 @@ int run_lowp_sweeps(LowpState& L, const jacobi_params& p, int& cur, double targe
             int c = start;
             if (cudaEventRecordWithFlags(pe.ev[0], cs, cudaEventRecordExternal) != cudaSuccess) return false;
             for (int si = 0; si < L.ord->S; ++si) {
-                if (launch_step32(L, si, c, cs, p.inner_tol, p.inner_max_sweeps, p.pivot_order,
+                if (launch_step32(L, si, c, cs, inner_tol, p.inner_max_sweeps, p.pivot_order,
                                   pe.ev[2 * si + 1]) != cudaSuccess)
                     return false;
                 if (cudaEventRecordWithFlags(pe.ev[2 * si + 2], cs, cudaEventRecordExternal) != cudaSuccess)
@@ -136,13 +141,16 @@ int run_lowp_sweeps(LowpState& L, const jacobi_params& p, int& cur, double targe
         if (h_err) return JACOBI_ERR_TIMEOUT;
         st->steps += L.ord->S;
         for (int si = 0; si < L.ord->S; ++si) {
-            st->ms_pivot += pe.ms(2 * si, 2 * si + 1);
-            st->ms_update += pe.ms(2 * si + 1, 2 * si + 2);
+            const double tp = pe.ms(2 * si, 2 * si + 1), tu = pe.ms(2 * si + 1, 2 * si + 2);
+            st->ms_pivot += tp;
+            st->ms_update += tu;
+            st->ms_pivot_lowp += tp;
+            st->ms_update_lowp += tu;
         }
-        // pivot + two tensor-core stages per step, one off-norm per sweep
-        st->launches += 3 * L.ord->S + 1;
+        // pivot, V split and two tensor-core stages per step, one off-norm per sweep
+        st->launches += 4 * L.ord->S + 1;
         st->pivot_launches += L.ord->S;
-        st->update_launches += 2 * L.ord->S;
+        st->update_launches += 3 * L.ord->S;
         const double off = sqrt(h_res[0]);
         if (sw < 64) st->off_hist[sw] = off;
         st->off_final = off;
@@ -211,6 +219,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.Qw[0] = ws.get<float>(np2);
     L.Qw[1] = ws.get<float>(np2);
     L.T = ws.get<float>(tc_update_tbuf_floats(E.ord.dev_per_step, k));
+    L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(E.ord.dev_per_step, k));
     L.err = ws.get<int>(1);
     if (ws.failed) return JACOBI_ERR_ALLOC;
     L.pcl = E.pcl;
@@ -275,29 +284,39 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         double* W = E.Aw[1];
         bool ok = launch_f32_to_f64((long long)np2, L.Qw[c32], X, s) == cudaSuccess;
         st->launches += 1;
-        const double nn = (double)np;
+        const double nn = (double)np, n3 = nn * nn * nn;
+        // X^T B for a symmetric result: the tiles meeting the lower triangle,
+        // then mirrored (about half the flops of the full product)
+        auto sym_xtb = [&](const double* B, double* out) {
+            return launch_gemm64(np, np, np, 1.0, X, np, 1, B, np, 0.0, out, np, s, 1) == cudaSuccess &&
+                   launch_mirror_lower(np, out, np, s) == cudaSuccess;
+        };
+        const double sym_flops = n3 + 2.0 * nn * nn * 128.0;  // lower tiles incl. the diagonal band
+        double fl = 0.0;
         for (int it = 0; ok && it < p.refine_steps; ++it) {
-            ok = launch_gemm64(np, np, np, 1.0, X, np, 1, X, np, 0.0, G, np, s) == cudaSuccess &&
+            ok = sym_xtb(X, G) &&
                  launch_gemm64(np, np, np, 1.0, A0p, np, 0, X, np, 0.0, W, np, s) == cudaSuccess &&
-                 launch_gemm64(np, np, np, 1.0, X, np, 1, W, np, 0.0, Xn, np, s) == cudaSuccess &&
+                 sym_xtb(W, Xn) &&
                  // Xn holds S now; E overwrites G
                  launch_oa_step_elementwise(np, Xn, G, lam, 1e-2, s) == cudaSuccess &&
                  cudaMemcpyAsync(Xn, X, np2 * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
                  launch_gemm64(np, np, np, 1.0, X, np, 0, G, np, 1.0, Xn, np, s) == cudaSuccess;
             std::swap(X, Xn);
-            st->flops_fp64 += 8.0 * nn * nn * nn;
-            st->launches += 6;
+            fl += 2.0 * sym_flops + 4.0 * n3;
+            st->launches += 8;
         }
-        // Newton-Schulz until ||I - X^T X||_F reaches the rounding level
+        // Newton-Schulz, X <- X + X (I - X^T X) / 2, until ||I - X^T X||_F
+        // reaches the rounding level.  A step maps r = ||I - X^T X|| to about
+        // 3 r^2 / 4, so once that prediction is below the goal the step is
+        // taken without forming X^T X again.
         const double orth_goal = 8.0 * U64 * sqrt(nn);
         for (int it = 0; ok && it < 4; ++it) {
-            ok = launch_gemm64(np, np, np, 1.0, X, np, 1, X, np, 0.0, G, np, s) == cudaSuccess &&
-                 launch_ns_halfres(np, G, s) == cudaSuccess &&
+            ok = sym_xtb(X, G) && launch_ns_halfres(np, G, s) == cudaSuccess &&
                  launch_offnorm(np, G, E.partial, E.ticket, E.result, false, s) == cudaSuccess &&
                  cudaMemcpyAsync(h_res, E.result, sizeof(h_res), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
                  cudaStreamSynchronize(s) == cudaSuccess;
-            st->flops_fp64 += 2.0 * nn * nn * nn;
-            st->launches += 3;
+            fl += sym_flops;
+            st->launches += 4;
             if (!ok) break;
             const double rnorm = 2.0 * sqrt(h_res[1]);
             if (!isfinite(rnorm)) {
@@ -308,18 +327,19 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
             ok = cudaMemcpyAsync(Xn, X, np2 * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
                  launch_gemm64(np, np, np, 1.0, X, np, 0, G, np, 1.0, Xn, np, s) == cudaSuccess;
             std::swap(X, Xn);
-            st->flops_fp64 += 2.0 * nn * nn * nn;
+            fl += 2.0 * n3;
             st->launches += 1;
+            if (0.75 * rnorm * rnorm <= 0.5 * orth_goal) break;
         }
-        // S = X^T A0 X, symmetrised into the A buffer paired with X (A0 is
-        // not needed after W = A0 X, so it takes the unsymmetrised product)
+        // S = X^T A0 X into the A buffer paired with X (its lower tiles, mirrored)
         cur = X == E.Qw[0] ? 0 : 1;
         double* Wt = E.Aw[cur ^ 1];
         ok = ok && launch_gemm64(np, np, np, 1.0, A0p, np, 0, X, np, 0.0, Wt, np, s) == cudaSuccess &&
-             launch_gemm64(np, np, np, 1.0, X, np, 1, Wt, np, 0.0, A0p, np, s) == cudaSuccess &&
-             launch_symmetrize(np, A0p, E.Aw[cur], s) == cudaSuccess;
-        st->flops_fp64 += 4.0 * nn * nn * nn;
+             sym_xtb(Wt, E.Aw[cur]);
+        fl += 2.0 * n3 + sym_flops;
         st->launches += 3;
+        st->flops_fp64 += fl;
+        st->flops_refine += fl;
         cudaEvent_t ev2;
         cudaEventCreate(&ev2);
         cudaEventRecord(ev2, s);
@@ -410,6 +430,7 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     L.Qw[0] = ws.get<float>(np2);
     L.Qw[1] = ws.get<float>(np2);
     L.T = ws.get<float>(tc_update_tbuf_floats(ord.dev_per_step, k));
+    L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(ord.dev_per_step, k));
     L.Vb = ws.get<double>((size_t)ord.max_pairs * 2 * k * k);
     L.rot = ws.get<int>(ord.max_pairs);
     const size_t gsz = pivot_gscratch_doubles(k);

@@ -151,16 +151,25 @@ struct TcUpdArgs {
     float* T;                                   // [npb][k*k] stage-1 products
     const int2* pairs; int npairs; int b, k;
     const double* V; const int* rot;            // pivot kernel outputs (FP64 V, V^T)
+    unsigned char* vimg;                        // per pair: V split into bf16 hi/lo operand tiles
     int* err;                                   // set on a timed-out tensor-core wait
     DevCounters* cnt;
 };
+// Launches the V split and the two stages.  T needs tc_update_tbuf_floats,
+// vimg tc_update_vimg_bytes (both for the step's entry count and k).
 cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s);
 size_t tc_update_tbuf_floats(int npairs, int k);
+size_t tc_update_vimg_bytes(int npairs, int k);
 
 cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
                              double* result, cudaStream_t s);
+// C = alpha op(A) B + beta C (FP64, column-major); lower = 1 computes only
+// the tiles that meet the lower triangle (for a symmetric product; mirror
+// afterwards with launch_mirror_lower).
 cudaError_t launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int transA,
-                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s);
+                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s,
+                          int lower = 0);
+cudaError_t launch_mirror_lower(int n, double* C, int ldc, cudaStream_t s);
 cudaError_t launch_load_sym32(int n, int np, const double* A, int lda, float* A32, float* Q32,
                               DevCounters* cnt, cudaStream_t s);
 cudaError_t launch_pad_sym64(int n, int np, const double* A, int lda, double* A0p, cudaStream_t s);

@@ -757,12 +757,13 @@ cudaError_t launch_gram(const double* G, int ldg, int m, const int2* pairs, int 
 // ======================================================================== general FP64 GEMM
 // C (M x N) = alpha op(A) B + beta C, column-major; op(A) = A (M x K) or A^T
 // (A stored K x M).  Tiles of 128 x 32 on 256 threads (the update kernels'
-// register tiling).
+// register tiling).  With `lower`, tiles strictly above the diagonal are
+// skipped (the caller mirrors a symmetric product afterwards).
 template <bool TRANS>
 __global__ void __launch_bounds__(UPD_T, 2) k_gemm64(int M, int N, int K, double alpha,
                                                      const double* __restrict__ A, int lda,
                                                      const double* __restrict__ B, int ldb, double beta,
-                                                     double* __restrict__ C, int ldc)
+                                                     double* __restrict__ C, int ldc, int lower)
 {
     extern __shared__ __align__(16) double sm[];
     constexpr int MR = 4, AS_LD = 32 * MR + 1;
@@ -770,6 +771,7 @@ __global__ void __launch_bounds__(UPD_T, 2) k_gemm64(int M, int N, int K, double
     double* Bs = As + KC * AS_LD;
     const int tid = threadIdx.x, ty = tid & 31, tx = tid >> 5;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * TN;
+    if (lower && n0 >= m0 + 128) return;
     const int Mt = min(128, M - m0), mr = (Mt + 31) >> 5;
     Tile<MR> t;
     t.zero();
@@ -789,18 +791,45 @@ __global__ void __launch_bounds__(UPD_T, 2) k_gemm64(int M, int N, int K, double
         }
 }
 
+// C(i, j) <- C(j, i) for i < j (upper triangle from the lower), n x n.
+__global__ void k_mirror_lower(int n, double* __restrict__ C, int ldc)
+{
+    __shared__ double t[32][33];
+    const int bi = blockIdx.x, bj = blockIdx.y;  // tile rows bi, columns bj of the upper part
+    if (bi > bj) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    // read the lower tile (rows bj*32.., cols bi*32..) coalesced, write it transposed
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bj * 32 + tx, j = bi * 32 + r;
+        t[r][tx] = (i < n && j < n) ? C[i + (size_t)ldc * j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi * 32 + tx, j = bj * 32 + r;
+        if (i < n && j < n && i < j) C[i + (size_t)ldc * j] = t[tx][r];
+    }
+}
+
+cudaError_t launch_mirror_lower(int n, double* C, int ldc, cudaStream_t s)
+{
+    const int nb = (n + 31) / 32;
+    k_mirror_lower<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(n, C, ldc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm64(int M, int N, int K, double alpha, const double* A, int lda, int transA,
-                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s)
+                          const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s,
+                          int lower)
 {
     const size_t smem = ((size_t)KC * (32 * 4 + 1) + (size_t)KC * T_LD) * sizeof(double);
     dim3 grid((M + 127) / 128, (N + TN - 1) / TN);
     cudaError_t e;
     if (transA) {
         if ((e = cudaFuncSetAttribute(k_gemm64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        k_gemm64<true><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        k_gemm64<true><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower);
     } else {
         if ((e = cudaFuncSetAttribute(k_gemm64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        k_gemm64<false><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        k_gemm64<false><<<grid, UPD_T, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower);
     }
     return cudaGetLastError();
 }

@@ -29,83 +29,9 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace jac {
-
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_T = 128;
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;          // one bf16 128 x 32 tile (8 KB)
-constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;          // A hi, A lo, B hi, B lo
-constexpr int TC_SMEM = 2 * TC_STAGE_BYTES + 1024;         // two stages + barriers, alignment
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Byte offset of element (r, k) of a 128 x 32 K-major bf16 tile in the
-// canonical no-swizzle layout: core matrix (r/8, k/8) at (r/8)*SBO + (k/8)*LBO,
-// row r%8 at 16 bytes, element k%8 at 2 bytes; LBO = 128 (next core matrix
-// along K), SBO = 512 (next 8-row group).
-__device__ __forceinline__ uint32_t tile_off(int r, int k)
-{
-    return (uint32_t)((r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits
-// [0,14), leading-dimension byte offset >> 4 in [16,30), stride byte offset
-// >> 4 in [32,46), version 1 in [46,48), no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator (bits
-// [4,6) = 1), A and B bf16 (bits [7,10) and [10,13) = 1), both K-major,
-// N >> 3 in [17,23), M >> 4 in [24,29).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
-{
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait until the mbarrier at `bar` completes the phase with parity `par`;
-// false if about 2 s pass first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par)
-{
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(par)
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
-    }
-}
-
-struct TcErr {
-    int* flag;   // device error word (set to 1 on a timed-out wait)
-};
 
 // C tile (128 x 128 at tile origin) = Aop * Bop over K; fa(m, k) and fb(k, n)
 // return FP32 operand values (0 outside the operands); st(m, n, v) stores.
@@ -269,147 +195,6 @@ cudaError_t launch_tc_gemm(int M, int N, int K, const float* A, int lda, int tra
     k_tc_gemm<<<grid, TC_T, TC_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, C, ldc, err);
     return cudaGetLastError();
 }
-
-// ---------------------------------------------------------------- mixed-precision step updates
-__device__ __forceinline__ int tc_map(int I, int J, int b, int x) { return x < b ? I * b + x : J * b + (x - b); }
-
-__device__ __forceinline__ bool tc_entry(const int2* pairs, int e, int& I, int& J)
-{
-    const int2 pr = pairs[e];
-    const bool fz = pr.x < 0;
-    I = fz ? -1 - pr.x : pr.x;
-    J = fz ? -1 - pr.y : pr.y;
-    return fz;
-}
-
-__device__ __forceinline__ void tc_decode_pb(int pb, int& e1, int& e2)
-{
-    int t = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)pb)) * 0.5f);
-    while (t * (t - 1) / 2 > pb) --t;
-    while ((t + 1) * t / 2 <= pb) ++t;
-    e2 = t;
-    e1 = pb - t * (t - 1) / 2;
-}
-
-// Stage 1 of a low-precision step.  Items [0, n_sand): tile (mt, nt) of
-// T_pb = A_{P1P2} V2 for pair-block pb = (P1 < P2) (k x k, FP32); items
-// beyond: tile (rt, nt) of Q'(:, P) = Q(:, P) V_P.  A pivot without rotation
-// (V = I) gives an exact copy instead of a tensor-core product.
-__global__ void __launch_bounds__(TC_T) k_tc_upd1(TcUpdArgs a, int n_sand)
-{
-    const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN;
-    int item = blockIdx.x;
-    if (item < n_sand) {
-        const int pb = item / (ntk * ntk), rem = item % (ntk * ntk), mt = rem / ntk, nt = rem % ntk;
-        int e1, e2, I1, J1, I2, J2;
-        tc_decode_pb(pb, e1, e2);
-        tc_entry(a.pairs, e1, I1, J1);
-        tc_entry(a.pairs, e2, I2, J2);
-        float* T = a.T + (size_t)pb * k * k;
-        const int m0 = mt * TC_BM, n0 = nt * TC_BN;
-        if (a.rot[e2] == 0) {
-            for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += TC_T) {
-                const int m = m0 + idx % TC_BM, j = n0 + idx / TC_BM;
-                if (m < k && j < k) T[m + (size_t)k * j] = a.Ain[tc_map(I1, J1, b, m) + (size_t)a.lda * tc_map(I2, J2, b, j)];
-            }
-            return;
-        }
-        const double* V2 = a.V + (size_t)e2 * 2 * k * k;
-        tc_gemm_tile(
-            k,
-            [&](int m, int kk) {
-                return m0 + m < k ? a.Ain[tc_map(I1, J1, b, m0 + m) + (size_t)a.lda * tc_map(I2, J2, b, kk)] : 0.f;
-            },
-            [&](int kk, int j) { return n0 + j < k ? (float)V2[kk + (size_t)k * (n0 + j)] : 0.f; },
-            [&](int m, int j, float v) {
-                if (m0 + m < k && n0 + j < k) T[(m0 + m) + (size_t)k * (n0 + j)] = v;
-            },
-            TcErr{a.err});
-        if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
-        return;
-    }
-    item -= n_sand;
-    const int nrt = (a.qrows + TC_BM - 1) / TC_BM;
-    const int e = item / (nrt * ntk), rem = item % (nrt * ntk), rt = rem / ntk, nt = rem % ntk;
-    int I, J;
-    tc_entry(a.pairs, e, I, J);
-    const int r0 = rt * TC_BM, n0 = nt * TC_BN;
-    if (a.rot[e] == 0) {
-        for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += TC_T) {
-            const int m = r0 + idx % TC_BM, j = n0 + idx / TC_BM;
-            if (m < a.qrows && j < k) {
-                const size_t o = m + (size_t)a.ldq * tc_map(I, J, b, j);
-                a.Qout[o] = a.Qin[o];
-            }
-        }
-        return;
-    }
-    const double* Vp = a.V + (size_t)e * 2 * k * k;
-    tc_gemm_tile(
-        k,
-        [&](int m, int kk) { return r0 + m < a.qrows ? a.Qin[(r0 + m) + (size_t)a.ldq * tc_map(I, J, b, kk)] : 0.f; },
-        [&](int kk, int j) { return n0 + j < k ? (float)Vp[kk + (size_t)k * (n0 + j)] : 0.f; },
-        [&](int m, int j, float v) {
-            if (r0 + m < a.qrows && n0 + j < k) a.Qout[(r0 + m) + (size_t)a.ldq * tc_map(I, J, b, n0 + j)] = v;
-        },
-        TcErr{a.err});
-    if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
-}
-
-// Stage 2: tile (mt, nt) of O_pb = V1^T T_pb, written to A' at (P1 rows, P2
-// columns) and mirrored to (P2 rows, P1 columns), so A' stays symmetric.
-__global__ void __launch_bounds__(TC_T) k_tc_upd2(TcUpdArgs a)
-{
-    const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN;
-    const int item = blockIdx.x;
-    const int pb = item / (ntk * ntk), rem = item % (ntk * ntk), mt = rem / ntk, nt = rem % ntk;
-    int e1, e2, I1, J1, I2, J2;
-    tc_decode_pb(pb, e1, e2);
-    tc_entry(a.pairs, e1, I1, J1);
-    tc_entry(a.pairs, e2, I2, J2);
-    const float* T = a.T + (size_t)pb * k * k;
-    const int m0 = mt * TC_BM, n0 = nt * TC_BN;
-    auto put = [&](int m, int j, float v) {
-        const int gi = tc_map(I1, J1, b, m), gj = tc_map(I2, J2, b, j);
-        a.Aout[gi + (size_t)a.lda * gj] = v;
-        a.Aout[gj + (size_t)a.lda * gi] = v;
-    };
-    if (a.rot[e1] == 0) {
-        for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += TC_T) {
-            const int m = m0 + idx % TC_BM, j = n0 + idx / TC_BM;
-            if (m < k && j < k) put(m, j, T[m + (size_t)k * j]);
-        }
-        return;
-    }
-    const double* V1t = a.V + (size_t)e1 * 2 * k * k + (size_t)k * k;
-    tc_gemm_tile(
-        k,
-        [&](int m, int kk) { return m0 + m < k ? (float)V1t[(m0 + m) + (size_t)k * kk] : 0.f; },
-        [&](int kk, int j) { return n0 + j < k ? T[kk + (size_t)k * (n0 + j)] : 0.f; },
-        [&](int m, int j, float v) {
-            if (m0 + m < k && n0 + j < k) put(m0 + m, n0 + j, v);
-        },
-        TcErr{a.err});
-    if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
-}
-
-cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s)
-{
-    const int ntk = (a.k + TC_BN - 1) / TC_BN;
-    const int npb = a.npairs * (a.npairs - 1) / 2;
-    const int n_sand = npb * ntk * ntk;
-    const int n_q = a.Qin ? a.npairs * ((a.qrows + TC_BM - 1) / TC_BM) * ntk : 0;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_upd2, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    if (n_sand + n_q > 0) k_tc_upd1<<<n_sand + n_q, TC_T, TC_SMEM, s>>>(a, n_sand);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand > 0) k_tc_upd2<<<n_sand, TC_T, TC_SMEM, s>>>(a);
-    return cudaGetLastError();
-}
-
-size_t tc_update_tbuf_floats(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
 
 }  // namespace jac
 

@@ -1,0 +1,497 @@
+// k_tc_upd.cu -- the block updates of one low-precision step of the mixed
+// form on the tcgen05 tensor cores (Algorithm 2's row and column updates,
+// with the symmetric pair-block formulation of the FP64 path):
+//
+//   stage 1: T_pb = A_{P1P2} V2 for every pair-block pb = (P1 < P2), and
+//            Q'(:,P) = Q(:,P) V_P for every pair P;
+//   stage 2: A'_{P1P2} = V1^T T_pb, written with its mirror A'_{P2P1}.
+//
+// The pivot blocks themselves receive D from the pivot kernel.  Every
+// product is formed from bf16 splits hi = bf16(x), lo = bf16(x - hi) as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+//
+// Data movement, per 128 x 128 output tile of a CTA (256 threads):
+//   * V_P (FP64, from the pivot kernel) is split once per step by
+//     k_tc_split_v into an "image": for every (128-column tile, 32-row
+//     chunk) the bf16 hi and lo tiles in the MMA operand layout (16 KB).  The
+//     same image is the B operand of stage 1 (V2(kk, n)) and the A operand of
+//     stage 2 (V1^T(m, kk) = V1(kk, m)), so stages copy it with 16-byte loads;
+//   * FP32 operands (A blocks, Q columns, T) are loaded eight values per
+//     thread item with all loads of a chunk issued back to back into
+//     registers one chunk ahead, then split and stored to shared memory;
+//   * three pipeline stages of 32 KB; one thread issues the chunk's six MMAs
+//     and commits them to the stage's mbarrier, which the stage's next
+//     filling waits for (bounded wait: a timeout sets the error word, the
+//     CTA skips the remaining work and still frees its TMEM);
+//   * the epilogue reads the accumulator with tcgen05.ld (8 warps: lane
+//     quarter w % 4, column half w / 4) and stores coalesced; the mirrored
+//     store of stage 2 writes 8 consecutive rows per thread.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace jac {
+
+namespace {
+
+constexpr int U_T = 256;
+constexpr int U_NS = 3;
+constexpr int U_SMEM = U_NS * TC_STAGE_BYTES + 1024;
+constexpr int U_IMG_TILE = 2 * TC_TILE_BYTES;   // hi + lo of one 128 x 32 operand tile
+
+__device__ __forceinline__ int umap(int I, int J, int b, int x) { return x < b ? I * b + x : J * b + (x - b); }
+
+__device__ __forceinline__ bool uentry(const int2* pairs, int e, int& I, int& J)
+{
+    const int2 pr = pairs[e];
+    const bool fz = pr.x < 0;
+    I = fz ? -1 - pr.x : pr.x;
+    J = fz ? -1 - pr.y : pr.y;
+    return fz;
+}
+
+__device__ __forceinline__ void decode_pb(int pb, int& e1, int& e2)
+{
+    int t = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)pb)) * 0.5f);
+    while (t * (t - 1) / 2 > pb) --t;
+    while ((t + 1) * t / 2 <= pb) ++t;
+    e2 = t;
+    e1 = pb - t * (t - 1) / 2;
+}
+
+// Eight bf16 values as one 16-byte word.
+struct Pack8 {
+    uint4 hi, lo;
+};
+
+__device__ __forceinline__ Pack8 split8(const float (&x)[8])
+{
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) split_bf16(x[u], h[u], l[u]);
+    Pack8 p;
+    p.hi = *reinterpret_cast<const uint4*>(h);
+    p.lo = *reinterpret_cast<const uint4*>(l);
+    return p;
+}
+
+// ---------------------------------------------------------------- operand loaders
+// A loader fills one 128 x 32 operand tile (hi at dst, lo at dst + 8 KB) of
+// chunk c in two phases: load(c) into registers, store() into shared memory.
+// Element (r, kk) of the tile is stored at tile_off(r, kk); r is the M (or N)
+// index, kk the K index.
+
+// FP32 gather: element (r, kk) = base[row(r) + ld * col(c * 32 + kk)], 0 where
+// row < 0 or col < 0.  Thread items (r, g): r = item % 128, g = item / 128
+// (eight consecutive K values), items tid and tid + 256.
+struct GatherF32 {
+    const float* base;
+    size_t ld;
+    int rows[2];        // global row of the thread's two items (or -1)
+    float v[2][8];
+    template <class COL>
+    __device__ __forceinline__ void load(int c, COL col)
+    {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int g = (tid + U_T * i) >> 7;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int cc = col(c * TC_BK + g * 8 + u);
+                v[i][u] = (rows[i] >= 0 && cc >= 0) ? __ldg(base + rows[i] + ld * (size_t)cc) : 0.f;
+            }
+        }
+    }
+    __device__ __forceinline__ void store(unsigned char* dst) const
+    {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int item = tid + U_T * i, r = item & 127, g = item >> 7;
+            const Pack8 p = split8(v[i]);
+            const uint32_t o = tile_off(r, g * 8);
+            *reinterpret_cast<uint4*>(dst + o) = p.hi;
+            *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+        }
+    }
+};
+
+// K-major FP32 (T of stage 2 as the B operand): element (n, kk) =
+// T[(c * 32 + kk) + k * (n0 + n)], 0 outside k x k.  Items (n, g) with
+// g = item % 4, n = item / 4, so a warp reads 128 contiguous bytes per n.
+struct KMajorF32 {
+    const float* T;
+    int k, n0;
+    bool vec4;
+    float v[2][8];
+    __device__ __forceinline__ void load(int c)
+    {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int item = tid + U_T * i, g = item & 3, n = item >> 2;
+            const int kk0 = c * TC_BK + g * 8, col = n0 + n;
+            const float* src = T + kk0 + (size_t)k * col;
+            if (col < k && vec4 && kk0 + 8 <= k) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(src + 4));
+                v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+                v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[i][u] = (col < k && kk0 + u < k) ? __ldg(src + u) : 0.f;
+            }
+        }
+    }
+    __device__ __forceinline__ void store(unsigned char* dst) const
+    {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int item = tid + U_T * i, g = item & 3, n = item >> 2;
+            const Pack8 p = split8(v[i]);
+            const uint32_t o = tile_off(n, g * 8);
+            *reinterpret_cast<uint4*>(dst + o) = p.hi;
+            *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+        }
+    }
+};
+
+// Pre-split image tile: 16 KB copied as 4 x 16 bytes per thread.
+struct ImageTile {
+    const unsigned char* img;   // tile (tile index t, chunk c) at img + (t * nchk + c) * 16 KB
+    int nchk;
+    int t;
+    uint4 v[4];
+    __device__ __forceinline__ void load(int c)
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(img + ((size_t)t * nchk + c) * U_IMG_TILE);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __ldg(src + threadIdx.x + U_T * i);
+    }
+    __device__ __forceinline__ void store(unsigned char* dst) const
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(dst)[threadIdx.x + U_T * i] = v[i];
+    }
+};
+
+// ---------------------------------------------------------------- the tile
+// acc(128 x 128) = Aop * Bop over nchk chunks of 32.  LA / LB: loaders with
+// load(c) / store(dst); EP(m, j0, v[8]): the epilogue for row m, columns
+// j0..j0+7.
+template <class LA, class LB, class EP>
+__device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char usm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[U_NS];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
+
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < U_NS; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+    uint32_t uses[U_NS];
+#pragma unroll
+    for (int s = 0; s < U_NS; ++s) uses[s] = 0;
+
+    la.load(0);
+    lb.load(0);
+    for (int c = 0; c < nchk; ++c) {
+        const int s = c % U_NS;
+        unsigned char* st = base + s * TC_STAGE_BYTES;
+        // the MMAs that last read this stage (chunk c - U_NS) must be complete
+        if (c >= U_NS && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+        la.store(st);
+        lb.store(st + 2 * TC_TILE_BYTES);
+        if (c + 1 < nchk) {  // next chunk's loads in flight during this chunk's MMAs
+            la.load(c + 1);
+            lb.load(c + 1);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TC_TILE_BYTES;
+            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < TC_BK / 16; ++ks) {
+                const uint32_t koff = ks * 2 * 128;
+                const uint64_t dah = smem_desc(a_hi + koff, 128, 512), dal = smem_desc(a_lo + koff, 128, 512);
+                const uint64_t dbh = smem_desc(b_hi + koff, 128, 512), dbl = smem_desc(b_lo + koff, 128, 512);
+                const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&s_bar[s]))
+                         : "memory");
+        }
+        uses[s]++;
+    }
+    // every MMA complete: wait for the last commit of each used stage
+    __syncthreads();
+    if (!s_fail) {
+        for (int s = 0; s < U_NS; ++s)
+            if (uses[s] > 0 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+        const int q = warp & 3, h = warp >> 2, m = q * 32 + lane;
+        for (int j0 = h * 64; j0 < h * 64 + 64; j0 += 8) {
+            uint32_t v[8];
+            const uint32_t addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float f[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) f[u] = __uint_as_float(v[u]);
+            ep(m, j0, f);
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+}
+
+// ---------------------------------------------------------------- kernels
+// Image of V_P per pair (skipped for pairs without rotation): tile (nt, c)
+// holds element (kk, n) = V_P(c * 32 + kk, nt * 128 + n), rounded to FP32
+// then split, at tile_off(n, kk).
+__global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V, const int* __restrict__ rot,
+                                                    int k, int ntk, int nchk, unsigned char* __restrict__ img)
+{
+    const int tile = blockIdx.x, e = tile / (ntk * nchk), rem = tile % (ntk * nchk);
+    const int nt = rem / nchk, c = rem % nchk;
+    if (rot[e] == 0) return;
+    const double* Ve = V + (size_t)e * 2 * k * k;
+    unsigned char* dst = img + (size_t)tile * U_IMG_TILE;
+    for (int i = 0; i < 2; ++i) {
+        const int item = threadIdx.x + U_T * i, g = item & 3, nn = item >> 2;
+        const int n = nt * TC_BN + nn, kk0 = c * TC_BK + g * 8;
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = (n < k && kk0 + u < k) ? (float)Ve[(kk0 + u) + (size_t)k * n] : 0.f;
+        const Pack8 p = split8(x);
+        const uint32_t o = tile_off(nn, g * 8);
+        *reinterpret_cast<uint4*>(dst + o) = p.hi;
+        *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+    }
+}
+
+// Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2; items
+// beyond: tile (rt, nt) of Q'(:, P) = Q(:, P) V_P.  A pivot without rotation
+// (V = I) gives an exact copy instead of a product.
+__global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
+{
+    const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
+    int item = blockIdx.x;
+    if (item < n_sand) {
+        const int pb = item / (ntk * ntk), rem = item % (ntk * ntk), mt = rem / ntk, nt = rem % ntk;
+        int e1, e2, I1, J1, I2, J2;
+        decode_pb(pb, e1, e2);
+        uentry(a.pairs, e1, I1, J1);
+        uentry(a.pairs, e2, I2, J2);
+        float* T = a.T + (size_t)pb * k * k;
+        const int m0 = mt * TC_BM, n0 = nt * TC_BN;
+        if (a.rot[e2] == 0) {
+            for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += U_T) {
+                const int m = m0 + idx % TC_BM, j = n0 + idx / TC_BM;
+                if (m < k && j < k) T[m + (size_t)k * j] = a.Ain[umap(I1, J1, b, m) + (size_t)a.lda * umap(I2, J2, b, j)];
+            }
+            return;
+        }
+        GatherF32 la;
+        la.base = a.Ain;
+        la.ld = (size_t)a.lda;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = (threadIdx.x + U_T * i) & 127;
+            la.rows[i] = m0 + r < k ? umap(I1, J1, b, m0 + r) : -1;
+        }
+        ImageTile lb{a.vimg + (size_t)e2 * ntk * nchk * U_IMG_TILE, nchk, nt};
+        struct LA {
+            GatherF32& g;
+            int I2, J2, b, k;
+            __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I2, J2, b, x) : -1; }); }
+            __device__ void store(unsigned char* d) const { g.store(d); }
+        } lawrap{la, I2, J2, b, k};
+        tc_tile(nchk, lawrap, lb,
+                [&](int m, int j0, const float (&v)[8]) {
+                    if (m0 + m >= k) return;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (n0 + j0 + u < k) T[(m0 + m) + (size_t)k * (n0 + j0 + u)] = v[u];
+                },
+                a.err);
+        if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
+        return;
+    }
+    item -= n_sand;
+    const int nrt = (a.qrows + TC_BM - 1) / TC_BM;
+    const int e = item / (nrt * ntk), rem = item % (nrt * ntk), rt = rem / ntk, nt = rem % ntk;
+    int I, J;
+    uentry(a.pairs, e, I, J);
+    const int r0 = rt * TC_BM, n0 = nt * TC_BN;
+    if (a.rot[e] == 0) {
+        for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += U_T) {
+            const int m = r0 + idx % TC_BM, j = n0 + idx / TC_BM;
+            if (m < a.qrows && j < k) {
+                const size_t o = m + (size_t)a.ldq * umap(I, J, b, j);
+                a.Qout[o] = a.Qin[o];
+            }
+        }
+        return;
+    }
+    GatherF32 la;
+    la.base = a.Qin;
+    la.ld = (size_t)a.ldq;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = (threadIdx.x + U_T * i) & 127;
+        la.rows[i] = r0 + r < a.qrows ? r0 + r : -1;
+    }
+    ImageTile lb{a.vimg + (size_t)e * ntk * nchk * U_IMG_TILE, nchk, nt};
+    struct LA {
+        GatherF32& g;
+        int I, J, b, k;
+        __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I, J, b, x) : -1; }); }
+        __device__ void store(unsigned char* d) const { g.store(d); }
+    } lawrap{la, I, J, b, k};
+    tc_tile(nchk, lawrap, lb,
+            [&](int m, int j0, const float (&v)[8]) {
+                if (r0 + m >= a.qrows) return;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (n0 + j0 + u < k) a.Qout[(r0 + m) + (size_t)a.ldq * umap(I, J, b, n0 + j0 + u)] = v[u];
+            },
+            a.err);
+    if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
+}
+
+// Stage 2: tile (mt, nt) of O_pb = V1^T T_pb, written to A' at (P1 rows, P2
+// columns) and mirrored to (P2 rows, P1 columns), so A' stays symmetric.
+__global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
+{
+    const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
+    const int item = blockIdx.x;
+    const int pb = item / (ntk * ntk), rem = item % (ntk * ntk), mt = rem / ntk, nt = rem % ntk;
+    int e1, e2, I1, J1, I2, J2;
+    decode_pb(pb, e1, e2);
+    uentry(a.pairs, e1, I1, J1);
+    uentry(a.pairs, e2, I2, J2);
+    const float* T = a.T + (size_t)pb * k * k;
+    const int m0 = mt * TC_BM, n0 = nt * TC_BN;
+    float* Ao = a.Aout;
+    const size_t lda = (size_t)a.lda;
+    if (a.rot[e1] == 0) {
+        for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += U_T) {
+            const int m = m0 + idx % TC_BM, j = n0 + idx / TC_BM;
+            if (m < k && j < k) {
+                const int gi = umap(I1, J1, b, m), gj = umap(I2, J2, b, j);
+                const float v = T[m + (size_t)k * j];
+                Ao[gi + lda * gj] = v;
+                Ao[gj + lda * gi] = v;
+            }
+        }
+        return;
+    }
+    ImageTile la{a.vimg + (size_t)e1 * ntk * nchk * U_IMG_TILE, nchk, mt};
+    KMajorF32 lb;
+    lb.T = T;
+    lb.k = k;
+    lb.n0 = n0;
+    lb.vec4 = (k & 3) == 0;
+    // 8 consecutive output columns land in 8 consecutive rows of the mirror
+    // when they stay inside one block of the pair and the address is 16-byte
+    // aligned
+    const bool mvec = (b & 7) == 0 && (lda & 3) == 0;
+    tc_tile(nchk, la, lb,
+            [&](int m, int j0, const float (&v)[8]) {
+                if (m0 + m >= k) return;
+                const int gi = umap(I1, J1, b, m0 + m);
+                const int jb = n0 + j0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (jb + u < k) Ao[gi + lda * umap(I2, J2, b, jb + u)] = v[u];
+                if (mvec && jb + 8 <= k) {
+                    float* dst = Ao + umap(I2, J2, b, jb) + lda * gi;
+                    reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (jb + u < k) Ao[umap(I2, J2, b, jb + u) + lda * gi] = v[u];
+                }
+            },
+            a.err);
+    if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
+}
+
+}  // namespace
+
+size_t tc_update_tbuf_floats(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
+
+size_t tc_update_vimg_bytes(int npairs, int k)
+{
+    const size_t ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
+    return (size_t)npairs * ntk * nchk * U_IMG_TILE;
+}
+
+cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s)
+{
+    const int ntk = (a.k + TC_BN - 1) / TC_BN, nchk = (a.k + TC_BK - 1) / TC_BK;
+    const int npb = a.npairs * (a.npairs - 1) / 2;
+    const int n_sand = npb * ntk * ntk;
+    const int n_q = a.Qin ? a.npairs * ((a.qrows + TC_BM - 1) / TC_BM) * ntk : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_upd2, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    if (e != cudaSuccess) return e;
+    if (a.npairs > 0) k_tc_split_v<<<a.npairs * ntk * nchk, U_T, 0, s>>>(a.V, a.rot, a.k, ntk, nchk, a.vimg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n_sand + n_q > 0) k_tc_upd1<<<n_sand + n_q, U_T, U_SMEM, s>>>(a, n_sand);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n_sand > 0) k_tc_upd2<<<n_sand, U_T, U_SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace jac
