@@ -138,6 +138,7 @@ struct jacobi_plan {
     DevCounters* d_cnt = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* graph_info = nullptr;        // info pointer baked into the graph
+    bool use_clusters = true;         // EVD orders above the smem size on clusters (JACOBI_BATCHED_CLUSTER=0: L2 slots)
     float last_ms = 0.f;
 };
 
@@ -148,17 +149,19 @@ size_t max_slot_elems(int kmax, bool vec)
     return batched_tri_pad(kmax) + (vec ? (size_t)kmax * kmax : 0);
 }
 
+// Launch the batch (or the sub-list `h_list` / `d_list`, matrix indices in
+// longest-first order): EVD matrices above the shared-memory size go to the
+// cluster kernel (grouped by cluster size, largest first), the rest to the
+// persistent kernel.
 template <typename T>
 cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape& sh, int grid,
-                        int batch_override = -1, const int* order_override = nullptr)
+                        const std::vector<int>& h_list, const int* d_list)
 {
     cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const int B = pl->batch;
+    const int B = pl->batch, count = (int)h_list.size();
     if (pl->kind == 0) {
         BatchedEvdArgs<T> a{};
-        a.batch = batch_override >= 0 ? batch_override : B;
-        a.order = order_override ? order_override : pl->d_order;
         a.n = pl->d_n;
         a.A = (T* const*)pl->d_ptrs;
         a.lda = pl->d_lda;
@@ -174,11 +177,41 @@ cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape&
         a.tol = (T)pl->p.inner_tol;
         a.max_sweeps = pl->p.max_sweeps;
         a.cnt = pl->d_cnt;
+        // the prefix of orders above the shared-memory size, by cluster size
+        const size_t cap = device_smem_optin() - 4096;
+        int nl = 0;
+        if (pl->use_clusters) {
+            while (nl < count) {
+                const int n = pl->h_n[h_list[nl]], k = n + (n & 1);
+                if (k <= sh.smem_kmax) break;
+                if (batched_cluster_size<T>(k, pl->vec, cap) == 0) {  // too large: all stay on L2 slots
+                    nl = 0;
+                    break;
+                }
+                ++nl;
+            }
+            for (int i = 0; i < nl;) {
+                const int n0 = pl->h_n[h_list[i]];
+                const int C = batched_cluster_size<T>(n0 + (n0 & 1), pl->vec, cap);
+                int j = i + 1;
+                while (j < nl) {
+                    const int nj = pl->h_n[h_list[j]];
+                    if (batched_cluster_size<T>(nj + (nj & 1), pl->vec, cap) != C) break;
+                    ++j;
+                }
+                const int kmax = (n0 + C - 1) / C * C;
+                if ((e = launch_batched_evd_cluster<T>(a, d_list + i, j - i, kmax, C, s)) != cudaSuccess) return e;
+                i = j;
+            }
+        }
+        a.batch = count - nl;
+        a.order = d_list + nl;
+        if (a.batch == 0) return cudaSuccess;
         return launch_batched_evd<T>(a, grid, sh.threads, s);
     }
     BatchedSvdArgs<T> a{};
-    a.batch = batch_override >= 0 ? batch_override : B;
-    a.order = order_override ? order_override : pl->d_order;
+    a.batch = count;
+    a.order = d_list;
     a.m = pl->d_m;
     a.n = pl->d_n;
     a.G = (T* const*)pl->d_ptrs;
@@ -199,10 +232,10 @@ cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape&
 }
 
 cudaError_t plan_launch_any(jacobi_plan* pl, int* info, cudaStream_t s, const Shape& sh, int grid,
-                            int batch_override = -1, const int* order_override = nullptr)
+                            const std::vector<int>& h_list, const int* d_list)
 {
-    return pl->esize == 8 ? plan_launch<double>(pl, info, s, sh, grid, batch_override, order_override)
-                          : plan_launch<float>(pl, info, s, sh, grid, batch_override, order_override);
+    return pl->esize == 8 ? plan_launch<double>(pl, info, s, sh, grid, h_list, d_list)
+                          : plan_launch<float>(pl, info, s, sh, grid, h_list, d_list);
 }
 
 template <typename T>
@@ -245,6 +278,7 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
     pl->batch = batch;
     pl->vec = p.want_vectors != 0;
     pl->p = p;
+    if (const char* env = getenv("JACOBI_BATCHED_CLUSTER")) pl->use_clusters = atoi(env) != 0;
     if (precision == JACOBI_PREC_FP32 && p.inner_tol == 4.0 * U64) pl->p.inner_tol = 4.0 * U32;
     pl->h_n.assign(h_n, h_n + batch);
     pl->h_m = kind == 1 ? std::vector<int>(h_m, h_m + batch) : pl->h_n;
@@ -363,9 +397,9 @@ extern "C" int jacobi_plan_autotune(jacobi_plan* pl, void* const* A_or_G, void* 
     for (const Shape& sh : cands) {
         const int grid = std::min(grid_for(pl, sh), device_sms() * 4);
         // warm, then time
-        if (plan_launch_any(pl, info, s, sh, grid, sample, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (plan_launch_any(pl, info, s, sh, grid, h_sub, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
         cudaEventRecord(e0, s);
-        if (plan_launch_any(pl, info, s, sh, grid, sample, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (plan_launch_any(pl, info, s, sh, grid, h_sub, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = JACOBI_ERR_CUDA; break; }
         float ms = 0.f;
@@ -419,7 +453,7 @@ extern "C" int jacobi_plan_execute(jacobi_plan* pl, void* const* A_or_G, void* c
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             ok = cudaMemcpyAsync(pl->d_ptrs, pl->h_ptrs, sizeof(void*) * 3 * B, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
-                 plan_launch_any(pl, info, cs, pl->shape, pl->grid) == cudaSuccess;
+                 plan_launch_any(pl, info, cs, pl->shape, pl->grid, pl->h_order, pl->d_order) == cudaSuccess;
             ok = (cudaStreamEndCapture(cs, &g) == cudaSuccess) && ok && g;
         }
         if (ok) ok = cudaGraphInstantiate(&pl->exec, g, 0) == cudaSuccess;

@@ -62,6 +62,16 @@ cudaError_t launch_batched_svd(const BatchedSvdArgs<T>& a, int kmax, int grid, i
 cudaError_t launch_quad_table(unsigned* qtab, int h, cudaStream_t s);
 template <typename T>
 int batched_evd_occupancy(int threads, int smem_kmax, bool vec);   // resident CTAs per SM
+// Matrices above the shared-memory size: one cluster of C CTAs per matrix
+// (order padded to a multiple of C).  list: `count` matrix indices; kmax:
+// the largest padded order among them.
+template <typename T>
+size_t batched_cluster_smem(int k, int C, bool vec);
+template <typename T>
+int batched_cluster_size(int k, bool vec, size_t smem_cap);   // smallest C that fits, 0 if none
+template <typename T>
+cudaError_t launch_batched_evd_cluster(const BatchedEvdArgs<T>& a, const int* list, int count, int kmax,
+                                       int C, cudaStream_t s);
 template <typename T>
 int batched_svd_occupancy(int threads, int kmax);
 

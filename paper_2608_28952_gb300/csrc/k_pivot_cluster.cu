@@ -25,66 +25,19 @@
 
 #include "internal.h"
 #include "jacobi_core.cuh"
+#include "cluster_common.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace jac {
 
 constexpr int PC_T = 512;
-constexpr int PC_MAXC = 8;
+constexpr int PC_MAXC8 = 8;   // pivot clusters: portable sizes only
 
 __device__ __forceinline__ int pc_pair_map(int I, int J, int b, int x)
 {
     return x < b ? I * b + x : J * b + (x - b);
 }
-
-// Row ranges: CTA r owns rows [row0[r], row0[r+1]) of the packed triangle,
-// chosen so the entry counts are as equal as possible.
-struct Split {
-    int C;
-    int row0[PC_MAXC + 1];
-    int base[PC_MAXC + 1];  // packed index of the first entry of row0[r]
-};
-
-__host__ __device__ inline void make_split(int k, int C, Split& s)
-{
-    s.C = C;
-    const long long total = (long long)k * (k + 1) / 2;
-    int row = 0;
-    s.row0[0] = 0;
-    s.base[0] = 0;
-    for (int r = 1; r < C; ++r) {
-        const long long target = total * r / C;
-        while (row < k && (long long)(row + 1) * (row + 2) / 2 <= target) ++row;
-        s.row0[r] = row;
-        s.base[r] = row * (row + 1) / 2;
-    }
-    s.row0[C] = k;
-    s.base[C] = (int)total;
-}
-
-__host__ inline int split_max_chunk(int k, int C)
-{
-    Split s;
-    make_split(k, C, s);
-    int m = 0;
-    for (int r = 0; r < C; ++r) m = s.base[r + 1] - s.base[r] > m ? s.base[r + 1] - s.base[r] : m;
-    return m;
-}
-
-struct DistPacked {
-    double* ptr[PC_MAXC];   // each CTA's chunk, as generic (DSMEM) addresses
-    Split sp;
-    __device__ __forceinline__ double* at(int i, int j) const
-    {
-        if (i < j) { const int t = i; i = j; j = t; }
-        int r = 0;
-#pragma unroll
-        for (int u = 1; u < PC_MAXC; ++u)
-            if (u < sp.C && i >= sp.row0[u]) r = u;
-        return ptr[r] + (tri(i) + j - sp.base[r]);
-    }
-};
 
 size_t pivot_cluster_smem(int k, int C)
 {
@@ -113,7 +66,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     }
     const bool frozen = a.pairs[e].x < 0;
 
-    DistPacked ap;
+    DistPacked<double, PC_MAXC8> ap;
     make_split(k, C, ap.sp);
     const int chunk_max = [&] {
         int m = 0;
@@ -133,7 +86,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     int* ron = rq + half;
     __shared__ int s_cnt;
     __shared__ double s_red[PC_T / 32];
-    __shared__ double s_part[PC_MAXC];
+    __shared__ double s_part[PC_MAXC8];
     __shared__ int s_dest[256];
     __shared__ int s_pos[256];
     for (int u = 0; u < C; ++u) ap.ptr[u] = cluster.map_shared_rank(my_chunk, u);
@@ -341,11 +294,16 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
 
 // Cluster size for a step with npairs pairs on an sms-SM GPU: the largest
 // power of two C <= 8 with npairs * C <= sms whose per-CTA share fits the
-// shared-memory limit, or 1 (use the one-CTA kernel).
+// shared-memory limit, or 1 (use the one-CTA kernel).  Small pivots gain
+// nothing from a cluster (two cluster barriers per round cost more than the
+// round's work): k <= 32 uses one CTA, k <= 64 at most 4 (measured on GB300:
+// n = 256, b = 16: 32 ms with one CTA, 37 ms with clusters of 4; n = 1024,
+// b = 32: best with 4).
 int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
 {
+    const int cmax = k <= 32 ? 1 : (k <= 64 ? 4 : PC_MAXC8);
     int best = 1;
-    for (int C = 2; C <= PC_MAXC; C *= 2) {
+    for (int C = 2; C <= cmax; C *= 2) {
         if (k % C || k / C < 8 || npairs * C > sms) break;
         if (pivot_cluster_smem(k, C) + 4096 <= smem_cap) best = C;
     }
