@@ -51,7 +51,15 @@ extern "C" {
 #define JACOBI_ORDER_ANTI_DIAGONAL 1
 
 /* Arithmetic of the update GEMMs.  Pivot solves, the off-norm test and the
- * closing sweeps are FP64 in every mode. */
+ * closing sweeps are FP64 in every mode.
+ *  FP64:          DFMA throughout.
+ *  FP32:          the batched forms' FP32 storage and arithmetic.
+ *  MIXED_BF16X3:  low-precision sweeps on FP32 working copies, products on the
+ *                 tensor cores from bf16 hi/lo splits (three products), then
+ *                 the FP64 refinement and closing sweeps (jacobi_syev).
+ *  MIXED_FP16X3:  the same with fp16 hi/lo splits (22 bits per operand), the
+ *                 FP32 operands scaled by powers of two per row / column.
+ *  MIXED_TF32:    reserved (returns JACOBI_ERR_UNSUPPORTED). */
 #define JACOBI_PREC_FP64 0
 #define JACOBI_PREC_FP32 1
 #define JACOBI_PREC_MIXED_BF16X3 2
@@ -125,6 +133,12 @@ typedef struct {
                                 sweeps (pivot solves included)                 */
     double ms_refine;        /* mixed forms: device time of the return to FP64
                                 (re-orthogonalisation, refinement, S = X^T A X) */
+    double ms_pivot_lowp;    /* mixed forms: of ms_pivot, in the low-precision
+                                sweeps                                         */
+    double ms_update_lowp;   /* mixed forms: of ms_update, in the low-precision
+                                sweeps (tensor-core update kernels)            */
+    double flops_refine;     /* mixed forms: of flops_fp64, in the refinement
+                                GEMMs                                          */
 } jacobi_stats;
 
 /* Fill *p with the defaults above.  Returns 0. */
@@ -310,10 +324,12 @@ int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, c
  * jacobi_syev_step), D is written back rounded to FP32, and every
  * block-row/column update of A (A'_{P1P2} = V1^T A_{P1P2} V2, mirrored) and
  * column update of Q (Q'(:,P) = Q(:,P) V_P) is formed from V rounded to FP32
- * by the split-precision product of jacobi_lowp_gemm.  A is a full
+ * by the split-precision product of jacobi_lowp_gemm (bf16 splits; fp16
+ * splits with power-of-two row/column scaling for MIXED_FP16X3).  A is a full
  * symmetric np x np FP32 matrix (exactly symmetric), np = N * p->b with N
  * even for round-robin; Q is np x np FP32 or NULL; both device, column-major,
- * updated in place.  p->precision must be JACOBI_PREC_MIXED_BF16X3.
+ * updated in place.  p->precision must be JACOBI_PREC_MIXED_BF16X3 or
+ * JACOBI_PREC_MIXED_FP16X3.
  * Returns 0, -k for an invalid argument, JACOBI_ERR_UNSUPPORTED for another
  * precision, JACOBI_ERR_TIMEOUT if a bounded tensor-core wait ran out,
  * JACOBI_ERR_CUDA / JACOBI_ERR_ALLOC.  Allocates its workspace

@@ -40,6 +40,8 @@ struct LowpState {
     float* Qw[2];
     float* T;
     unsigned char* vimg;
+    unsigned* tmax;
+    int f16;
     double* Vb;
     int* rot;
     double* gscratch;
@@ -83,6 +85,8 @@ cudaError_t launch_step32(const LowpState& L, int s, int cur, cudaStream_t cs, d
     ua.qrows = L.np;
     ua.T = L.T;
     ua.vimg = L.vimg;
+    ua.tmax = L.tmax;
+    ua.f16 = L.f16;
     ua.pairs = L.dpairs + p0;
     ua.npairs = nps;
     ua.b = L.b;
@@ -168,7 +172,8 @@ int run_lowp_sweeps(LowpState& L, const jacobi_params& p, int& cur, double targe
 int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const jacobi_params& pin,
                jacobi_stats* st, cudaStream_t s)
 {
-    if (pin.precision != JACOBI_PREC_MIXED_BF16X3) return JACOBI_ERR_UNSUPPORTED;
+    if (pin.precision != JACOBI_PREC_MIXED_BF16X3 && pin.precision != JACOBI_PREC_MIXED_FP16X3)
+        return JACOBI_ERR_UNSUPPORTED;
     if (pin.warm_start) return JACOBI_ERR_UNSUPPORTED;
     jacobi_params p = pin;
     if (p.refine_steps < 0 || p.refine_steps > 8 || !(p.switch_tol >= 0.0)) return -7;
@@ -220,6 +225,8 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.Qw[1] = ws.get<float>(np2);
     L.T = ws.get<float>(tc_update_tbuf_floats(E.ord.dev_per_step, k));
     L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(E.ord.dev_per_step, k));
+    L.tmax = ws.get<unsigned>(tc_update_tmax_words(E.ord.dev_per_step, k));
+    L.f16 = p.precision == JACOBI_PREC_MIXED_FP16X3;
     L.err = ws.get<int>(1);
     if (ws.failed) return JACOBI_ERR_ALLOC;
     L.pcl = E.pcl;
@@ -406,7 +413,8 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     if (pin) p = *pin; else jacobi_params_default(&p);
     int e = check_params(p);
     if (e) return e == -7 ? -6 : e;
-    if (p.precision != JACOBI_PREC_MIXED_BF16X3) return JACOBI_ERR_UNSUPPORTED;
+    if (p.precision != JACOBI_PREC_MIXED_BF16X3 && p.precision != JACOBI_PREC_MIXED_FP16X3)
+        return JACOBI_ERR_UNSUPPORTED;
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2) return -1;
     if (!A) return -2;
@@ -431,6 +439,8 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     L.Qw[1] = ws.get<float>(np2);
     L.T = ws.get<float>(tc_update_tbuf_floats(ord.dev_per_step, k));
     L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(ord.dev_per_step, k));
+    L.tmax = ws.get<unsigned>(tc_update_tmax_words(ord.dev_per_step, k));
+    L.f16 = p.precision == JACOBI_PREC_MIXED_FP16X3;
     L.Vb = ws.get<double>((size_t)ord.max_pairs * 2 * k * k);
     L.rot = ws.get<int>(ord.max_pairs);
     const size_t gsz = pivot_gscratch_doubles(k);

@@ -151,7 +151,9 @@ struct TcUpdArgs {
     float* T;                                   // [npb][k*k] stage-1 products
     const int2* pairs; int npairs; int b, k;
     const double* V; const int* rot;            // pivot kernel outputs (FP64 V, V^T)
-    unsigned char* vimg;                        // per pair: V split into bf16 hi/lo operand tiles
+    unsigned char* vimg;                        // per pair: V split into hi/lo operand tiles
+    unsigned* tmax;                             // FP16x3: per pair-block column maxima of T
+    int f16;                                    // 0: bf16 hi/lo (BF16x3), 1: fp16 hi/lo (FP16x3)
     int* err;                                   // set on a timed-out tensor-core wait
     DevCounters* cnt;
 };
@@ -160,6 +162,7 @@ struct TcUpdArgs {
 cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s);
 size_t tc_update_tbuf_floats(int npairs, int k);
 size_t tc_update_vimg_bytes(int npairs, int k);
+size_t tc_update_tmax_words(int npairs, int k);
 
 cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
                              double* result, cudaStream_t s);

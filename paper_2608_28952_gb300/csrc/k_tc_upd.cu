@@ -7,8 +7,14 @@
 //   stage 2: A'_{P1P2} = V1^T T_pb, written with its mirror A'_{P2P1}.
 //
 // The pivot blocks themselves receive D from the pivot kernel.  Every
-// product is formed from bf16 splits hi = bf16(x), lo = bf16(x - hi) as
-// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+// product is formed from splits hi = r(x), lo = r(x - hi) as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory, r = bf16
+// (BF16x3) or fp16 (FP16x3).  fp16 has 5 exponent bits, so in the FP16x3
+// form the FP32 operands are scaled by powers of two (exact) before the
+// split: every row of a stage-1 A tile by its own row maximum over K, every
+// column of T by its column maximum (collected by stage 1's epilogue); the
+// products are scaled back in the epilogues.  V and Q (|entries| <= 1) are
+// split unscaled.
 //
 // Data movement, per 128 x 128 output tile of a CTA (256 threads):
 //   * V_P (FP64, from the pivot kernel) is split once per step by
@@ -67,16 +73,34 @@ struct Pack8 {
     uint4 hi, lo;
 };
 
-__device__ __forceinline__ Pack8 split8(const float (&x)[8])
+template <bool F16>
+__device__ __forceinline__ Pack8 split8(const float (&x)[8], float scale = 1.f)
 {
-    __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) split_bf16(x[u], h[u], l[u]);
     Pack8 p;
-    p.hi = *reinterpret_cast<const uint4*>(h);
-    p.lo = *reinterpret_cast<const uint4*>(l);
+    if (F16) {
+        __half h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) split_f16(x[u] * scale, h[u], l[u]);
+        p.hi = *reinterpret_cast<const uint4*>(h);
+        p.lo = *reinterpret_cast<const uint4*>(l);
+    } else {
+        __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) split_bf16(x[u] * scale, h[u], l[u]);
+        p.hi = *reinterpret_cast<const uint4*>(h);
+        p.lo = *reinterpret_cast<const uint4*>(l);
+    }
     return p;
 }
+
+// Power-of-two scaling: e with mx * 2^-e in [0.5, 1) (0 for mx == 0), and 2^e.
+__device__ __forceinline__ int exp_of(float mx)
+{
+    if (!(mx > 0.f)) return 0;
+    const int e = ilogbf(mx) + 1;
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+__device__ __forceinline__ float pow2(int e) { return __int_as_float((127 + e) << 23); }
 
 // ---------------------------------------------------------------- operand loaders
 // A loader fills one 128 x 32 operand tile (hi at dst, lo at dst + 8 KB) of
@@ -87,10 +111,12 @@ __device__ __forceinline__ Pack8 split8(const float (&x)[8])
 // FP32 gather: element (r, kk) = base[row(r) + ld * col(c * 32 + kk)], 0 where
 // row < 0 or col < 0.  Thread items (r, g): r = item % 128, g = item / 128
 // (eight consecutive K values), items tid and tid + 256.
+template <bool F16>
 struct GatherF32 {
     const float* base;
     size_t ld;
     int rows[2];        // global row of the thread's two items (or -1)
+    float scale[2];     // power-of-two scale of the two items' rows (FP16x3)
     float v[2][8];
     template <class COL>
     __device__ __forceinline__ void load(int c, COL col)
@@ -112,7 +138,7 @@ struct GatherF32 {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, r = item & 127, g = item >> 7;
-            const Pack8 p = split8(v[i]);
+            const Pack8 p = split8<F16>(v[i], scale[i]);
             const uint32_t o = tile_off(r, g * 8);
             *reinterpret_cast<uint4*>(dst + o) = p.hi;
             *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
@@ -123,10 +149,12 @@ struct GatherF32 {
 // K-major FP32 (T of stage 2 as the B operand): element (n, kk) =
 // T[(c * 32 + kk) + k * (n0 + n)], 0 outside k x k.  Items (n, g) with
 // g = item % 4, n = item / 4, so a warp reads 128 contiguous bytes per n.
+template <bool F16>
 struct KMajorF32 {
     const float* T;
     int k, n0;
     bool vec4;
+    const float* cscale;   // shared memory: power-of-two scale of column n (FP16x3), or null
     float v[2][8];
     __device__ __forceinline__ void load(int c)
     {
@@ -153,7 +181,7 @@ struct KMajorF32 {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, g = item & 3, n = item >> 2;
-            const Pack8 p = split8(v[i]);
+            const Pack8 p = split8<F16>(v[i], cscale ? cscale[n] : 1.f);
             const uint32_t o = tile_off(n, g * 8);
             *reinterpret_cast<uint4*>(dst + o) = p.hi;
             *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
@@ -184,7 +212,7 @@ struct ImageTile {
 // acc(128 x 128) = Aop * Bop over nchk chunks of 32.  LA / LB: loaders with
 // load(c) / store(dst); EP(m, j0, v[8]): the epilogue for row m, columns
 // j0..j0+7.
-template <class LA, class LB, class EP>
+template <bool F16, class LA, class LB, class EP>
 __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
 {
     extern __shared__ __align__(1024) unsigned char usm[];
@@ -210,7 +238,7 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+    const uint32_t idesc = F16 ? idesc_f16(TC_BM, TC_BN) : idesc_bf16(TC_BM, TC_BN);
     uint32_t uses[U_NS];
 #pragma unroll
     for (int s = 0; s < U_NS; ++s) uses[s] = 0;
@@ -296,6 +324,7 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
 // Image of V_P per pair (skipped for pairs without rotation): tile (nt, c)
 // holds element (kk, n) = V_P(c * 32 + kk, nt * 128 + n), rounded to FP32
 // then split, at tile_off(n, kk).
+template <bool F16>
 __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V, const int* __restrict__ rot,
                                                     int k, int ntk, int nchk, unsigned char* __restrict__ img)
 {
@@ -310,7 +339,7 @@ __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V
         float x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = (n < k && kk0 + u < k) ? (float)Ve[(kk0 + u) + (size_t)k * n] : 0.f;
-        const Pack8 p = split8(x);
+        const Pack8 p = split8<F16>(x);
         const uint32_t o = tile_off(nn, g * 8);
         *reinterpret_cast<uint4*>(dst + o) = p.hi;
         *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
@@ -319,9 +348,13 @@ __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V
 
 // Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2; items
 // beyond: tile (rt, nt) of Q'(:, P) = Q(:, P) V_P.  A pivot without rotation
-// (V = I) gives an exact copy instead of a product.
+// (V = I) gives an exact copy instead of a product.  FP16x3: the rows of the
+// A tile are scaled by their maxima over K (a first pass over the tile's
+// rows), and the epilogue records every T column's maximum for stage 2.
+template <bool F16>
 __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
 {
+    __shared__ float s_rmax[2][TC_BM];
     const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
     int item = blockIdx.x;
     if (item < n_sand) {
@@ -331,37 +364,72 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
         uentry(a.pairs, e1, I1, J1);
         uentry(a.pairs, e2, I2, J2);
         float* T = a.T + (size_t)pb * k * k;
+        unsigned* tmax = F16 ? a.tmax + (size_t)pb * k : nullptr;
         const int m0 = mt * TC_BM, n0 = nt * TC_BN;
         if (a.rot[e2] == 0) {
             for (int idx = threadIdx.x; idx < TC_BM * TC_BN; idx += U_T) {
                 const int m = m0 + idx % TC_BM, j = n0 + idx / TC_BM;
-                if (m < k && j < k) T[m + (size_t)k * j] = a.Ain[umap(I1, J1, b, m) + (size_t)a.lda * umap(I2, J2, b, j)];
+                if (m < k && j < k) {
+                    const float v = a.Ain[umap(I1, J1, b, m) + (size_t)a.lda * umap(I2, J2, b, j)];
+                    T[m + (size_t)k * j] = v;
+                    if (F16 && v != 0.f) atomicMax(tmax + j, __float_as_uint(fabsf(v)));
+                }
             }
             return;
         }
-        GatherF32 la;
+        GatherF32<F16> la;
         la.base = a.Ain;
         la.ld = (size_t)a.lda;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int r = (threadIdx.x + U_T * i) & 127;
             la.rows[i] = m0 + r < k ? umap(I1, J1, b, m0 + r) : -1;
+            la.scale[i] = 1.f;
+        }
+        if (F16) {
+            // row maxima over all K: thread (r, half h) scans columns h, h + 2, ...
+            const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
+            const int row = m0 + r < k ? umap(I1, J1, b, m0 + r) : -1;
+            float mx = 0.f;
+            if (row >= 0)
+                for (int x = h; x < k; x += 2) mx = fmaxf(mx, fabsf(__ldg(a.Ain + row + (size_t)a.lda * umap(I2, J2, b, x))));
+            s_rmax[h][r] = mx;
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int rr = (threadIdx.x + U_T * i) & 127;
+                la.scale[i] = pow2(-exp_of(fmaxf(s_rmax[0][rr], s_rmax[1][rr])));
+            }
         }
         ImageTile lb{a.vimg + (size_t)e2 * ntk * nchk * U_IMG_TILE, nchk, nt};
         struct LA {
-            GatherF32& g;
+            GatherF32<F16>& g;
             int I2, J2, b, k;
             __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I2, J2, b, x) : -1; }); }
             __device__ void store(unsigned char* d) const { g.store(d); }
         } lawrap{la, I2, J2, b, k};
-        tc_tile(nchk, lawrap, lb,
-                [&](int m, int j0, const float (&v)[8]) {
-                    if (m0 + m >= k) return;
+        tc_tile<F16>(nchk, lawrap, lb,
+                     [&](int m, int j0, const float (&v)[8]) {
+                         const bool live = m0 + m < k;
+                         const float up = F16 ? pow2(exp_of(fmaxf(s_rmax[0][m], s_rmax[1][m]))) : 1.f;
+                         float w[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (n0 + j0 + u < k) T[(m0 + m) + (size_t)k * (n0 + j0 + u)] = v[u];
-                },
-                a.err);
+                         for (int u = 0; u < 8; ++u) {
+                             w[u] = v[u] * up;
+                             if (live && n0 + j0 + u < k) T[(m0 + m) + (size_t)k * (n0 + j0 + u)] = w[u];
+                         }
+                         if (F16) {
+                             // column maxima over the warp's 32 rows, one atomic per column
+#pragma unroll
+                             for (int u = 0; u < 8; ++u) {
+                                 float x = live ? fabsf(w[u]) : 0.f;
+                                 for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+                                 if ((threadIdx.x & 31) == 0 && x > 0.f && n0 + j0 + u < k)
+                                     atomicMax(tmax + n0 + j0 + u, __float_as_uint(x));
+                             }
+                         }
+                     },
+                     a.err);
         if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
         return;
     }
@@ -381,36 +449,41 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
         }
         return;
     }
-    GatherF32 la;
+    GatherF32<F16> la;
     la.base = a.Qin;
     la.ld = (size_t)a.ldq;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int r = (threadIdx.x + U_T * i) & 127;
         la.rows[i] = r0 + r < a.qrows ? r0 + r : -1;
+        la.scale[i] = 1.f;
     }
     ImageTile lb{a.vimg + (size_t)e * ntk * nchk * U_IMG_TILE, nchk, nt};
     struct LA {
-        GatherF32& g;
+        GatherF32<F16>& g;
         int I, J, b, k;
         __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I, J, b, x) : -1; }); }
         __device__ void store(unsigned char* d) const { g.store(d); }
     } lawrap{la, I, J, b, k};
-    tc_tile(nchk, lawrap, lb,
-            [&](int m, int j0, const float (&v)[8]) {
-                if (r0 + m >= a.qrows) return;
+    tc_tile<F16>(nchk, lawrap, lb,
+                 [&](int m, int j0, const float (&v)[8]) {
+                     if (r0 + m >= a.qrows) return;
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (n0 + j0 + u < k) a.Qout[(r0 + m) + (size_t)a.ldq * umap(I, J, b, n0 + j0 + u)] = v[u];
-            },
-            a.err);
+                     for (int u = 0; u < 8; ++u)
+                         if (n0 + j0 + u < k) a.Qout[(r0 + m) + (size_t)a.ldq * umap(I, J, b, n0 + j0 + u)] = v[u];
+                 },
+                 a.err);
     if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
 }
 
 // Stage 2: tile (mt, nt) of O_pb = V1^T T_pb, written to A' at (P1 rows, P2
 // columns) and mirrored to (P2 rows, P1 columns), so A' stays symmetric.
+// FP16x3: T's columns are scaled by their maxima from stage 1 and the
+// products scaled back.
+template <bool F16>
 __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
 {
+    __shared__ float s_cscale[TC_BN];
     const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
     const int item = blockIdx.x;
     const int pb = item / (ntk * ntk), rem = item % (ntk * ntk), mt = rem / ntk, nt = rem % ntk;
@@ -434,35 +507,44 @@ __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
         }
         return;
     }
+    if (F16) {
+        for (int j = threadIdx.x; j < TC_BN; j += U_T)
+            s_cscale[j] = n0 + j < k ? pow2(-exp_of(__uint_as_float(a.tmax[(size_t)pb * k + n0 + j]))) : 1.f;
+        __syncthreads();
+    }
     ImageTile la{a.vimg + (size_t)e1 * ntk * nchk * U_IMG_TILE, nchk, mt};
-    KMajorF32 lb;
+    KMajorF32<F16> lb;
     lb.T = T;
     lb.k = k;
     lb.n0 = n0;
     lb.vec4 = (k & 3) == 0;
+    lb.cscale = F16 ? s_cscale : nullptr;
     // 8 consecutive output columns land in 8 consecutive rows of the mirror
     // when they stay inside one block of the pair and the address is 16-byte
     // aligned
     const bool mvec = (b & 7) == 0 && (lda & 3) == 0;
-    tc_tile(nchk, la, lb,
-            [&](int m, int j0, const float (&v)[8]) {
-                if (m0 + m >= k) return;
-                const int gi = umap(I1, J1, b, m0 + m);
-                const int jb = n0 + j0;
+    tc_tile<F16>(nchk, la, lb,
+                 [&](int m, int j0, const float (&v0)[8]) {
+                     if (m0 + m >= k) return;
+                     float v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (jb + u < k) Ao[gi + lda * umap(I2, J2, b, jb + u)] = v[u];
-                if (mvec && jb + 8 <= k) {
-                    float* dst = Ao + umap(I2, J2, b, jb) + lda * gi;
-                    reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-                } else {
+                     for (int u = 0; u < 8; ++u) v[u] = F16 ? v0[u] / s_cscale[j0 + u] : v0[u];
+                     const int gi = umap(I1, J1, b, m0 + m);
+                     const int jb = n0 + j0;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (jb + u < k) Ao[umap(I2, J2, b, jb + u) + lda * gi] = v[u];
-                }
-            },
-            a.err);
+                     for (int u = 0; u < 8; ++u)
+                         if (jb + u < k) Ao[gi + lda * umap(I2, J2, b, jb + u)] = v[u];
+                     if (mvec && jb + 8 <= k) {
+                         float* dst = Ao + umap(I2, J2, b, jb) + lda * gi;
+                         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                         reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+                     } else {
+#pragma unroll
+                         for (int u = 0; u < 8; ++u)
+                             if (jb + u < k) Ao[umap(I2, J2, b, jb + u) + lda * gi] = v[u];
+                     }
+                 },
+                 a.err);
     if (threadIdx.x == 0) atomicAdd(&a.cnt->flops_lowp, 6ull * TC_BM * TC_BN * k);
 }
 
@@ -470,28 +552,38 @@ __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
 
 size_t tc_update_tbuf_floats(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
 
+size_t tc_update_tmax_words(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k; }
+
 size_t tc_update_vimg_bytes(int npairs, int k)
 {
     const size_t ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
     return (size_t)npairs * ntk * nchk * U_IMG_TILE;
 }
 
-cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s)
+template <bool F16>
+static cudaError_t launch_tc_update_t(const TcUpdArgs& a, cudaStream_t s)
 {
     const int ntk = (a.k + TC_BN - 1) / TC_BN, nchk = (a.k + TC_BK - 1) / TC_BK;
     const int npb = a.npairs * (a.npairs - 1) / 2;
     const int n_sand = npb * ntk * ntk;
     const int n_q = a.Qin ? a.npairs * ((a.qrows + TC_BM - 1) / TC_BM) * ntk : 0;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_upd2, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    e = cudaFuncSetAttribute(k_tc_upd2<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
     if (e != cudaSuccess) return e;
-    if (a.npairs > 0) k_tc_split_v<<<a.npairs * ntk * nchk, U_T, 0, s>>>(a.V, a.rot, a.k, ntk, nchk, a.vimg);
+    if (F16 && npb > 0 && (e = cudaMemsetAsync(a.tmax, 0, sizeof(unsigned) * (size_t)npb * a.k, s)) != cudaSuccess)
+        return e;
+    if (a.npairs > 0) k_tc_split_v<F16><<<a.npairs * ntk * nchk, U_T, 0, s>>>(a.V, a.rot, a.k, ntk, nchk, a.vimg);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand + n_q > 0) k_tc_upd1<<<n_sand + n_q, U_T, U_SMEM, s>>>(a, n_sand);
+    if (n_sand + n_q > 0) k_tc_upd1<F16><<<n_sand + n_q, U_T, U_SMEM, s>>>(a, n_sand);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand > 0) k_tc_upd2<<<n_sand, U_T, U_SMEM, s>>>(a);
+    if (n_sand > 0) k_tc_upd2<F16><<<n_sand, U_T, U_SMEM, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s)
+{
+    return a.f16 ? launch_tc_update_t<true>(a, s) : launch_tc_update_t<false>(a, s);
 }
 
 }  // namespace jac

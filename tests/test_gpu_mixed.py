@@ -21,6 +21,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 MIXED = 2
+MIXED_F16 = 3
 
 
 @pytest.fixture(scope="module")
@@ -59,8 +60,9 @@ LOWP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
 @pytest.mark.parametrize("np_,b,ordering,steps", LOWP_CASES)
-def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps):
+def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps, prec):
     import torch
     d = np.linspace(1.0, 2.0 * np_, np_)
     A32 = (np.diag(d) + 0.05 * gen.sym_gaussian(np_, 4000 + np_ + b)).astype(np.float32)
@@ -75,7 +77,7 @@ def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps
         V = np.linalg.solve(Q64, Q_or) if np_ <= 1024 else None
         Ad = jg.colmajor(A32, device="cuda", dtype=torch.float32)
         Qd = jg.colmajor(Q32, device="cuda", dtype=torch.float32)
-        rc = jg.jacobi_syev_step_lowp(Ad, Qd, s, jg.params(b=b, ordering=ordering, precision=MIXED))
+        rc = jg.jacobi_syev_step_lowp(Ad, Qd, s, jg.params(b=b, ordering=ordering, precision=prec))
         assert rc == 0
         Ag, Qg = _np(Ad).astype(np.float64), _np(Qd).astype(np.float64)
         assert np.array_equal(Ag, Ag.T)
@@ -83,6 +85,12 @@ def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps
         c = 2.0 ** -15 + 4 * k * U32
         boundA = c * (aV.T @ np.abs(A64) @ aV) + 1e-30
         boundQ = c * (np.abs(Q64) @ aV) + 1e-30
+        if prec == MIXED_F16:
+            # fp16 splits: 22 bits in the normal range; entries of V and Q
+            # below it (|x| < 2^-14) keep an absolute error of at most 2^-25
+            c16 = 2.0 ** -20 + 4 * k * U32
+            boundA = c16 * (aV.T @ np.abs(A64) @ aV) + 2.0 ** -24 * (np.abs(A64) @ np.ones_like(aV)).max() + 1e-30
+            boundQ = c16 * (np.abs(Q64) @ aV) + 2.0 ** -24 * k + 1e-30
         ra = np.abs(Ag - A_or) / boundA
         rq = np.abs(Qg - Q_or) / boundQ
         assert ra.max() <= 1.0, ra.max()
@@ -104,10 +112,11 @@ def test_lowp_step_without_q_and_arguments(jg):
 
 
 # ------------------------------------------------------------------ full mixed solves
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
 @pytest.mark.parametrize("n,b", [(256, 32), (300, 32), (512, 64), (1024, 128)])
-def test_mixed_solve_uniform_spectrum(jg, n, b):
+def test_mixed_solve_uniform_spectrum(jg, n, b, prec):
     A, lam = gen.sym_known(n, "uniform", seed=4300 + n)
-    w, Q, _, st = jg.syev(A, b=b, precision=MIXED)
+    w, Q, _, st = jg.syev(A, b=b, precision=prec)
     assert st.status == 0
     assert st.sweeps_lowp >= 1 and st.flops_lowp > 0
     check(A, _np(w), _np(Q), np.sort(lam))
@@ -121,10 +130,11 @@ def test_mixed_matches_oracle_eigenvalues(jg):
     check(A, _np(w), _np(Q), w_or)
 
 
-def test_mixed_graded_spectrum(jg):
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+def test_mixed_graded_spectrum(jg, prec):
     A, lam = gen.sym_known(256, "graded", seed=gen.SEEDS["c2g"])
     w_or, *_ = oracle.syev(A, b=32)
-    w, Q, _, st = jg.syev(A, b=32, precision=MIXED)
+    w, Q, _, st = jg.syev(A, b=32, precision=prec)
     assert st.status == 0
     check(A, _np(w), _np(Q), w_or)
 
@@ -173,6 +183,7 @@ def test_mixed_edge_cases(jg):
     A[7, 3] = 0.0
     Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
     assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=MIXED, warm_start=1))[0] == jg.ERR_UNSUPPORTED
+    assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=4))[0] == jg.ERR_UNSUPPORTED
 
 
 def test_mixed_deterministic(jg):
@@ -182,12 +193,13 @@ def test_mixed_deterministic(jg):
     assert np.array_equal(_np(w1), _np(w2)) and np.array_equal(_np(Q1), _np(Q2))
 
 
-def test_mixed_n4096_b64(jg):
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+def test_mixed_n4096_b64(jg, prec):
     """The benchmark's mixed workload size class: against the constructed
     spectrum, with fewer FP64 sweeps than the plain FP64 solve needs."""
     n, b = 4096, 64
     A, lam = gen.sym_known(n, "uniform", seed=gen.SEEDS["c2u"])
-    w, Q, _, st = jg.syev(A, b=b, precision=MIXED)
+    w, Q, _, st = jg.syev(A, b=b, precision=prec)
     assert st.status == 0
     check(A, _np(w), _np(Q), np.sort(lam))
     assert st.sweeps - st.sweeps_lowp <= 4
