@@ -54,7 +54,9 @@ class jacobi_stats(C.Structure):
                 ("update_launches", C.c_longlong),
                 ("flops_fp64", C.c_double), ("flops_update", C.c_double),
                 ("flops_fp32", C.c_double), ("flops_lowp", C.c_double),
-                ("ms_lowp", C.c_double), ("ms_refine", C.c_double)]
+                ("ms_lowp", C.c_double), ("ms_refine", C.c_double),
+                ("ms_pivot_lowp", C.c_double), ("ms_update_lowp", C.c_double),
+                ("flops_refine", C.c_double)]
 
 
 @dataclass
@@ -82,6 +84,9 @@ class Stats:
     flops_lowp: float
     ms_lowp: float
     ms_refine: float
+    ms_pivot_lowp: float
+    ms_update_lowp: float
+    flops_refine: float
     off_hist: list = field(default_factory=list)
 
 
@@ -90,7 +95,7 @@ def _stats(s: jacobi_stats) -> Stats:
                  s.rotations, s.inner_sweeps, s.norm_fro, s.off_initial, s.off_final,
                  s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
                  s.update_launches, s.flops_fp64, s.flops_update, s.flops_fp32, s.flops_lowp,
-                 s.ms_lowp, s.ms_refine,
+                 s.ms_lowp, s.ms_refine, s.ms_pivot_lowp, s.ms_update_lowp, s.flops_refine,
                  list(s.off_hist)[: max(0, min(64, s.sweeps))])
 
 
