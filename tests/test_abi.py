@@ -75,3 +75,35 @@ def test_invalid_schedule_arguments(jg):
         jg.jacobi_ordering_table(0, 1)
     with pytest.raises(ValueError):
         jg.jacobi_ordering_table(7, 8)
+
+
+def _header_struct_fields(name):
+    txt = open(os.path.join(ROOT, "include", "jacobi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r";", txt)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype = decl.split()[0] if not decl.startswith("long long") else "long long"
+        names = decl[len(ctype):].split(",")
+        for nm in names:
+            nm = nm.strip()
+            arr = re.match(r"(\w+)\[(\d+)\]", nm)
+            fields.append((arr.group(1), ctype, int(arr.group(2))) if arr else (nm, ctype, 1))
+    return fields
+
+
+@pytest.mark.parametrize("name", ["jacobi_params", "jacobi_stats"])
+def test_binding_structs_mirror_the_header(jg, name):
+    """Field names, order, C types and array lengths of the ctypes mirrors
+    equal the header's, so the library never writes past the Python struct."""
+    want = _header_struct_fields(name)
+    got = getattr(jg, name)._fields_
+    ctmap = {"int": C.c_int, "double": C.c_double, "long long": C.c_longlong}
+    assert [f[0] for f in want] == [g[0] for g in got]
+    for (nm, ct, ln), (gnm, gty) in zip(want, got):
+        base = ctmap[ct]
+        assert gty == (base * ln if ln > 1 else base), nm
