@@ -138,7 +138,10 @@ struct jacobi_plan {
     DevCounters* d_cnt = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* graph_info = nullptr;        // info pointer baked into the graph
-    bool use_clusters = true;         // EVD orders above the smem size on clusters (JACOBI_BATCHED_CLUSTER=0: L2 slots)
+    int large_mode = 2;               // EVD orders above the smem size: 0 L2 slots, 1 clusters, 2 blocked
+    void* d_blk = nullptr;            // blocked-form slots
+    size_t blk_slot = 0;
+    int blk_grid = 0;
     float last_ms = 0.f;
 };
 
@@ -177,10 +180,45 @@ cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape&
         a.tol = (T)pl->p.inner_tol;
         a.max_sweeps = pl->p.max_sweeps;
         a.cnt = pl->d_cnt;
-        // the prefix of orders above the shared-memory size, by cluster size
+        // the prefix of orders above the shared-memory size
         const size_t cap = device_smem_optin() - 4096;
         int nl = 0;
-        if (pl->use_clusters) {
+        if (pl->large_mode == 2 && pl->d_blk) {
+            // blocked method for the largest orders; in FP64, where both are
+            // bound by the FP64 pipe, orders up to 320 go to clusters (the
+            // scalar method issues fewer operations there: measured on GB300,
+            // 64 matrices of order 256 in 0.12 s on clusters, 0.20 s blocked;
+            // order 384: 0.77 s / 0.69 s)
+            const int blk_min = pl->esize == 8 ? 320 : 0;
+            int nb = 0;
+            while (nb < count) {
+                const int n = pl->h_n[h_list[nb]], k = n + (n & 1);
+                if (k <= sh.smem_kmax || k <= blk_min) break;
+                ++nb;
+            }
+            if ((e = launch_batched_evd_blocked<T>(a, d_list, nb, pl->d_queue + 1, (T*)pl->d_blk, pl->blk_slot,
+                                                   pl->blk_grid, s)) != cudaSuccess)
+                return e;
+            nl = nb;
+            while (nl < count) {
+                const int n = pl->h_n[h_list[nl]], k = n + (n & 1);
+                if (k <= sh.smem_kmax || batched_cluster_size<T>(k, pl->vec, cap) == 0) break;
+                ++nl;
+            }
+            for (int i = nb; i < nl;) {
+                const int n0 = pl->h_n[h_list[i]];
+                const int C = batched_cluster_size<T>(n0 + (n0 & 1), pl->vec, cap);
+                int j = i + 1;
+                while (j < nl) {
+                    const int nj = pl->h_n[h_list[j]];
+                    if (batched_cluster_size<T>(nj + (nj & 1), pl->vec, cap) != C) break;
+                    ++j;
+                }
+                const int kmax = (n0 + C - 1) / C * C;
+                if ((e = launch_batched_evd_cluster<T>(a, d_list + i, j - i, kmax, C, s)) != cudaSuccess) return e;
+                i = j;
+            }
+        } else if (pl->large_mode == 1) {
             while (nl < count) {
                 const int n = pl->h_n[h_list[nl]], k = n + (n & 1);
                 if (k <= sh.smem_kmax) break;
@@ -278,7 +316,12 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
     pl->batch = batch;
     pl->vec = p.want_vectors != 0;
     pl->p = p;
-    if (const char* env = getenv("JACOBI_BATCHED_CLUSTER")) pl->use_clusters = atoi(env) != 0;
+    // JACOBI_BATCHED_LARGE = l2 | cluster | blocked (default) selects the
+    // route of the orders above the shared-memory size
+    if (const char* env = getenv("JACOBI_BATCHED_LARGE")) {
+        if (!strcmp(env, "l2")) pl->large_mode = 0;
+        else if (!strcmp(env, "cluster")) pl->large_mode = 1;
+    }
     if (precision == JACOBI_PREC_FP32 && p.inner_tol == 4.0 * U64) pl->p.inner_tol = 4.0 * U32;
     pl->h_n.assign(h_n, h_n + batch);
     pl->h_m = kind == 1 ? std::vector<int>(h_m, h_m + batch) : pl->h_n;
@@ -331,7 +374,7 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
         cudaMalloc(&pl->d_ldq, sizeof(int) * batch) != cudaSuccess ||
         cudaMalloc(&pl->d_ptrs, sizeof(void*) * 3 * batch) != cudaSuccess ||
         cudaMallocHost(&pl->h_ptrs, sizeof(void*) * 3 * batch) != cudaSuccess ||
-        cudaMalloc(&pl->d_queue, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&pl->d_queue, 2 * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&pl->d_qtab, sizeof(unsigned) * (kBatchedMaxK / 2) * (kBatchedMaxK / 2 - 1) / 2) != cudaSuccess ||
         cudaMalloc(&pl->d_cnt, sizeof(DevCounters)) != cudaSuccess) {
         cudaGetLastError();
@@ -340,6 +383,15 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
     if (kind == 0 && cudaMalloc(&pl->d_scratch, pl->slot_elems * pl->esize * (size_t)maxgrid) != cudaSuccess) {
         cudaGetLastError();
         return fail(JACOBI_ERR_ALLOC);
+    }
+    if (kind == 0 && pl->large_mode == 2) {
+        const int nmax = *std::max_element(pl->h_n.begin(), pl->h_n.end());
+        pl->blk_slot = pl->esize == 8 ? batched_blocked_slot_elems<double>(nmax) : batched_blocked_slot_elems<float>(nmax);
+        pl->blk_grid = device_sms() * (pl->esize == 8 ? batched_blocked_ctas_per_sm<double>() : batched_blocked_ctas_per_sm<float>());
+        if (cudaMalloc(&pl->d_blk, pl->blk_slot * pl->esize * (size_t)pl->blk_grid) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(JACOBI_ERR_ALLOC);
+        }
     }
     memset(pl->h_ptrs, 0, sizeof(void*) * 3 * batch);
     if (cudaMemcpyAsync(pl->d_order, pl->h_order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -511,6 +563,7 @@ extern "C" void jacobi_plan_destroy(jacobi_plan* pl)
     cudaFree(pl->d_queue);
     cudaFree(pl->d_qtab);
     cudaFree(pl->d_scratch);
+    cudaFree(pl->d_blk);
     cudaFree(pl->d_cnt);
     delete pl;
 }

@@ -74,5 +74,17 @@ cudaError_t launch_batched_evd_cluster(const BatchedEvdArgs<T>& a, const int* li
                                        int C, cudaStream_t s);
 template <typename T>
 int batched_svd_occupancy(int threads, int kmax);
+// Matrices above the shared-memory size by the blocked method, one CTA per
+// matrix (persistent over `list`, its own queue word); slots: grid x
+// slot_elems working storage (A and Q, padded).
+template <typename T>
+size_t batched_blocked_smem();
+template <typename T>
+int batched_blocked_ctas_per_sm();
+template <typename T>
+size_t batched_blocked_slot_elems(int nmax);
+template <typename T>
+cudaError_t launch_batched_evd_blocked(const BatchedEvdArgs<T>& a, const int* list, int count, unsigned* queue,
+                                       T* slots, size_t slot_elems, int grid, cudaStream_t s);
 
 }  // namespace jac

@@ -143,24 +143,26 @@ def test_batched_tall_svd_f32(jg):
 
 
 @pytest.mark.parametrize("f32", [False, True])
-def test_batched_cluster_path_against_oracle_and_l2_path(jg, monkeypatch, f32):
-    """Orders above the shared-memory size run on thread-block clusters
-    (one cluster per matrix, order padded to a multiple of the cluster size);
-    the L2-slot path (JACOBI_BATCHED_CLUSTER=0) solves the same matrices."""
+def test_batched_large_orders_every_route_against_oracle(jg, monkeypatch, f32):
+    """Orders above the shared-memory size: the blocked method, one CTA per
+    matrix (default), thread-block clusters (one cluster per matrix, order
+    padded to a multiple of the cluster size) and the L2-slot scalar solve
+    (JACOBI_BATCHED_LARGE = blocked | cluster | l2) all meet the oracle's
+    bounds and agree with each other."""
     import torch
     sizes = [512, 511, 384, 300, 257, 256, 200, 161, 130, 64, 9]
     mats = [gen.sym_gaussian(n, 76, n) for n in sizes]
-    mats[3][17, 5] = np.inf        # a non-finite entry in a cluster-path matrix
+    mats[3][17, 5] = np.inf        # a non-finite entry in a large matrix
     dtype = torch.float32 if f32 else torch.float64
     sc = SCALE32 if f32 else 1.0
     outs = []
-    for env in ("1", "0"):
-        monkeypatch.setenv("JACOBI_BATCHED_CLUSTER", env)
+    for route in ("blocked", "cluster", "l2"):
+        monkeypatch.setenv("JACOBI_BATCHED_LARGE", route)
         As, ws, Qs, info = _mk(jg, mats, dtype)
         rc, st = jg.jacobi_syev_batched(As, ws, Qs, info, jg.params(), f32=f32)
         assert rc == 0
         inf = info.cpu().tolist()
-        assert inf[3] == -100 and all(v == 0 for i, v in enumerate(inf) if i != 3), inf
+        assert inf[3] == -100 and all(v == 0 for i, v in enumerate(inf) if i != 3), (route, inf)
         outs.append([w.double().cpu().numpy() for w in ws])
         for i, (A, w, Q) in enumerate(zip(mats, ws, Qs)):
             if i == 3:
@@ -170,9 +172,10 @@ def test_batched_cluster_path_against_oracle_and_l2_path(jg, monkeypatch, f32):
             Q = Q.double().cpu().numpy()
             w_or = oracle_eig(A)
             nrm2 = np.abs(w_or).max()
-            assert np.abs(w - w_or).max() <= 1e-13 * sc * nrm2, (env, n, np.abs(w - w_or).max() / nrm2)
-            assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * sc * np.linalg.norm(A)
-            assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * sc * n
-    for i in range(len(mats)):
-        if i != 3:
-            assert np.abs(outs[0][i] - outs[1][i]).max() <= 2e-13 * sc * np.abs(outs[1][i]).max()
+            assert np.abs(w - w_or).max() <= 1e-13 * sc * nrm2, (route, n, np.abs(w - w_or).max() / nrm2)
+            assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * sc * np.linalg.norm(A), (route, n)
+            assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * sc * n, (route, n)
+    for o in outs[1:]:
+        for i in range(len(mats)):
+            if i != 3:
+                assert np.abs(outs[0][i] - o[i]).max() <= 2e-13 * sc * np.abs(o[i]).max()
