@@ -35,9 +35,15 @@ constexpr int BK = 32;            // pivot order 2b
 constexpr int BLD = 33;           // padded leading dimension of 32 x 32 tiles in shared memory
 constexpr int BMAXP = kBatchedMaxK / BK;   // pairs per step at most (16)
 
+// Leading dimension of the staging tiles and of the kept V's: FP32 uses 36
+// (16-byte rows for the vectorised, register-blocked 32 x 32 products), FP64
+// 33 (conflict-free scalar access).
+template <typename T>
+constexpr int sld() { return sizeof(T) == 4 ? 36 : BLD; }
+
 template <typename T>
 struct BlkWarp {                  // per-warp scratch
-    T tile[BK * BLD];             // pivot (lower triangle) / staging of a 32 x 32 block
+    alignas(16) T tile[BK * sld<T>()];   // pivot (lower triangle, ld BLD) / staging of a 32 x 32 block
     T dlo[BK];
     T rs[BK / 2], rtau[BK / 2], rt[BK / 2], rapq[BK / 2];
     int rp[BK / 2], rq[BK / 2], ron[BK / 2];
@@ -45,7 +51,28 @@ struct BlkWarp {                  // per-warp scratch
 };
 
 template <typename T>
-constexpr int blk_threads() { return 256; }
+constexpr int blk_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+// FP32: acc(i, j) += sum_k A(8 ty + i, k) B(k, 4 tx + j), ty = lane / 8,
+// tx = lane % 8, for 32 x 32 x 32 operands in shared memory: A column-major
+// (A(m, k) at A[m + 36 k]), B row-major (B(k, n) at B[n + 36 k]); two 16-byte
+// loads of A and one of B feed 32 FMAs.
+__device__ __forceinline__ void mm32(const float* A, const float* B, float (&acc)[8][4], int lane)
+{
+    const int ty = lane >> 3, tx = lane & 7;
+#pragma unroll 4
+    for (int k = 0; k < BK; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(A + 8 * ty + 36 * k);
+        const float4 a1 = *reinterpret_cast<const float4*>(A + 8 * ty + 4 + 36 * k);
+        const float4 b = *reinterpret_cast<const float4*>(B + 4 * tx + 36 * k);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+}
 
 __device__ __forceinline__ int bmap(int I, int J, int x) { return x < BB ? I * BB + x : J * BB + (x - BB); }
 
@@ -142,8 +169,9 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
                                                                         size_t slot_elems)
 {
     extern __shared__ __align__(16) unsigned char bsm[];
-    T* Vs = (T*)bsm;                                          // [BMAXP][BK * BLD] pivot V's of the step
-    BlkWarp<T>* warps = (BlkWarp<T>*)(Vs + (size_t)BMAXP * BK * BLD);
+    constexpr int VLD = sld<T>();
+    T* Vs = (T*)bsm;                                          // [BMAXP][BK * VLD] pivot V's of the step
+    BlkWarp<T>* warps = (BlkWarp<T>*)(Vs + (size_t)BMAXP * BK * VLD);
     __shared__ int s_item, s_rot, s_prot[BMAXP];
     __shared__ unsigned long long s_flops;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -187,7 +215,7 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
                 for (int e = wid; e < npairs; e += nw) {
                     int I, J;
                     rr_pair(N, s, e, I, J);
-                    T* V = Vs + (size_t)e * BK * BLD;
+                    T* V = Vs + (size_t)e * BK * VLD;   // accumulated column-major, ld BLD
                     for (int c = 0; c < BK; ++c) {
                         // lane = row: the lower triangle of the pivot, and V = I
                         if (lane >= c) w.tile[lane * BLD + c] = Aw[bmap(I, J, lane) + (size_t)np * bmap(I, J, c)];
@@ -224,12 +252,18 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
                         Aw[bmap(I, J, w.dest[i]) + (size_t)np * bmap(I, J, w.dest[j])] = v;
                     }
                     if (rot > 0) {
+                        // V <- V P; FP32 keeps it row-major (ld 36) for the products
                         T col[BK];
 #pragma unroll
                         for (int c = 0; c < BK; ++c) col[c] = V[lane + BLD * c];
                         __syncwarp();
+                        if constexpr (sizeof(T) == 4) {
 #pragma unroll
-                        for (int c = 0; c < BK; ++c) V[lane + BLD * w.dest[c]] = col[c];
+                            for (int c = 0; c < BK; ++c) V[w.dest[c] + VLD * lane] = col[c];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < BK; ++c) V[lane + BLD * w.dest[c]] = col[c];
+                        }
                     }
                     if (lane == 0) {
                         s_prot[e] = rot;
@@ -255,38 +289,69 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
                         int I1, J1, I2, J2;
                         rr_pair(N, s, e1, I1, J1);
                         rr_pair(N, s, e2, I2, J2);
-                        const T* V1 = Vs + (size_t)e1 * BK * BLD;
-                        const T* V2 = Vs + (size_t)e2 * BK * BLD;
+                        const T* V1 = Vs + (size_t)e1 * BK * VLD;
+                        const T* V2 = Vs + (size_t)e2 * BK * VLD;
                         const size_t row = bmap(I1, J1, lane);
-                        for (int c = 0; c < BK; ++c) S[lane + BLD * c] = Aw[row + (size_t)np * bmap(I2, J2, c)];
+                        for (int c = 0; c < BK; ++c) S[lane + VLD * c] = Aw[row + (size_t)np * bmap(I2, J2, c)];
                         __syncwarp();
-                        // lane j: T(:, j) = A_blk V2(:, j), then O(:, j) = V1^T T(:, j)
-                        T t[BK];
+                        if constexpr (sizeof(T) == 4) {
+                            const int ty = lane >> 3, tx = lane & 7;
+                            float acc[8][4];
 #pragma unroll
-                        for (int l = 0; l < BK; ++l) t[l] = T(0);
-                        if (r2) {
-                            for (int c = 0; c < BK; ++c) {
-                                const T v = V2[c + BLD * lane];
+                            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                                for (int l = 0; l < BK; ++l) t[l] = fma(S[l + BLD * c], v, t[l]);
+                                for (int j = 0; j < 4; ++j) acc[i][j] = r2 ? 0.f : S[(8 * ty + i) + VLD * (4 * tx + j)];
+                            if (r2) mm32(S, V2, acc, lane);                    // T = A_blk V2
+                            __syncwarp();
+                            if (r1) {
+                                // T row-major into S, then O = V1^T T (V1 row-major = V1^T column-major)
+#pragma unroll
+                                for (int i = 0; i < 8; ++i)
+                                    *reinterpret_cast<float4*>(S + 4 * tx + VLD * (8 * ty + i)) =
+                                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                                __syncwarp();
+#pragma unroll
+                                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+                                mm32(V1, S, acc, lane);
+                                __syncwarp();
                             }
+                            // O column-major (ld BLD) for the coalesced write-back
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) S[(8 * ty + i) + BLD * (4 * tx + j)] = acc[i][j];
+                            __syncwarp();
                         } else {
+                            // lane j: T(:, j) = A_blk V2(:, j), then O(:, j) = V1^T T(:, j)
+                            T t[BK];
 #pragma unroll
-                            for (int l = 0; l < BK; ++l) t[l] = S[l + BLD * lane];
-                        }
-                        __syncwarp();
-                        if (r1) {
-                            for (int i = 0; i < BK; ++i) {
-                                T o = T(0);
+                            for (int l = 0; l < BK; ++l) t[l] = T(0);
+                            if (r2) {
+                                for (int c = 0; c < BK; ++c) {
+                                    const T v = V2[c + BLD * lane];
 #pragma unroll
-                                for (int l = 0; l < BK; ++l) o = fma(V1[l + BLD * i], t[l], o);
-                                S[i + BLD * lane] = o;
+                                    for (int l = 0; l < BK; ++l) t[l] = fma(S[l + BLD * c], v, t[l]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int l = 0; l < BK; ++l) t[l] = S[l + BLD * lane];
                             }
-                        } else {
+                            __syncwarp();
+                            if (r1) {
+                                for (int i = 0; i < BK; ++i) {
+                                    T o = T(0);
 #pragma unroll
-                            for (int i = 0; i < BK; ++i) S[i + BLD * lane] = t[i];
+                                    for (int l = 0; l < BK; ++l) o = fma(V1[l + BLD * i], t[l], o);
+                                    S[i + BLD * lane] = o;
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < BK; ++i) S[i + BLD * lane] = t[i];
+                            }
+                            __syncwarp();
                         }
-                        __syncwarp();
                         // O(lane, c) to (P1 row lane, P2 column c); the mirror
                         // O(r, lane) to (P2 row lane, P1 column r)
                         for (int c = 0; c < BK; ++c) Aw[row + (size_t)np * bmap(I2, J2, c)] = S[lane + BLD * c];
@@ -298,20 +363,35 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
                         if (!s_prot[e]) continue;                  // V = I
                         int I, J;
                         rr_pair(N, s, e, I, J);
-                        const T* V = Vs + (size_t)e * BK * BLD;
-                        for (int c = 0; c < BK; ++c) S[lane + BLD * c] = Qw[(r0 + lane) + (size_t)np * bmap(I, J, c)];
+                        const T* V = Vs + (size_t)e * BK * VLD;
+                        for (int c = 0; c < BK; ++c) S[lane + VLD * c] = Qw[(r0 + lane) + (size_t)np * bmap(I, J, c)];
                         __syncwarp();
-                        T o[BK];
+                        if constexpr (sizeof(T) == 4) {
+                            const int ty = lane >> 3, tx = lane & 7;
+                            float acc[8][4];
 #pragma unroll
-                        for (int r = 0; r < BK; ++r) o[r] = T(0);
-                        for (int c = 0; c < BK; ++c) {
-                            const T v = V[c + BLD * lane];
+                            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                            for (int r = 0; r < BK; ++r) o[r] = fma(S[r + BLD * c], v, o[r]);
+                                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+                            mm32(S, V, acc, lane);
+                            __syncwarp();
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) S[(8 * ty + i) + BLD * (4 * tx + j)] = acc[i][j];
+                        } else {
+                            T o[BK];
+#pragma unroll
+                            for (int r = 0; r < BK; ++r) o[r] = T(0);
+                            for (int c = 0; c < BK; ++c) {
+                                const T v = V[c + BLD * lane];
+#pragma unroll
+                                for (int r = 0; r < BK; ++r) o[r] = fma(S[r + BLD * c], v, o[r]);
+                            }
+                            __syncwarp();
+#pragma unroll
+                            for (int r = 0; r < BK; ++r) S[r + BLD * lane] = o[r];
                         }
-                        __syncwarp();
-#pragma unroll
-                        for (int r = 0; r < BK; ++r) S[r + BLD * lane] = o[r];
                         __syncwarp();
                         for (int c = 0; c < BK; ++c) Qw[(r0 + lane) + (size_t)np * bmap(I, J, c)] = S[lane + BLD * c];
                         if (lane == 0) atomicAdd(&s_flops, 2ull * BK * BK * BK);
@@ -366,7 +446,7 @@ __global__ void __launch_bounds__(blk_threads<T>()) k_batched_evd_blocked(Batche
 template <typename T>
 size_t batched_blocked_smem()
 {
-    return (size_t)BMAXP * BK * BLD * sizeof(T) + (size_t)(blk_threads<T>() / 32) * sizeof(BlkWarp<T>);
+    return (size_t)BMAXP * BK * sld<T>() * sizeof(T) + (size_t)(blk_threads<T>() / 32) * sizeof(BlkWarp<T>);
 }
 
 template <typename T>
