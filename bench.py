@@ -87,6 +87,26 @@ WORKLOADS = {
                       desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                            "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, "
                            "b=128, lam ~ U[-1,1], eigenvalues + full Q, off <= 1e-14 ||A||_F"),
+    "mixed4096f16": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=3,
+                         refine_steps=2, ref_sweeps=13,
+                         desc="mixed-precision two-sided block Jacobi EVD (fp16 hi/lo x3 tensor-core "
+                              "updates with power-of-two scaling, FP64 pivots, FP64 refinement + closing "
+                              "sweeps), n=4096, b=64, lam ~ U[-1,1], eigenvalues + full Q"),
+    "mixed4096tf32": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=4,
+                          refine_steps=2, ref_sweeps=13,
+                          desc="mixed-precision two-sided block Jacobi EVD (tf32 big/small x3 tensor-core "
+                               "updates, FP64 pivots, FP64 refinement + closing sweeps), n=4096, b=64, "
+                               "lam ~ U[-1,1], eigenvalues + full Q"),
+    "mixed8192f16": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=3,
+                         refine_steps=1, ref_sweeps=14,
+                         desc="mixed-precision two-sided block Jacobi EVD (fp16 hi/lo x3 tensor-core "
+                              "updates with power-of-two scaling, FP64 pivots, FP64 refinement + closing "
+                              "sweeps), n=8192, b=128, lam ~ U[-1,1], eigenvalues + full Q"),
+    "mixed8192tf32": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=4,
+                          refine_steps=1, ref_sweeps=14,
+                          desc="mixed-precision two-sided block Jacobi EVD (tf32 big/small x3 tensor-core "
+                               "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, b=128, "
+                               "lam ~ U[-1,1], eigenvalues + full Q"),
     "evd8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, ref_sweeps=14,
                     desc="plain FP64 two-sided block Jacobi EVD, n=8192, b=128, round-robin, "
                          "lam ~ U[-1,1], eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
@@ -555,13 +575,13 @@ def run_gpu(args, wl):
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == 0 else "bf16x3+f32+f64",
+                "dtype": "f64" if prec == 0 else {2: "bf16x3", 3: "fp16x3", 4: "tf32x3"}[prec] + "+f32+f64",
                 "data": "synthetic (seeded; see config)",
                 "config": {"workload": wl["desc"], "b": b,
                            "n": wl["n"], **({"m": wl["m"]} if "m" in wl else {}),
                            "seed": wl["seed"], "parallelism": f"replicas x{world}",
-                           **({"precision": "mixed bf16x3", "refine_steps": wl.get("refine_steps")}
-                              if prec else {}),
+                           **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3"}[prec],
+                               "refine_steps": wl.get("refine_steps")} if prec else {}),
                            "l2": "inputs larger than L2 (working A, Q double-buffered: "
                                  "4 x n^2 x 8 B)"},
                 "eff_tflops_issued": (sum(st_.flops_fp64 + st_.flops_lowp for st_ in stats)

@@ -59,7 +59,8 @@ extern "C" {
  *                 the FP64 refinement and closing sweeps (jacobi_syev).
  *  MIXED_FP16X3:  the same with fp16 hi/lo splits (22 bits per operand), the
  *                 FP32 operands scaled by powers of two per row / column.
- *  MIXED_TF32:    reserved (returns JACOBI_ERR_UNSUPPORTED). */
+ *  MIXED_TF32:    the same with tf32 big/small splits (x = big + small, big =
+ *                 x with its low 13 mantissa bits cleared; kind::tf32). */
 #define JACOBI_PREC_FP64 0
 #define JACOBI_PREC_FP32 1
 #define JACOBI_PREC_MIXED_BF16X3 2
@@ -328,8 +329,8 @@ int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, c
  * splits with power-of-two row/column scaling for MIXED_FP16X3).  A is a full
  * symmetric np x np FP32 matrix (exactly symmetric), np = N * p->b with N
  * even for round-robin; Q is np x np FP32 or NULL; both device, column-major,
- * updated in place.  p->precision must be JACOBI_PREC_MIXED_BF16X3 or
- * JACOBI_PREC_MIXED_FP16X3.
+ * updated in place.  p->precision must be JACOBI_PREC_MIXED_BF16X3,
+ * JACOBI_PREC_MIXED_FP16X3 or JACOBI_PREC_MIXED_TF32 (tf32 big/small splits).
  * Returns 0, -k for an invalid argument, JACOBI_ERR_UNSUPPORTED for another
  * precision, JACOBI_ERR_TIMEOUT if a bounded tensor-core wait ran out,
  * JACOBI_ERR_CUDA / JACOBI_ERR_ALLOC.  Allocates its workspace

@@ -41,7 +41,7 @@ struct LowpState {
     float* T;
     unsigned char* vimg;
     unsigned* tmax;
-    int f16;
+    int kind;
     double* Vb;
     int* rot;
     double* gscratch;
@@ -86,7 +86,7 @@ cudaError_t launch_step32(const LowpState& L, int s, int cur, cudaStream_t cs, d
     ua.T = L.T;
     ua.vimg = L.vimg;
     ua.tmax = L.tmax;
-    ua.f16 = L.f16;
+    ua.kind = L.kind;
     ua.pairs = L.dpairs + p0;
     ua.npairs = nps;
     ua.b = L.b;
@@ -172,7 +172,8 @@ int run_lowp_sweeps(LowpState& L, const jacobi_params& p, int& cur, double targe
 int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const jacobi_params& pin,
                jacobi_stats* st, cudaStream_t s)
 {
-    if (pin.precision != JACOBI_PREC_MIXED_BF16X3 && pin.precision != JACOBI_PREC_MIXED_FP16X3)
+    if (pin.precision != JACOBI_PREC_MIXED_BF16X3 && pin.precision != JACOBI_PREC_MIXED_FP16X3 &&
+        pin.precision != JACOBI_PREC_MIXED_TF32)
         return JACOBI_ERR_UNSUPPORTED;
     if (pin.warm_start) return JACOBI_ERR_UNSUPPORTED;
     jacobi_params p = pin;
@@ -226,7 +227,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.T = ws.get<float>(tc_update_tbuf_floats(E.ord.dev_per_step, k));
     L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(E.ord.dev_per_step, k));
     L.tmax = ws.get<unsigned>(tc_update_tmax_words(E.ord.dev_per_step, k));
-    L.f16 = p.precision == JACOBI_PREC_MIXED_FP16X3;
+    L.kind = p.precision == JACOBI_PREC_MIXED_FP16X3 ? 1 : (p.precision == JACOBI_PREC_MIXED_TF32 ? 2 : 0);
     L.err = ws.get<int>(1);
     if (ws.failed) return JACOBI_ERR_ALLOC;
     L.pcl = E.pcl;
@@ -413,7 +414,8 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     if (pin) p = *pin; else jacobi_params_default(&p);
     int e = check_params(p);
     if (e) return e == -7 ? -6 : e;
-    if (p.precision != JACOBI_PREC_MIXED_BF16X3 && p.precision != JACOBI_PREC_MIXED_FP16X3)
+    if (p.precision != JACOBI_PREC_MIXED_BF16X3 && p.precision != JACOBI_PREC_MIXED_FP16X3 &&
+        p.precision != JACOBI_PREC_MIXED_TF32)
         return JACOBI_ERR_UNSUPPORTED;
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2) return -1;
@@ -440,7 +442,7 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     L.T = ws.get<float>(tc_update_tbuf_floats(ord.dev_per_step, k));
     L.vimg = ws.get<unsigned char>(tc_update_vimg_bytes(ord.dev_per_step, k));
     L.tmax = ws.get<unsigned>(tc_update_tmax_words(ord.dev_per_step, k));
-    L.f16 = p.precision == JACOBI_PREC_MIXED_FP16X3;
+    L.kind = p.precision == JACOBI_PREC_MIXED_FP16X3 ? 1 : (p.precision == JACOBI_PREC_MIXED_TF32 ? 2 : 0);
     L.Vb = ws.get<double>((size_t)ord.max_pairs * 2 * k * k);
     L.rot = ws.get<int>(ord.max_pairs);
     const size_t gsz = pivot_gscratch_doubles(k);

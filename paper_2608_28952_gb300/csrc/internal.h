@@ -153,7 +153,7 @@ struct TcUpdArgs {
     const double* V; const int* rot;            // pivot kernel outputs (FP64 V, V^T)
     unsigned char* vimg;                        // per pair: V split into hi/lo operand tiles
     unsigned* tmax;                             // FP16x3: per pair-block column maxima of T
-    int f16;                                    // 0: bf16 hi/lo (BF16x3), 1: fp16 hi/lo (FP16x3)
+    int kind;                                   // 0: bf16 hi/lo, 1: fp16 hi/lo (scaled), 2: tf32 big/small
     int* err;                                   // set on a timed-out tensor-core wait
     DevCounters* cnt;
 };

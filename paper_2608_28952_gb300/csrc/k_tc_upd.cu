@@ -45,8 +45,31 @@ namespace {
 
 constexpr int U_T = 256;
 constexpr int U_NS = 3;
-constexpr int U_SMEM = U_NS * TC_STAGE_BYTES + 1024;
-constexpr int U_IMG_TILE = 2 * TC_TILE_BYTES;   // hi + lo of one 128 x 32 operand tile
+
+// Operand kinds: 0 bf16 hi/lo, 1 fp16 hi/lo (power-of-two scaled), 2 tf32
+// big/small (x = big + small, big = x with its low 13 mantissa bits cleared,
+// the tensor core reading the top 19 bits of each).
+template <int KIND>
+struct KT {
+    static constexpr int EB = KIND == 2 ? 4 : 2;            // bytes per element in shared memory
+    static constexpr int TILE = TC_BM * TC_BK * EB;          // one 128 x 32 part (8 or 16 KB)
+    static constexpr int STAGE = 4 * TILE;                   // A hi, A lo, B hi, B lo
+    static constexpr int SMEM = U_NS * STAGE + 1024;
+    static constexpr int IMG = 2 * TILE;                     // hi + lo of one operand tile
+    static constexpr int SBO = KIND == 2 ? 1024 : 512;       // next 8-row group of core matrices
+    static constexpr int KSTEP = KIND == 2 ? 8 : 16;         // K of one MMA
+};
+
+// Byte offset of element (r, k) in a part: 8 x 16-byte core matrices, K-major
+// (8 bf16/fp16 or 4 tf32 values per core-matrix row), no swizzle.
+template <int KIND>
+__device__ __forceinline__ uint32_t toff(int r, int k)
+{
+    if constexpr (KIND == 2)
+        return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    else
+        return tile_off(r, k);
+}
 
 __device__ __forceinline__ int umap(int I, int J, int b, int x) { return x < b ? I * b + x : J * b + (x - b); }
 
@@ -93,6 +116,32 @@ __device__ __forceinline__ Pack8 split8(const float (&x)[8], float scale = 1.f)
     return p;
 }
 
+// Eight consecutive K values (r, kk0..kk0+7) of an operand split into the
+// hi part at dst and the lo part at dst + TILE.
+template <int KIND>
+__device__ __forceinline__ void store8(unsigned char* dst, int r, int kk0, const float (&x)[8], float scale)
+{
+    if constexpr (KIND == 2) {
+        float big[8], sml[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float v = x[u] * scale;
+            big[u] = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+            sml[u] = v - big[u];
+        }
+        const uint32_t o0 = toff<2>(r, kk0), o1 = toff<2>(r, kk0 + 4);
+        *reinterpret_cast<float4*>(dst + o0) = make_float4(big[0], big[1], big[2], big[3]);
+        *reinterpret_cast<float4*>(dst + o1) = make_float4(big[4], big[5], big[6], big[7]);
+        *reinterpret_cast<float4*>(dst + KT<2>::TILE + o0) = make_float4(sml[0], sml[1], sml[2], sml[3]);
+        *reinterpret_cast<float4*>(dst + KT<2>::TILE + o1) = make_float4(sml[4], sml[5], sml[6], sml[7]);
+    } else {
+        const Pack8 p = split8<KIND == 1>(x, scale);
+        const uint32_t o = tile_off(r, kk0);
+        *reinterpret_cast<uint4*>(dst + o) = p.hi;
+        *reinterpret_cast<uint4*>(dst + KT<KIND>::TILE + o) = p.lo;
+    }
+}
+
 // Power-of-two scaling: e with mx * 2^-e in [0.5, 1) (0 for mx == 0), and 2^e.
 __device__ __forceinline__ int exp_of(float mx)
 {
@@ -111,7 +160,7 @@ __device__ __forceinline__ float pow2(int e) { return __int_as_float((127 + e) <
 // FP32 gather: element (r, kk) = base[row(r) + ld * col(c * 32 + kk)], 0 where
 // row < 0 or col < 0.  Thread items (r, g): r = item % 128, g = item / 128
 // (eight consecutive K values), items tid and tid + 256.
-template <bool F16>
+template <int KIND>
 struct GatherF32 {
     const float* base;
     size_t ld;
@@ -138,10 +187,7 @@ struct GatherF32 {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, r = item & 127, g = item >> 7;
-            const Pack8 p = split8<F16>(v[i], scale[i]);
-            const uint32_t o = tile_off(r, g * 8);
-            *reinterpret_cast<uint4*>(dst + o) = p.hi;
-            *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+            store8<KIND>(dst, r, g * 8, v[i], scale[i]);
         }
     }
 };
@@ -149,7 +195,7 @@ struct GatherF32 {
 // K-major FP32 (T of stage 2 as the B operand): element (n, kk) =
 // T[(c * 32 + kk) + k * (n0 + n)], 0 outside k x k.  Items (n, g) with
 // g = item % 4, n = item / 4, so a warp reads 128 contiguous bytes per n.
-template <bool F16>
+template <int KIND>
 struct KMajorF32 {
     const float* T;
     int k, n0;
@@ -181,30 +227,29 @@ struct KMajorF32 {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, g = item & 3, n = item >> 2;
-            const Pack8 p = split8<F16>(v[i], cscale ? cscale[n] : 1.f);
-            const uint32_t o = tile_off(n, g * 8);
-            *reinterpret_cast<uint4*>(dst + o) = p.hi;
-            *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+            store8<KIND>(dst, n, g * 8, v[i], cscale ? cscale[n] : 1.f);
         }
     }
 };
 
-// Pre-split image tile: 16 KB copied as 4 x 16 bytes per thread.
+// Pre-split image tile (hi and lo parts, 16 or 32 KB) copied 16 bytes at a time.
+template <int KIND>
 struct ImageTile {
-    const unsigned char* img;   // tile (tile index t, chunk c) at img + (t * nchk + c) * 16 KB
+    static constexpr int NV = KT<KIND>::IMG / 16 / U_T;
+    const unsigned char* img;   // tile (tile index t, chunk c) at img + (t * nchk + c) * IMG
     int nchk;
     int t;
-    uint4 v[4];
+    uint4 v[NV];
     __device__ __forceinline__ void load(int c)
     {
-        const uint4* src = reinterpret_cast<const uint4*>(img + ((size_t)t * nchk + c) * U_IMG_TILE);
+        const uint4* src = reinterpret_cast<const uint4*>(img + ((size_t)t * nchk + c) * KT<KIND>::IMG);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = __ldg(src + threadIdx.x + U_T * i);
+        for (int i = 0; i < NV; ++i) v[i] = __ldg(src + threadIdx.x + U_T * i);
     }
     __device__ __forceinline__ void store(unsigned char* dst) const
     {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) reinterpret_cast<uint4*>(dst)[threadIdx.x + U_T * i] = v[i];
+        for (int i = 0; i < NV; ++i) reinterpret_cast<uint4*>(dst)[threadIdx.x + U_T * i] = v[i];
     }
 };
 
@@ -212,7 +257,7 @@ struct ImageTile {
 // acc(128 x 128) = Aop * Bop over nchk chunks of 32.  LA / LB: loaders with
 // load(c) / store(dst); EP(m, j0, v[8]): the epilogue for row m, columns
 // j0..j0+7.
-template <bool F16, class LA, class LB, class EP>
+template <int KIND, class LA, class LB, class EP>
 __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
 {
     extern __shared__ __align__(1024) unsigned char usm[];
@@ -238,7 +283,9 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = F16 ? idesc_f16(TC_BM, TC_BN) : idesc_bf16(TC_BM, TC_BN);
+    const uint32_t idesc = KIND == 2 ? idesc_tf32(TC_BM, TC_BN)
+                                     : (KIND == 1 ? idesc_f16(TC_BM, TC_BN) : idesc_bf16(TC_BM, TC_BN));
+    constexpr int TB = KT<KIND>::TILE, SBO = KT<KIND>::SBO;
     uint32_t uses[U_NS];
 #pragma unroll
     for (int s = 0; s < U_NS; ++s) uses[s] = 0;
@@ -247,11 +294,11 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
     lb.load(0);
     for (int c = 0; c < nchk; ++c) {
         const int s = c % U_NS;
-        unsigned char* st = base + s * TC_STAGE_BYTES;
+        unsigned char* st = base + s * KT<KIND>::STAGE;
         // the MMAs that last read this stage (chunk c - U_NS) must be complete
         if (c >= U_NS && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
         la.store(st);
-        lb.store(st + 2 * TC_TILE_BYTES);
+        lb.store(st + 2 * TB);
         if (c + 1 < nchk) {  // next chunk's loads in flight during this chunk's MMAs
             la.load(c + 1);
             lb.load(c + 1);
@@ -261,26 +308,41 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
         if (s_fail) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TC_TILE_BYTES;
-            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
+            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TB;
+            const uint32_t b_hi = a_hi + 2 * TB, b_lo = a_hi + 3 * TB;
 #pragma unroll
-            for (int ks = 0; ks < TC_BK / 16; ++ks) {
-                const uint32_t koff = ks * 2 * 128;
-                const uint64_t dah = smem_desc(a_hi + koff, 128, 512), dal = smem_desc(a_lo + koff, 128, 512);
-                const uint64_t dbh = smem_desc(b_hi + koff, 128, 512), dbl = smem_desc(b_lo + koff, 128, 512);
+            for (int ks = 0; ks < TC_BK / KT<KIND>::KSTEP; ++ks) {
+                const uint32_t koff = ks * 2 * 128;   // two core matrices along K per MMA
+                const uint64_t dah = smem_desc(a_hi + koff, 128, SBO), dal = smem_desc(a_lo + koff, 128, SBO);
+                const uint64_t dbh = smem_desc(b_hi + koff, 128, SBO), dbl = smem_desc(b_lo + koff, 128, SBO);
                 const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+                if constexpr (KIND == 2) {
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+                } else {
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&s_bar[s]))
@@ -324,7 +386,7 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
 // Image of V_P per pair (skipped for pairs without rotation): tile (nt, c)
 // holds element (kk, n) = V_P(c * 32 + kk, nt * 128 + n), rounded to FP32
 // then split, at tile_off(n, kk).
-template <bool F16>
+template <int KIND>
 __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V, const int* __restrict__ rot,
                                                     int k, int ntk, int nchk, unsigned char* __restrict__ img)
 {
@@ -332,17 +394,14 @@ __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V
     const int nt = rem / nchk, c = rem % nchk;
     if (rot[e] == 0) return;
     const double* Ve = V + (size_t)e * 2 * k * k;
-    unsigned char* dst = img + (size_t)tile * U_IMG_TILE;
+    unsigned char* dst = img + (size_t)tile * KT<KIND>::IMG;
     for (int i = 0; i < 2; ++i) {
         const int item = threadIdx.x + U_T * i, g = item & 3, nn = item >> 2;
         const int n = nt * TC_BN + nn, kk0 = c * TC_BK + g * 8;
         float x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = (n < k && kk0 + u < k) ? (float)Ve[(kk0 + u) + (size_t)k * n] : 0.f;
-        const Pack8 p = split8<F16>(x);
-        const uint32_t o = tile_off(nn, g * 8);
-        *reinterpret_cast<uint4*>(dst + o) = p.hi;
-        *reinterpret_cast<uint4*>(dst + TC_TILE_BYTES + o) = p.lo;
+        store8<KIND>(dst, nn, kk0 - c * TC_BK, x, 1.f);
     }
 }
 
@@ -351,9 +410,10 @@ __global__ void __launch_bounds__(U_T) k_tc_split_v(const double* __restrict__ V
 // (V = I) gives an exact copy instead of a product.  FP16x3: the rows of the
 // A tile are scaled by their maxima over K (a first pass over the tile's
 // rows), and the epilogue records every T column's maximum for stage 2.
-template <bool F16>
+template <int KIND>
 __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
 {
+    constexpr bool F16 = KIND == 1;
     __shared__ float s_rmax[2][TC_BM];
     const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
     int item = blockIdx.x;
@@ -377,7 +437,7 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
             }
             return;
         }
-        GatherF32<F16> la;
+        GatherF32<KIND> la;
         la.base = a.Ain;
         la.ld = (size_t)a.lda;
 #pragma unroll
@@ -401,14 +461,14 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
                 la.scale[i] = pow2(-exp_of(fmaxf(s_rmax[0][rr], s_rmax[1][rr])));
             }
         }
-        ImageTile lb{a.vimg + (size_t)e2 * ntk * nchk * U_IMG_TILE, nchk, nt};
+        ImageTile<KIND> lb{a.vimg + (size_t)e2 * ntk * nchk * KT<KIND>::IMG, nchk, nt};
         struct LA {
-            GatherF32<F16>& g;
+            GatherF32<KIND>& g;
             int I2, J2, b, k;
             __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I2, J2, b, x) : -1; }); }
             __device__ void store(unsigned char* d) const { g.store(d); }
         } lawrap{la, I2, J2, b, k};
-        tc_tile<F16>(nchk, lawrap, lb,
+        tc_tile<KIND>(nchk, lawrap, lb,
                      [&](int m, int j0, const float (&v)[8]) {
                          const bool live = m0 + m < k;
                          const float up = F16 ? pow2(exp_of(fmaxf(s_rmax[0][m], s_rmax[1][m]))) : 1.f;
@@ -449,7 +509,7 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
         }
         return;
     }
-    GatherF32<F16> la;
+    GatherF32<KIND> la;
     la.base = a.Qin;
     la.ld = (size_t)a.ldq;
 #pragma unroll
@@ -458,14 +518,14 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
         la.rows[i] = r0 + r < a.qrows ? r0 + r : -1;
         la.scale[i] = 1.f;
     }
-    ImageTile lb{a.vimg + (size_t)e * ntk * nchk * U_IMG_TILE, nchk, nt};
+    ImageTile<KIND> lb{a.vimg + (size_t)e * ntk * nchk * KT<KIND>::IMG, nchk, nt};
     struct LA {
-        GatherF32<F16>& g;
+        GatherF32<KIND>& g;
         int I, J, b, k;
         __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I, J, b, x) : -1; }); }
         __device__ void store(unsigned char* d) const { g.store(d); }
     } lawrap{la, I, J, b, k};
-    tc_tile<F16>(nchk, lawrap, lb,
+    tc_tile<KIND>(nchk, lawrap, lb,
                  [&](int m, int j0, const float (&v)[8]) {
                      if (r0 + m >= a.qrows) return;
 #pragma unroll
@@ -480,9 +540,10 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
 // columns) and mirrored to (P2 rows, P1 columns), so A' stays symmetric.
 // FP16x3: T's columns are scaled by their maxima from stage 1 and the
 // products scaled back.
-template <bool F16>
+template <int KIND>
 __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
 {
+    constexpr bool F16 = KIND == 1;
     __shared__ float s_cscale[TC_BN];
     const int k = a.k, b = a.b, ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
     const int item = blockIdx.x;
@@ -512,8 +573,8 @@ __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
             s_cscale[j] = n0 + j < k ? pow2(-exp_of(__uint_as_float(a.tmax[(size_t)pb * k + n0 + j]))) : 1.f;
         __syncthreads();
     }
-    ImageTile la{a.vimg + (size_t)e1 * ntk * nchk * U_IMG_TILE, nchk, mt};
-    KMajorF32<F16> lb;
+    ImageTile<KIND> la{a.vimg + (size_t)e1 * ntk * nchk * KT<KIND>::IMG, nchk, mt};
+    KMajorF32<KIND> lb;
     lb.T = T;
     lb.k = k;
     lb.n0 = n0;
@@ -523,7 +584,7 @@ __global__ void __launch_bounds__(U_T) k_tc_upd2(TcUpdArgs a)
     // when they stay inside one block of the pair and the address is 16-byte
     // aligned
     const bool mvec = (b & 7) == 0 && (lda & 3) == 0;
-    tc_tile<F16>(nchk, la, lb,
+    tc_tile<KIND>(nchk, la, lb,
                  [&](int m, int j0, const float (&v0)[8]) {
                      if (m0 + m >= k) return;
                      float v[8];
@@ -557,33 +618,36 @@ size_t tc_update_tmax_words(int npairs, int k) { return (size_t)(npairs * (npair
 size_t tc_update_vimg_bytes(int npairs, int k)
 {
     const size_t ntk = (k + TC_BN - 1) / TC_BN, nchk = (k + TC_BK - 1) / TC_BK;
-    return (size_t)npairs * ntk * nchk * U_IMG_TILE;
+    return (size_t)npairs * ntk * nchk * KT<2>::IMG;   // the largest kind
 }
 
-template <bool F16>
+template <int KIND>
 static cudaError_t launch_tc_update_t(const TcUpdArgs& a, cudaStream_t s)
 {
+    constexpr bool F16 = KIND == 1;
+    constexpr int U_SMEM = KT<KIND>::SMEM;
     const int ntk = (a.k + TC_BN - 1) / TC_BN, nchk = (a.k + TC_BK - 1) / TC_BK;
     const int npb = a.npairs * (a.npairs - 1) / 2;
     const int n_sand = npb * ntk * ntk;
     const int n_q = a.Qin ? a.npairs * ((a.qrows + TC_BM - 1) / TC_BM) * ntk : 0;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_upd1<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_upd2<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
+    e = cudaFuncSetAttribute(k_tc_upd2<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, U_SMEM);
     if (e != cudaSuccess) return e;
     if (F16 && npb > 0 && (e = cudaMemsetAsync(a.tmax, 0, sizeof(unsigned) * (size_t)npb * a.k, s)) != cudaSuccess)
         return e;
-    if (a.npairs > 0) k_tc_split_v<F16><<<a.npairs * ntk * nchk, U_T, 0, s>>>(a.V, a.rot, a.k, ntk, nchk, a.vimg);
+    if (a.npairs > 0) k_tc_split_v<KIND><<<a.npairs * ntk * nchk, U_T, 0, s>>>(a.V, a.rot, a.k, ntk, nchk, a.vimg);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand + n_q > 0) k_tc_upd1<F16><<<n_sand + n_q, U_T, U_SMEM, s>>>(a, n_sand);
+    if (n_sand + n_q > 0) k_tc_upd1<KIND><<<n_sand + n_q, U_T, U_SMEM, s>>>(a, n_sand);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand > 0) k_tc_upd2<F16><<<n_sand, U_T, U_SMEM, s>>>(a);
+    if (n_sand > 0) k_tc_upd2<KIND><<<n_sand, U_T, U_SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_update(const TcUpdArgs& a, cudaStream_t s)
 {
-    return a.f16 ? launch_tc_update_t<true>(a, s) : launch_tc_update_t<false>(a, s);
+    return a.kind == 2 ? launch_tc_update_t<2>(a, s)
+                       : (a.kind == 1 ? launch_tc_update_t<1>(a, s) : launch_tc_update_t<0>(a, s));
 }
 
 }  // namespace jac

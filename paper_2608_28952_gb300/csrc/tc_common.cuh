@@ -55,6 +55,12 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// kind::tf32: A and B tf32 (type field 2).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // hi = fp16(x), lo = fp16(x - hi): for |x| in fp16's normal range the pair
 // carries 22 significant bits; the caller scales x by a power of two so that
 // |x| <= 1 (no overflow) and the entries that matter stay normal.

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 MIXED = 2
 MIXED_F16 = 3
+MIXED_TF32 = 4
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +61,7 @@ LOWP_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16, MIXED_TF32])
 @pytest.mark.parametrize("np_,b,ordering,steps", LOWP_CASES)
 def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps, prec):
     import torch
@@ -112,7 +113,7 @@ def test_lowp_step_without_q_and_arguments(jg):
 
 
 # ------------------------------------------------------------------ full mixed solves
-@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16, MIXED_TF32])
 @pytest.mark.parametrize("n,b", [(256, 32), (300, 32), (512, 64), (1024, 128)])
 def test_mixed_solve_uniform_spectrum(jg, n, b, prec):
     A, lam = gen.sym_known(n, "uniform", seed=4300 + n)
@@ -130,7 +131,7 @@ def test_mixed_matches_oracle_eigenvalues(jg):
     check(A, _np(w), _np(Q), w_or)
 
 
-@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16, MIXED_TF32])
 def test_mixed_graded_spectrum(jg, prec):
     A, lam = gen.sym_known(256, "graded", seed=gen.SEEDS["c2g"])
     w_or, *_ = oracle.syev(A, b=32)
@@ -183,7 +184,7 @@ def test_mixed_edge_cases(jg):
     A[7, 3] = 0.0
     Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
     assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=MIXED, warm_start=1))[0] == jg.ERR_UNSUPPORTED
-    assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=4))[0] == jg.ERR_UNSUPPORTED
+    assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=5))[0] == -7
 
 
 def test_mixed_deterministic(jg):
@@ -193,7 +194,7 @@ def test_mixed_deterministic(jg):
     assert np.array_equal(_np(w1), _np(w2)) and np.array_equal(_np(Q1), _np(Q2))
 
 
-@pytest.mark.parametrize("prec", [MIXED, MIXED_F16])
+@pytest.mark.parametrize("prec", [MIXED, MIXED_F16, MIXED_TF32])
 def test_mixed_n4096_b64(jg, prec):
     """The benchmark's mixed workload size class: against the constructed
     spectrum, with fewer FP64 sweeps than the plain FP64 solve needs."""
