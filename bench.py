@@ -839,10 +839,29 @@ def run_batched(args, wl):
 
 def run_ncu_case(args, wl):
     """A handful of single steps of the workload (for ncu captures): FP64
-    steps, or low-precision steps for the mixed workloads."""
+    steps, or low-precision steps for the mixed workloads; for a batch, one
+    plan execution over its 32 largest matrices."""
     import torch
 
     import paper_2608_28952_gb300 as jg
+    if wl["kind"] in ("batched_evd", "batched_svd"):
+        import jacobi_inputs as gen
+        dev = torch.device("cuda", 0)
+        evd = wl["kind"] == "batched_evd"
+        shapes = sorted(batch_shapes(wl), key=lambda mn: -mn[0] * mn[1] * mn[1])[:32]
+        dtype = torch.float32 if wl["f32"] else torch.float64
+        flat, X, _ = gen.batch_flat_torch(shapes, wl["seed"], dev, dtype, symmetric=evd)
+        Y = [torch.empty(n, dtype=dtype, device=dev) for _, n in shapes]
+        Z = [jg.colmajor_empty(n, n, dtype, dev) for _, n in shapes]
+        info = torch.zeros(len(shapes), dtype=torch.int32, device=dev)
+        plan = jg.Plan(0 if evd else 1, jg.PREC_FP32 if wl["f32"] else jg.PREC_FP64, [n for _, n in shapes],
+                       m=None if evd else [m for m, _ in shapes], p=jg.params())
+        rc, _ = plan.execute(X, Y, Z, info)
+        torch.cuda.synchronize()
+        assert rc == 0 and int((info != 0).sum()) == 0
+        plan.close()
+        print(json.dumps({"ncu_case": wl["desc"], "matrices": len(shapes)}))
+        return 0
     X, _ = make_input(wl)
     dev = torch.device("cuda", 0)
     mixed = wl.get("precision", 0) != 0
