@@ -67,6 +67,10 @@ WORKLOADS = {
     "evd4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, ref_sweeps=13,
                     desc="plain FP64 two-sided block Jacobi EVD, n=4096, b=64, round-robin, "
                          "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
+    "evd4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=5, ref_sweeps=13,
+                       desc="two-sided block Jacobi EVD with FP64-accurate update products on the bf16 "
+                            "tensor cores (eight 7-bit slices per operand), FP64 pivots and off-norm, "
+                            "n=4096, b=64, round-robin, eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
     "evd256": dict(kind="evd", n=256, b=16, spectrum="uniform", seed=1,
                    desc="plain FP64 two-sided block Jacobi EVD, n=256, b=16, round-robin, "
                         "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
@@ -373,16 +377,29 @@ def evd_kernel_classes(stats, wl, peaks):
     lowp_steps = sum(st.sweeps_lowp for st in stats) * S
     tot = lambda f: sum(getattr(st, f) for st in stats)
     bf16 = peaks.get("bf16_tflops_sustained")
+    emu = wl.get("precision", 0) == 5
     cls = {
         "pivot": dict(kernel="k_pivot / k_pivot_cluster", ms=tot("ms_pivot"),
                       launches=tot("pivot_launches"),
-                      flops=tot("flops_fp64") - tot("flops_update") - tot("flops_refine"),
+                      flops=tot("flops_fp64") - (0 if emu else tot("flops_update")) - tot("flops_refine"),
                       bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS),
-        "update_fp64": dict(kernel="k_update_evd", ms=tot("ms_update") - tot("ms_update_lowp"),
-                            launches=tot("update_launches") - 3 * lowp_steps,
-                            flops=tot("flops_update"), bound="alu", peak=FP64_PEAK_TFLOPS,
-                            peak_basis=FP64_BASIS),
     }
+    if emu:
+        # FP64-accurate products from bf16 slices: the roofline is the bf16
+        # tensor pipe on the issued slice products; the FP64-equivalent rate
+        # is reported beside it
+        cls["update_emu"] = dict(kernel="k_emu_upd1 + k_emu_upd2 (tcgen05, FP64-accurate)",
+                                 ms=tot("ms_update"), launches=tot("update_launches"),
+                                 flops=tot("flops_lowp"), bound="tensor", peak=bf16,
+                                 peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
+                                            "flops = the 36 bf16 slice products issued",
+                                 fp64_equiv_tflops=(tot("flops_update") / (tot("ms_update") / 1e3) / 1e12
+                                                    if tot("ms_update") > 0 else None))
+    else:
+        cls["update_fp64"] = dict(kernel="k_update_evd", ms=tot("ms_update") - tot("ms_update_lowp"),
+                                  launches=tot("update_launches") - 3 * lowp_steps,
+                                  flops=tot("flops_update"), bound="alu", peak=FP64_PEAK_TFLOPS,
+                                  peak_basis=FP64_BASIS)
     if tot("sweeps_lowp") > 0:
         cls["update_lowp"] = dict(kernel="k_tc_split_v + k_tc_upd1 + k_tc_upd2 (tcgen05)",
                                   ms=tot("ms_update_lowp"), launches=3 * lowp_steps, flops=tot("flops_lowp"), bound="tensor",
@@ -498,13 +515,14 @@ def run_gpu(args, wl):
         kernels = evd_kernel_classes(stats, wl, peaks)
         dom = max(kernels, key=lambda c: kernels[c]["ms"])
         kc = kernels[dom]
-        if dom in ("update_fp64", "pivot") and kc["launches"]:
+        if dom in ("update_fp64", "update_emu", "pivot") and kc["launches"]:
             avg_ms = kc["ms"] / kc["launches"]
             per_launch = kc["flops"] / kc["launches"]
         else:
             avg_ms, per_launch = kc["ms"], kc["flops"]
         npd = padded_np(wl["n"], b)
         prof_name = {"update_fp64": f"update_evd_n{wl['n']}_b{b}",
+                     "update_emu": f"emu_update_n{wl['n']}_b{b}",
                      "pivot": f"pivot_n{wl['n']}_b{b}",
                      "refine": f"gemm64_n{wl['n']}",
                      "update_lowp": f"tc_update_n{wl['n']}_b{b}"}[dom]
@@ -575,12 +593,14 @@ def run_gpu(args, wl):
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == 0 else {2: "bf16x3", 3: "fp16x3", 4: "tf32x3"}[prec] + "+f32+f64",
+                "dtype": "f64" if prec == 0 else ("f64 (products from bf16 slices)" if prec == 5 else
+                                                  {2: "bf16x3", 3: "fp16x3", 4: "tf32x3"}[prec] + "+f32+f64"),
                 "data": "synthetic (seeded; see config)",
                 "config": {"workload": wl["desc"], "b": b,
                            "n": wl["n"], **({"m": wl["m"]} if "m" in wl else {}),
                            "seed": wl["seed"], "parallelism": f"replicas x{world}",
-                           **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3"}[prec],
+                           **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3",
+                                             5: "fp64 emulated products"}[prec],
                                "refine_steps": wl.get("refine_steps")} if prec else {}),
                            "l2": "inputs larger than L2 (working A, Q double-buffered: "
                                  "4 x n^2 x 8 B)"},

@@ -60,12 +60,17 @@ extern "C" {
  *  MIXED_FP16X3:  the same with fp16 hi/lo splits (22 bits per operand), the
  *                 FP32 operands scaled by powers of two per row / column.
  *  MIXED_TF32:    the same with tf32 big/small splits (x = big + small, big =
- *                 x with its low 13 mantissa bits cleared; kind::tf32). */
+ *                 x with its low 13 mantissa bits cleared; kind::tf32).
+ *  FP64_EMU:      the plain FP64 method with every update product formed
+ *                 FP64-accurately on the bf16 tensor cores (eight 7-bit slices
+ *                 per operand, see jacobi_f64emu_gemm); pivots, off-norm and
+ *                 everything else as FP64.  jacobi_syev and jacobi_syev_step. */
 #define JACOBI_PREC_FP64 0
 #define JACOBI_PREC_FP32 1
 #define JACOBI_PREC_MIXED_BF16X3 2
 #define JACOBI_PREC_MIXED_FP16X3 3
 #define JACOBI_PREC_MIXED_TF32 4
+#define JACOBI_PREC_FP64_EMU 5
 
 /* Stop criteria.
  *  OFF_ABS: Xi(A) = sqrt(sum_{i!=j} a_ij^2) <= tol * ||A||_F (Sec. 2.1,
@@ -208,6 +213,9 @@ int jacobi_gesvd_h(int m, int n, double* h_G, int ldg, double* h_sigma, double* 
  * matrix (both triangles read; it must be exactly symmetric) with np = N * p->b
  * and N the block count (even for round-robin).  No sorting, no stop test.
  *   A  device, np x np, lda >= np;   Q  device, np x np, ldq >= np, or NULL.
+ * p->precision: JACOBI_PREC_FP64 or JACOBI_PREC_FP64_EMU (the update
+ * products on the tensor cores, FP64-accurate); others return
+ * JACOBI_ERR_UNSUPPORTED.
  * Returns 0, or <0 on an invalid argument / CUDA error.
  */
 int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq, const jacobi_params* p,
@@ -317,6 +325,22 @@ int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
  */
 int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, const float* B,
                      int ldb, float* C, int ldc, void* stream);
+
+/*
+ * jacobi_f64emu_gemm -- an FP64-accurate product on the bf16 tensor cores:
+ * C = op(A) B with every row of op(A) and column of B scaled by a power of two
+ * and cut into eight 7-bit integer slices (bf16), the 36 slice products with
+ * p + q <= 9 accumulated exactly in FP32 per significance level (tcgen05,
+ * TMEM) and combined in FP64 (the error-free splitting of Ozaki et al.,
+ * applied with bf16 slices).  Error below about (9 K + 64) 2^-56 2^{E_m + F_n}
+ * per entry, where 2^{E_m} > max |op(A)(m, :)| and 2^{F_n} > max |B(:, n)|.
+ * Column-major FP64 on the device: A is M x K (transA = 0, lda >= M) or
+ * K x M (transA = 1, lda >= K), B K x N (ldb >= K), C M x N (ldc >= M);
+ * K <= 256 (JACOBI_ERR_UNSUPPORTED above).  Returns 0, -k for an invalid
+ * argument, JACOBI_ERR_TIMEOUT if a bounded tensor-core wait ran out.
+ */
+int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B,
+                       int ldb, double* C, int ldc, void* stream);
 
 /*
  * jacobi_syev_step_lowp -- one step of the mixed form's low-precision phase

@@ -26,6 +26,7 @@ PREC_FP32 = 1
 PREC_MIXED_BF16X3 = 2
 PREC_MIXED_FP16X3 = 3
 PREC_MIXED_TF32 = 4
+PREC_FP64_EMU = 5
 CONV_OFF_ABS = 0
 CONV_REL = 1
 ERR_NONFINITE = -100
@@ -124,6 +125,7 @@ SIGNATURES = {
     "jacobi_syev_step_noalloc": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_lowp_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
     "jacobi_syev_step_lowp": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
+    "jacobi_f64emu_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
 }
 
 _LIB = None
@@ -282,6 +284,15 @@ def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
     M = C.shape[0]
     return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
                                   _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
+
+
+def jacobi_f64emu_gemm(A, B, C, transA: bool = False, stream=None):
+    """C ``jacobi_f64emu_gemm``: C = op(A) B (FP64, column-major CUDA tensors,
+    K <= 256) on the tensor cores from eight bf16 slices per operand."""
+    K, N = B.shape
+    M = C.shape[0]
+    return lib().jacobi_f64emu_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
+                                    _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
 
 
 def jacobi_syev_step_lowp(A, Q, step: int, p: jacobi_params | None = None, stream=None):

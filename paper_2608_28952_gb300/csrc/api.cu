@@ -98,6 +98,10 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     ua.V = E.Vb;
     ua.rot = E.rot;
     ua.cnt = E.cnt;
+    if (E.T64) {
+        EmuUpdArgs ea{ua, E.T64, E.err};
+        return launch_emu_update(ea, cs);
+    }
     return launch_update_evd(ua, cs);
 }
 
@@ -194,8 +198,13 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         int* rank = ws.get<int>(n);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        if (p.precision == JACOBI_PREC_FP64_EMU) {
+            E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
+            E.err = ws.get<int>(1);
+        }
         if (ws.failed) return JACOBI_ERR_ALLOC;
         if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        if (E.err && cudaMemsetAsync(E.err, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(E.dpairs, E.ord.dev_pairs.data(), E.ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemsetAsync(E.cnt, 0, sizeof(DevCounters), s) != cudaSuccess ||
@@ -234,9 +243,12 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
                                 ldq, A, lda, rank, s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
         st->launches += 4;  // load, first off-norm, rank, finalise
+        int h_err = 0;
         if (cudaMemcpyAsync(&hc, E.cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            (E.err && cudaMemcpyAsync(&h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
+        if (h_err) return JACOBI_ERR_TIMEOUT;
         fill_counters(st, hc);
     }
     st->ms_total = timer.stop();
@@ -261,7 +273,7 @@ extern "C" int jacobi_syev(int n, double* A, int lda, double* w, double* Q, int 
     memset(&st, 0, sizeof(st));
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
-    if (p.precision == JACOBI_PREC_FP64) {
+    if (p.precision == JACOBI_PREC_FP64 || p.precision == JACOBI_PREC_FP64_EMU) {
         rc = syev_fp64(n, A, lda, w, Q, ldq, p, &st, s);
     } else {
         rc = syev_mixed(n, A, lda, w, Q, ldq, p, &st, s);
@@ -561,7 +573,14 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         E.cnt = ws.get<DevCounters>(1);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        if (p.precision == JACOBI_PREC_FP64_EMU) {
+            E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
+            E.err = ws.get<int>(1);
+        } else if (p.precision != JACOBI_PREC_FP64) {
+            return JACOBI_ERR_UNSUPPORTED;
+        }
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (E.err && cudaMemsetAsync(E.err, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(E.dpairs, E.ord.dev_pairs.data(), E.ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -582,7 +601,11 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         if (Q && cudaMemcpy2DAsync(Q, (size_t)ldq * 8, E.Qw[1], (size_t)np * 8, (size_t)np * 8, np,
                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        int h_err = 0;
+        if ((E.err && cudaMemcpyAsync(&h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return JACOBI_ERR_CUDA;
+        if (h_err) return JACOBI_ERR_TIMEOUT;
     }
     return 0;
 }

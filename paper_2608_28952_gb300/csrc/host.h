@@ -153,7 +153,7 @@ inline int check_params(const jacobi_params& p)
     if (!(p.tol >= 0.0) || !(p.inner_tol >= 0.0)) return -7;
     if (p.conv != JACOBI_CONV_OFF_ABS && p.conv != JACOBI_CONV_REL) return -7;
     if (p.pivot_order != 0 && p.pivot_order != 1) return -7;
-    if (p.precision < JACOBI_PREC_FP64 || p.precision > JACOBI_PREC_MIXED_TF32) return -7;
+    if (p.precision < JACOBI_PREC_FP64 || p.precision > JACOBI_PREC_FP64_EMU) return -7;
     return 0;
 }
 
@@ -189,6 +189,10 @@ struct EvdState {
     unsigned* ticket;
     double* result;
     DevCounters* cnt;
+    // FP64 products on the tensor cores (JACOBI_PREC_FP64_EMU): the stage-1
+    // products and the timeout word
+    double* T64 = nullptr;
+    int* err = nullptr;
 };
 
 // Result of a run of sweeps: code 0 converged, 1 max_sweeps ran out, <0 error.

@@ -164,6 +164,19 @@ size_t tc_update_tbuf_floats(int npairs, int k);
 size_t tc_update_vimg_bytes(int npairs, int k);
 size_t tc_update_tmax_words(int npairs, int k);
 
+// FP64-accurate product on the bf16 tensor cores (slices, K <= 256):
+// C (M x N) = op(A) B, column-major FP64.
+cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                            double* C, int ldc, int* err, cudaStream_t s);
+// The step update of the FP64 path with every product FP64-accurate on the
+// tensor cores (stage 1 T = A_{P1P2} V2 and Q V_P, stage 2 V1^T T mirrored).
+struct EmuUpdArgs {
+    UpdateArgs u;
+    double* T;      // [npb][k*k]
+    int* err;       // set on a timed-out tensor-core wait
+};
+cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s);
+size_t emu_update_tbuf_doubles(int npairs, int k);
 cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
                              double* result, cudaStream_t s);
 // C = alpha op(A) B + beta C (FP64, column-major); lower = 1 computes only

@@ -1,0 +1,505 @@
+// k_emu.cu -- FP64-accurate products on the bf16 tensor cores (tcgen05) by
+// slicing: the error-free splitting of Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer.
+// Algorithms 59, 2012), with integer-valued bf16 slices.
+//
+// Every row m of Aop is scaled by 2^{E_m}, E_m > the exponent of its largest
+// entry, and written in fixed point with 56 fraction bits, X = |a| 2^{56-E_m}
+// (rounded), written with eight balanced base-2^7 digits d_1..d_8, and slice
+// p holds d_p 2^{-7(p-1)} (exact in bf16).  Columns of Bop likewise with F_n.
+// Then a = 2^{E_m - 7} sum_p A_p and
+//     C(m, n) = 2^{E_m + F_n - 14} sum_{p + q <= 9} sum_k A_p(m, k) B_q(k, n).
+// A product A_p B_q is an integer times 2^{-7(p + q - 2)}; with K <= 256 the
+// sums of level l = p + q - 2 <= 4 stay below 2^24 in magnitude (|d_1| <= 128,
+// |d_p| <= 64 for p > 1) and are exact in the FP32 accumulators of the tensor
+// cores, one accumulator per level; levels 5..7 (relative weight <= 2^-35)
+// share one.  The accumulators are combined exactly in 64-bit integers (units
+// of 2^-35) and converted once.  The dropped products (p + q > 9), the
+// rounding to 56 fraction bits and the rounding of the lowest levels in the
+// combination leave an error below about (9 K + 64) 2^-56 2^{E_m + F_n}, the
+// size of FP64 rounding in a K-term dot product of the scaled rows and
+// columns.
+//
+// One CTA computes a 128 x 64 tile (six 64-column accumulators in 512 TMEM
+// columns); K is streamed in chunks of 32 through two 96 KB stages (8 slices
+// of A, 128 x 32, and of B, 64 x 32, in the canonical no-swizzle K-major
+// layout); one thread issues the 72 MMAs of a chunk (2 K steps x 36 slice
+// products) and commits them to the stage's mbarrier (bounded waits).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace jac {
+
+namespace {
+
+constexpr int EM = 128, EN = 64, EK = 32, ENS = 8, ENACC = 6, E_T = 256;
+constexpr int E_ATILE = EM * EK * 2;                      // one A slice tile (8 KB)
+constexpr int E_BTILE = EN * EK * 2;                      // one B slice tile (4 KB)
+constexpr int E_STAGE = ENS * (E_ATILE + E_BTILE);        // 96 KB
+constexpr int E_SMEM = 2 * E_STAGE + 1024;
+
+// unbiased exponent e with |x| in [2^e, 2^{e+1}) (-1100 for 0)
+__device__ __forceinline__ int exp2_of(double x)
+{
+    if (x == 0.0) return -1100;
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int ea = (int)((b >> 52) & 0x7FF);
+    if (ea) return ea - 1023;
+    return -1075 + (64 - __clzll((long long)(b & 0xFFFFFFFFFFFFFull)));   // subnormal
+}
+
+// The eight slices of x for the row/column scale 2^E (|x| < 2^E): the signed
+// fixed-point value Xs = x 2^{56-E} (rounded to nearest where x is more than
+// four binades below the scale; exact otherwise) written with balanced
+// base-2^7 digits, Xs = sum_p d_p 2^{56-7p}, d_1 in [-128, 128], the others in
+// [-64, 64] (each rounded to nearest, the last one the exact remainder).
+// Balanced digits keep the discarded low-order products unbiased; with
+// truncated digits they always shrink |a b| and the bias builds up over the
+// hundreds of update steps of a solve.
+__device__ __forceinline__ void slice8(double x, int E, __nv_bfloat16 (&s)[ENS])
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int ea = (int)((b >> 52) & 0x7FF);
+    uint64_t M = b & 0xFFFFFFFFFFFFFull;
+    int e = -1022;
+    if (ea) {
+        M |= 1ull << 52;
+        e = ea - 1023;
+    }
+    const int sh = e - E + 4;   // |Xs| = M 2^sh < 2^56
+    uint64_t X;
+    if (sh >= 0) X = M << sh;
+    else if (sh > -54) X = (M + (1ull << (-sh - 1))) >> -sh;
+    else X = 0ull;
+    long long r = (b >> 63) ? -(long long)X : (long long)X;
+#pragma unroll
+    for (int p = 1; p <= ENS; ++p) {
+        long long d;
+        if (p < ENS) {
+            const int shp = 56 - 7 * p;
+            d = (r + (1ll << (shp - 1))) >> shp;   // round half up (arithmetic shift)
+            r -= d << shp;
+        } else {
+            d = r;
+        }
+        s[p - 1] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * (p - 1)) << 23));
+    }
+}
+
+// Eight consecutive K values of one row r of a slice tile set: slice p of
+// value u to tile p at tile_off(r, kk0 + u).
+__device__ __forceinline__ void store_slices(unsigned char* base, int tile_bytes, int r, int kk0,
+                                             const double (&x)[8], int E)
+{
+    __nv_bfloat16 sl[8][ENS];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) slice8(x[u], E, sl[u]);
+    const uint32_t o = tile_off(r, kk0);
+#pragma unroll
+    for (int p = 0; p < ENS; ++p) {
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = sl[u][p];
+        *reinterpret_cast<uint4*>(base + p * tile_bytes + o) = *reinterpret_cast<const uint4*>(v);
+    }
+}
+
+}  // namespace
+
+// C tile (128 x 64) = Aop (128 x K) * Bop (K x 64) in FP64 accuracy, K <= 256.
+// fa(m, k), fb(k, n): FP64 operand values (0 outside); eA[m], eB[n]: the
+// row / column scale exponents in shared memory (filled by the caller, all
+// threads synchronised); st(m, n, v) stores.
+template <class FA, class FB, class ST>
+__device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST st, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char esm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* base = (unsigned char*)(((uintptr_t)esm + 1023) & ~(uintptr_t)1023);
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = idesc_bf16(EM, EN);
+    const int nchk = (K + EK - 1) / EK;
+    uint32_t uses[2] = {0, 0};
+    for (int c = 0; c < nchk; ++c) {
+        const int s = c & 1;
+        unsigned char* st_a = base + s * E_STAGE;
+        unsigned char* st_b = st_a + ENS * E_ATILE;
+        if (c >= 2 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+        // A: 128 rows x 4 groups of 8 K values, two items per thread
+        for (int it = tid; it < EM * (EK / 8); it += E_T) {
+            const int r = it & (EM - 1), g = it >> 7, k0 = c * EK + g * 8;
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? fa(r, k0 + u) : 0.0;
+            store_slices(st_a, E_ATILE, r, g * 8, x, eA[r]);
+        }
+        // B: 64 columns x 4 groups, one item per thread
+        for (int it = tid; it < EN * (EK / 8); it += E_T) {
+            const int n = it & (EN - 1), g = it >> 6, k0 = c * EK + g * 8;
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? fb(k0 + u, n) : 0.0;
+            store_slices(st_b, E_BTILE, n, g * 8, x, eB[n]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(st_a), b0 = smem_u32(st_b);
+#pragma unroll
+            for (int ks = 0; ks < EK / 16; ++ks) {
+                const uint32_t koff = ks * 256;
+#pragma unroll
+                for (int p = 1; p <= ENS; ++p) {
+                    const uint64_t da = smem_desc(a0 + (p - 1) * E_ATILE + koff, 128, 512);
+#pragma unroll
+                    for (int q = 1; q <= ENS + 1 - p; ++q) {
+                        const uint64_t db = smem_desc(b0 + (q - 1) * E_BTILE + koff, 128, 512);
+                        const int l = p + q - 2 < ENACC - 1 ? p + q - 2 : ENACC - 1;
+                        const uint32_t acc = (c > 0 || ks > 0 || p > 1 || q > ENACC) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(tmem + (uint32_t)(l * EN)),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&s_bar[s]))
+                         : "memory");
+        }
+        uses[s]++;
+    }
+    __syncthreads();
+    if (!s_fail)
+        for (int s = 0; s < 2; ++s)
+            if (uses[s] > 0 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+        const int qd = warp & 3, h = warp >> 2, m = qd * 32 + lane;
+        for (int j0 = h * 32; j0 < h * 32 + 32; j0 += 8) {
+            // The exact levels hold integers I_l 2^{-7l} (|I_l| < 2^24): their sum
+            // is the integer S = sum_l I_l 2^{7(5-l)} in units of 2^-35 (|S| <
+            // 2^58), formed exactly in 64-bit integers; the shared low levels
+            // (weights 2^-35 .. 2^-49) are rounded to that unit, 2^-57 of the
+            // level-0 unit.  One conversion to FP64, and the scale
+            // 2^{E_m + F_n - 49} goes into the exponent field.
+            long long S[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) S[u] = 0;
+#pragma unroll
+            for (int l = 0; l < ENACC; ++l) {
+                uint32_t v[8];
+                const uint32_t addr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(l * EN + j0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const float up = __int_as_float((127 + 7 * l) << 23);   // 2^{7 l} (2^35 for the shared one)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float x = __uint_as_float(v[u]) * up;
+                    if (l < ENACC - 1) S[u] += (long long)__float2int_rn(x) * (1ll << (7 * (ENACC - 1 - l)));
+                    else S[u] += __float2ll_rn(x);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                double d = __ll2double_rn(S[u]);
+                const int e = eA[m] + eB[j0 + u] - 49;
+                if (d != 0.0) {
+                    const long long bits = __double_as_longlong(d);
+                    const int ex = (int)((bits >> 52) & 0x7FF) + e;
+                    d = (ex > 0 && ex < 2047) ? __longlong_as_double(bits + (long long)e * (1ll << 52)) : ldexp(d, e);
+                }
+                st(m, j0 + u, d);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+namespace {
+
+// Row scale exponents of an Aop tile (rows m < M) and column exponents of a
+// Bop tile: E = 1 + the largest entry exponent (0 for an all-zero line).
+template <class F>
+__device__ void line_exponents(int lines, int K, F f, int* out, int* scratch)
+{
+    // thread t: line t % lines, K range split over the threads of that line
+    const int per = E_T / lines;
+    const int li = threadIdx.x % lines, part = threadIdx.x / lines;
+    int mx = -1100;
+    if (part < per)
+        for (int k = part; k < K; k += per) mx = max(mx, exp2_of(f(li, k)));
+    scratch[threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.x < lines) {
+        int m = -1100;
+        for (int p = 0; p < per; ++p) m = max(m, scratch[threadIdx.x + lines * p]);
+        out[threadIdx.x] = m <= -1100 ? 0 : m + 1;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(E_T, 1) k_emu_gemm(int M, int N, int K, const double* __restrict__ A, int lda,
+                                                     int transA, const double* __restrict__ B, int ldb,
+                                                     double* __restrict__ C, int ldc, int* err)
+{
+    __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
+    const int m0 = blockIdx.x * EM, n0 = blockIdx.y * EN;
+    auto fa = [&](int m, int k) -> double {
+        const int mm = m0 + m;
+        if (mm >= M || k >= K) return 0.0;
+        return transA ? A[k + (size_t)lda * mm] : A[mm + (size_t)lda * k];
+    };
+    auto fb = [&](int k, int n) -> double {
+        const int nn = n0 + n;
+        return (nn < N && k < K) ? B[k + (size_t)ldb * nn] : 0.0;
+    };
+    line_exponents(EM, K, fa, s_eA, s_scr);
+    line_exponents(EN, K, [&](int n, int k) { return fb(k, n); }, s_eB, s_scr);
+    emu_tile(K, fa, fb, s_eA, s_eB,
+             [&](int m, int n, double v) {
+                 if (m0 + m < M && n0 + n < N) C[(m0 + m) + (size_t)ldc * (n0 + n)] = v;
+             },
+             err);
+}
+
+}  // namespace
+
+cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                            double* C, int ldc, int* err, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
+    k_emu_gemm<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, C, ldc, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- emulated FP64 step update
+namespace {
+
+__device__ __forceinline__ int emap(int I, int J, int b, int x) { return x < b ? I * b + x : J * b + (x - b); }
+
+__device__ __forceinline__ void eentry(const int2* pairs, int e, int& I, int& J)
+{
+    const int2 pr = pairs[e];
+    I = pr.x < 0 ? -1 - pr.x : pr.x;
+    J = pr.x < 0 ? -1 - pr.y : pr.y;
+}
+
+__device__ __forceinline__ void edecode_pb(int pb, int& e1, int& e2)
+{
+    int t = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)pb)) * 0.5f);
+    while (t * (t - 1) / 2 > pb) --t;
+    while ((t + 1) * t / 2 <= pb) ++t;
+    e2 = t;
+    e1 = pb - t * (t - 1) / 2;
+}
+
+// Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2 (FP64,
+// k x k per pair-block); items beyond: tile (rt, nt) of Q'(:,P) = Q(:,P) V_P.
+// V^T (stored after V by the pivot kernel) gives the coalesced operand loads.
+__global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
+{
+    __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
+    const UpdateArgs& u = a.u;
+    const int k = u.k, b = u.b, nmt = (k + EM - 1) / EM, nnt = (k + EN - 1) / EN;
+    int item = blockIdx.x;
+    if (item < n_sand) {
+        const int pb = item / (nmt * nnt), rem = item % (nmt * nnt), mt = rem / nnt, nt = rem % nnt;
+        int e1, e2, I1, J1, I2, J2;
+        edecode_pb(pb, e1, e2);
+        eentry(u.pairs, e1, I1, J1);
+        eentry(u.pairs, e2, I2, J2);
+        double* T = a.T + (size_t)pb * k * k;
+        const int m0 = mt * EM, n0 = nt * EN;
+        if (u.rot[e2] == 0) {
+            for (int idx = threadIdx.x; idx < EM * EN; idx += E_T) {
+                const int m = m0 + idx % EM, j = n0 + idx / EM;
+                if (m < k && j < k) T[m + (size_t)k * j] = u.Ain[emap(I1, J1, b, m) + (size_t)u.lda * emap(I2, J2, b, j)];
+            }
+            return;
+        }
+        const double* V2t = u.V + (size_t)e2 * 2 * k * k + (size_t)k * k;
+        auto fa = [&](int m, int kk) -> double {
+            return m0 + m < k && kk < k ? u.Ain[emap(I1, J1, b, m0 + m) + (size_t)u.lda * emap(I2, J2, b, kk)] : 0.0;
+        };
+        auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? V2t[(n0 + n) + (size_t)k * kk] : 0.0; };
+        line_exponents(EM, k, fa, s_eA, s_scr);
+        line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+        emu_tile(k, fa, fb, s_eA, s_eB,
+                 [&](int m, int n, double v) {
+                     if (m0 + m < k && n0 + n < k) T[(m0 + m) + (size_t)k * (n0 + n)] = v;
+                 },
+                 a.err);
+        if (threadIdx.x == 0) {
+            atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
+            atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
+        }
+        return;
+    }
+    item -= n_sand;
+    const int nrt = (u.qrows + EM - 1) / EM;
+    const int e = item / (nrt * nnt), rem = item % (nrt * nnt), rt = rem / nnt, nt = rem % nnt;
+    int I, J;
+    eentry(u.pairs, e, I, J);
+    const int r0 = rt * EM, n0 = nt * EN;
+    if (u.rot[e] == 0) {
+        for (int idx = threadIdx.x; idx < EM * EN; idx += E_T) {
+            const int m = r0 + idx % EM, j = n0 + idx / EM;
+            if (m < u.qrows && j < k) {
+                const size_t o = m + (size_t)u.ldq * emap(I, J, b, j);
+                u.Qout[o] = u.Qin[o];
+            }
+        }
+        return;
+    }
+    const double* Vt = u.V + (size_t)e * 2 * k * k + (size_t)k * k;
+    auto fa = [&](int m, int kk) -> double {
+        return r0 + m < u.qrows && kk < k ? u.Qin[(r0 + m) + (size_t)u.ldq * emap(I, J, b, kk)] : 0.0;
+    };
+    auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? Vt[(n0 + n) + (size_t)k * kk] : 0.0; };
+    line_exponents(EM, k, fa, s_eA, s_scr);
+    line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+    emu_tile(k, fa, fb, s_eA, s_eB,
+             [&](int m, int n, double v) {
+                 if (r0 + m < u.qrows && n0 + n < k) u.Qout[(r0 + m) + (size_t)u.ldq * emap(I, J, b, n0 + n)] = v;
+             },
+             a.err);
+    if (threadIdx.x == 0) {
+        atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
+        atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
+    }
+}
+
+// Stage 2: tile (mt, nt) of O_pb = V1^T T_pb, written to A' at (P1 rows, P2
+// columns) and mirrored.
+__global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
+{
+    __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
+    const UpdateArgs& u = a.u;
+    const int k = u.k, b = u.b, nmt = (k + EM - 1) / EM, nnt = (k + EN - 1) / EN;
+    const int item = blockIdx.x;
+    const int pb = item / (nmt * nnt), rem = item % (nmt * nnt), mt = rem / nnt, nt = rem % nnt;
+    int e1, e2, I1, J1, I2, J2;
+    edecode_pb(pb, e1, e2);
+    eentry(u.pairs, e1, I1, J1);
+    eentry(u.pairs, e2, I2, J2);
+    const double* T = a.T + (size_t)pb * k * k;
+    const int m0 = mt * EM, n0 = nt * EN;
+    double* Ao = u.Aout;
+    const size_t lda = (size_t)u.lda;
+    auto put = [&](int m, int n, double v) {
+        const int gi = emap(I1, J1, b, m), gj = emap(I2, J2, b, n);
+        Ao[gi + lda * gj] = v;
+        Ao[gj + lda * gi] = v;
+    };
+    if (u.rot[e1] == 0) {
+        for (int idx = threadIdx.x; idx < EM * EN; idx += E_T) {
+            const int m = m0 + idx % EM, j = n0 + idx / EM;
+            if (m < k && j < k) put(m, j, T[m + (size_t)k * j]);
+        }
+        return;
+    }
+    const double* V1t = u.V + (size_t)e1 * 2 * k * k + (size_t)k * k;   // V1^T(m, kk) at V1t[m + k kk]
+    auto fa = [&](int m, int kk) -> double { return m0 + m < k && kk < k ? V1t[(m0 + m) + (size_t)k * kk] : 0.0; };
+    auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? T[kk + (size_t)k * (n0 + n)] : 0.0; };
+    line_exponents(EM, k, fa, s_eA, s_scr);
+    line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+    emu_tile(k, fa, fb, s_eA, s_eB,
+             [&](int m, int n, double v) {
+                 if (m0 + m < k && n0 + n < k) put(m0 + m, n0 + n, v);
+             },
+             a.err);
+    if (threadIdx.x == 0) {
+        atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
+        atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
+    }
+}
+
+}  // namespace
+
+size_t emu_update_tbuf_doubles(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
+
+cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
+{
+    const UpdateArgs& u = a.u;
+    const int nmt = (u.k + EM - 1) / EM, nnt = (u.k + EN - 1) / EN;
+    const int npb = u.npairs * (u.npairs - 1) / 2;
+    const int n_sand = npb * nmt * nnt;
+    const int n_q = u.Qin ? u.npairs * ((u.qrows + EM - 1) / EM) * nnt : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_upd1, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_emu_upd2, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM)) != cudaSuccess)
+        return e;
+    if (n_sand + n_q > 0) k_emu_upd1<<<n_sand + n_q, E_T, E_SMEM, s>>>(a, n_sand);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n_sand > 0) k_emu_upd2<<<n_sand, E_T, E_SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace jac
+
+// FP64-accurate product on the tensor cores (see the top of this file).
+extern "C" int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B,
+                                  int ldb, double* C, int ldc, void* stream)
+{
+    if (M < 0 || N < 0 || K < 0) return -1;
+    if (K > 256) return JACOBI_ERR_UNSUPPORTED;
+    if (!A || !B || !C) return -5;
+    if ((!transA && lda < M) || (transA && lda < K) || ldb < K || ldc < M) return -5;
+    if (M == 0 || N == 0) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (K == 0) {
+        if (cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)M * 8, N, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return JACOBI_ERR_CUDA;
+        return 0;
+    }
+    int* err = nullptr;
+    if (cudaMallocAsync(&err, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    int h = 0, rc = 0;
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+        jac::launch_emu_gemm(M, N, K, A, lda, transA, B, ldb, C, ldc, err, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        rc = JACOBI_ERR_CUDA;
+    cudaFreeAsync(err, s);
+    cudaStreamSynchronize(s);
+    if (rc == 0 && h) rc = JACOBI_ERR_TIMEOUT;
+    return rc;
+}

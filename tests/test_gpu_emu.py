@@ -1,0 +1,138 @@
+"""FP64-accurate products on the bf16 tensor cores (slicing; jacobi_f64emu_gemm)
+against the exact product.  The model: every row of op(A) and column of B is
+written as 2^{E-7} sum_p slice_p with eight 7-bit integer slices, and the
+slice products of total significance p + q <= 9 are summed exactly.  Per
+term of the dot product, rounding each operand to 56 fraction bits costs
+< 2^{E+F-56} and the dropped products p + q >= 10 (balanced digits of at
+most 64, weights 2^{-7(p+q-2)}) < 2^{E+F-56}, and the combination of the
+accumulators rounds the three lowest levels to 2^{E+F-49} (half of it at
+most); the bound per entry is taken as (9.1 K + 64) 2^-56 2^{E_m + F_n} with
+2^{E_m} > max|op(A)(m, :)| and 2^{F_n} > max|B(:, n)|, the size of FP64
+rounding (K 2^-53 |op(A)| |B|) for K >= 8."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_28952_gb300 as m
+    m.lib()
+    return m
+
+
+def _pow2_above(x):
+    m = np.abs(x).max()
+    return 2.0 ** (np.floor(np.log2(m)) + 1) if m > 0 else 1.0
+
+
+def _exact(A, B):
+    # the product to well below FP64 rounding: long double where the platform
+    # has it (x86), else FP64 (the bound's FP64 term covers it)
+    if np.finfo(np.longdouble).eps < 1e-17:
+        return (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+    return A @ B
+
+
+@pytest.mark.parametrize("M,N,K,trans", [(128, 64, 32, False), (128, 64, 256, False), (300, 200, 128, False),
+                                          (256, 130, 77, True), (1, 5, 3, False), (129, 65, 200, True)])
+def test_emu_gemm_is_fp64_accurate(jg, M, N, K, trans):
+    import torch
+    r = np.random.default_rng(M * 7 + N + K)
+    A = r.standard_normal((K, M) if trans else (M, K))
+    B = r.standard_normal((K, N))
+    # graded rows and columns: the scaling is per row / column
+    A *= (10.0 ** r.uniform(-8, 8, A.shape[1] if trans else A.shape[0]))[None, :] if trans else \
+        (10.0 ** r.uniform(-8, 8, A.shape[0]))[:, None]
+    B *= (10.0 ** r.uniform(-8, 8, N))[None, :]
+    Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
+    Bd = jg.colmajor(B, device="cuda", dtype=torch.float64)
+    Cd = jg.colmajor_empty(M, N, torch.float64, "cuda")
+    assert jg.jacobi_f64emu_gemm(Ad, Bd, Cd, transA=trans) == 0
+    C = Cd.cpu().numpy()
+    Aop = A.T if trans else A
+    want = _exact(Aop, B)
+    rs = np.array([_pow2_above(Aop[i]) for i in range(M)])
+    cs = np.array([_pow2_above(B[:, j]) for j in range(N)])
+    bound = (9.1 * K + 64) * 2.0 ** -56 * rs[:, None] * cs[None, :] + 4 * 2.0 ** -53 * np.abs(want)
+    assert np.all(np.abs(C - want) <= bound), np.max(np.abs(C - want) / bound)
+
+
+def test_emu_gemm_special_values(jg):
+    import torch
+    M, N, K = 64, 64, 16
+    A = np.zeros((M, K))
+    A[3, :] = 2.0 ** -1000 * np.arange(1, K + 1)   # tiny entries keep their row's own scale
+    A[4, :] = (-1.0) ** np.arange(K) * 2.0 ** np.arange(K)   # signs and a 2^15 range in one row
+    A[5, 7] = -2.0 ** 60
+    B = np.eye(K, N)
+    B[2, 9] = 3.0
+    Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
+    Bd = jg.colmajor(B, device="cuda", dtype=torch.float64)
+    Cd = jg.colmajor_empty(M, N, torch.float64, "cuda")
+    assert jg.jacobi_f64emu_gemm(Ad, Bd, Cd) == 0
+    C = Cd.cpu().numpy()
+    assert np.array_equal(C, A @ B)          # integers and powers of two are exact
+    assert jg.jacobi_f64emu_gemm(Ad, jg.colmajor(np.zeros((300, 4)), device="cuda", dtype=torch.float64),
+                                 jg.colmajor_empty(M, 4, torch.float64, "cuda")) == jg.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ the FP64 method with emulated products
+import jacobi_inputs as gen  # noqa: E402
+import oracle  # noqa: E402
+
+EMU = 5
+
+
+@pytest.mark.parametrize("np_,b,ordering,steps", [
+    (256, 64, 0, [0, 1]), (512, 128, 0, [0]), (96, 16, 0, [0, 4]), (40, 5, 0, [0, 2]), (80, 8, 1, [0, 1]),
+])
+def test_emu_step_matches_oracle(jg, np_, b, ordering, steps):
+    """One parallel step with the update products on the tensor cores gives
+    the oracle's FP64 step to the same 1e-13 as the DFMA path (well
+    separated pivots: a well-conditioned step)."""
+    import torch
+    d = np.linspace(1.0, 2.0 * np_, np_)
+    A0 = np.asfortranarray(np.diag(d) + 0.05 * gen.sym_gaussian(np_, 5000 + np_ + b))
+    tab = oracle.ordering(ordering, np_ // b)
+    for s in steps:
+        A_or, Q_or, _ = oracle.syev_step(A0, np.eye(np_), b, tab[s])
+        Ad = jg.colmajor(A0, device="cuda", dtype=torch.float64)
+        Qd = jg.colmajor(np.eye(np_), device="cuda", dtype=torch.float64)
+        assert jg.jacobi_syev_step(Ad, Qd, s, jg.params(b=b, ordering=ordering, precision=EMU)) == 0
+        Ag, Qg = Ad.cpu().numpy(), Qd.cpu().numpy()
+        assert np.array_equal(Ag, Ag.T)
+        assert np.abs(Ag - A_or).max() <= 1e-13 * np.abs(A0).max(), np.abs(Ag - A_or).max() / np.abs(A0).max()
+        assert np.abs(Qg - Q_or).max() <= 1e-13, np.abs(Qg - Q_or).max()
+
+
+def _check(A, w, Q, w_ref, eig=1e-13, res=1e-12, orth=1e-13):
+    n = A.shape[0]
+    nrm2 = np.abs(w_ref).max()
+    assert np.abs(w - w_ref).max() <= eig * nrm2, np.abs(w - w_ref).max() / nrm2
+    assert np.linalg.norm(A @ Q - Q * w[None, :]) <= res * np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= orth * n
+
+
+@pytest.mark.parametrize("n,b,kind", [(512, 64, "uniform"), (1024, 64, "uniform"), (300, 32, "uniform"),
+                                       (256, 32, "graded"), (512, 128, "uniform")])
+def test_emu_full_solve_meets_the_fp64_gates(jg, n, b, kind):
+    A, lam = gen.sym_known(n, kind, seed=5100 + n)
+    w, Q, _, st = jg.syev(A, b=b, precision=EMU)
+    assert st.status == 0
+    _check(A, w.cpu().numpy(), Q.cpu().numpy(), np.sort(lam) if kind == "uniform" else oracle.syev(A, b=b)[0])
+
+
+def test_emu_n4096_b64(jg):
+    """The benchmark matrix: the FP64 gates against the constructed spectrum."""
+    n, b = 4096, 64
+    A, lam = gen.sym_known(n, "uniform", seed=gen.SEEDS["c2u"])
+    w, Q, _, st = jg.syev(A, b=b, precision=EMU)
+    assert st.status == 0
+    _check(A, w.cpu().numpy(), Q.cpu().numpy(), np.sort(lam))
