@@ -884,7 +884,7 @@ def run_ncu_case(args, wl):
         return 0
     X, _ = make_input(wl)
     dev = torch.device("cuda", 0)
-    mixed = wl.get("precision", 0) != 0
+    mixed = wl.get("precision", 0) in (2, 3, 4)
     dt = torch.float32 if mixed else torch.float64
     Xd = jg.colmajor(X, device=dev, dtype=dt)
     Qd = jg.colmajor(torch.eye(X.shape[0], dtype=dt), device=dev)

@@ -43,11 +43,12 @@ constexpr int E_BTILE = EN * EK * 2;                      // one B slice tile (4
 constexpr int E_STAGE = ENS * (E_ATILE + E_BTILE);        // 96 KB
 constexpr int E_SMEM = 2 * E_STAGE + 1024;
 
-// unbiased exponent e with |x| in [2^e, 2^{e+1}) (-1100 for 0)
+// unbiased exponent e with |x| in [2^e, 2^{e+1}) (-1100 for 0); integer
+// operations only (GB300's FP64 pipe runs at 1/64 rate)
 __device__ __forceinline__ int exp2_of(double x)
 {
-    if (x == 0.0) return -1100;
     const uint64_t b = (uint64_t)__double_as_longlong(x);
+    if ((b << 1) == 0) return -1100;
     const int ea = (int)((b >> 52) & 0x7FF);
     if (ea) return ea - 1023;
     return -1075 + (64 - __clzll((long long)(b & 0xFFFFFFFFFFFFFull)));   // subnormal
@@ -87,7 +88,7 @@ __device__ __forceinline__ void slice8(double x, int E, __nv_bfloat16 (&s)[ENS])
         } else {
             d = r;
         }
-        s[p - 1] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * (p - 1)) << 23));
+        s[p - 1] = __float2bfloat16_rn(__int2float_rn((int)d) * __int_as_float((127 - 7 * (p - 1)) << 23));
     }
 }
 
@@ -143,27 +144,37 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
     const uint32_t idesc = idesc_bf16(EM, EN);
     const int nchk = (K + EK - 1) / EK;
     uint32_t uses[2] = {0, 0};
+    // operand registers of one chunk: A items (r, g) = tid, tid + 256 (rows
+    // r = it % 128, eight K values g * 8 ..), B item (n, g) = tid; the next
+    // chunk's loads are issued before the current chunk's MMAs
+    double xa[2][8], xb[8];
+    auto load_chunk = [&](int c) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int it = tid + E_T * i, r = it & (EM - 1), k0 = c * EK + (it >> 7) * 8;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xa[i][u] = k0 + u < K ? fa(r, k0 + u) : 0.0;
+        }
+        const int n = tid & (EN - 1), k0 = c * EK + (tid >> 6) * 8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xb[u] = k0 + u < K ? fb(k0 + u, n) : 0.0;
+    };
+    load_chunk(0);
     for (int c = 0; c < nchk; ++c) {
         const int s = c & 1;
         unsigned char* st_a = base + s * E_STAGE;
         unsigned char* st_b = st_a + ENS * E_ATILE;
         if (c >= 2 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
-        // A: 128 rows x 4 groups of 8 K values, two items per thread
-        for (int it = tid; it < EM * (EK / 8); it += E_T) {
-            const int r = it & (EM - 1), g = it >> 7, k0 = c * EK + g * 8;
-            double x[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? fa(r, k0 + u) : 0.0;
-            store_slices(st_a, E_ATILE, r, g * 8, x, eA[r]);
+        for (int i = 0; i < 2; ++i) {
+            const int it = tid + E_T * i, r = it & (EM - 1);
+            store_slices(st_a, E_ATILE, r, (it >> 7) * 8, xa[i], eA[r]);
         }
-        // B: 64 columns x 4 groups, one item per thread
-        for (int it = tid; it < EN * (EK / 8); it += E_T) {
-            const int n = it & (EN - 1), g = it >> 6, k0 = c * EK + g * 8;
-            double x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = k0 + u < K ? fb(k0 + u, n) : 0.0;
-            store_slices(st_b, E_BTILE, n, g * 8, x, eB[n]);
+        {
+            const int n = tid & (EN - 1);
+            store_slices(st_b, E_BTILE, n, (tid >> 6) * 8, xb, eB[n]);
         }
+        if (c + 1 < nchk) load_chunk(c + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (s_fail) break;
@@ -224,19 +235,29 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
                 const float up = __int_as_float((127 + 7 * l) << 23);   // 2^{7 l} (2^35 for the shared one)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const float x = __uint_as_float(v[u]) * up;
-                    if (l < ENACC - 1) S[u] += (long long)__float2int_rn(x) * (1ll << (7 * (ENACC - 1 - l)));
-                    else S[u] += __float2ll_rn(x);
+                    const int x = __float2int_rn(__uint_as_float(v[u]) * up);   // |x| < 2^24 (2^17 for the shared one)
+                    S[u] += l < ENACC - 1 ? (long long)x * (1ll << (7 * (ENACC - 1 - l))) : (long long)x;
                 }
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                double d = __ll2double_rn(S[u]);
+                // S 2^{E_m + F_n - 49} in FP64, rounded to nearest even, by integer operations
+                const long long sv = S[u];
                 const int e = eA[m] + eB[j0 + u] - 49;
-                if (d != 0.0) {
-                    const long long bits = __double_as_longlong(d);
-                    const int ex = (int)((bits >> 52) & 0x7FF) + e;
-                    d = (ex > 0 && ex < 2047) ? __longlong_as_double(bits + (long long)e * (1ll << 52)) : ldexp(d, e);
+                double d = 0.0;
+                if (sv != 0) {
+                    const uint64_t sg = sv < 0 ? (1ull << 63) : 0ull;
+                    const uint64_t mag = sv < 0 ? (uint64_t)(-sv) : (uint64_t)sv;
+                    const int lz = __clzll((long long)mag);
+                    const uint64_t mm = mag << lz;                    // leading one at bit 63
+                    uint64_t mant = mm >> 11;                         // 53 bits
+                    const uint64_t low = mm & 0x7FFull;
+                    if (low > 0x400ull || (low == 0x400ull && (mant & 1ull))) ++mant;
+                    const int ex = 63 - lz + e + 1023;               // biased exponent of the result
+                    if (ex > 0 && ex < 2047)
+                        d = __longlong_as_double((long long)(sg | (((uint64_t)ex << 52) + (mant - (1ull << 52)))));
+                    else
+                        d = ldexp(__ll2double_rn(sv), e);             // out of the normal range (not met in Jacobi updates)
                 }
                 st(m, j0 + u, d);
             }
@@ -262,7 +283,14 @@ __device__ void line_exponents(int lines, int K, F f, int* out, int* scratch)
     const int li = threadIdx.x % lines, part = threadIdx.x / lines;
     int mx = -1100;
     if (part < per)
-        for (int k = part; k < K; k += per) mx = max(mx, exp2_of(f(li, k)));
+        for (int k0 = part; k0 < K; k0 += 8 * per) {
+            // eight independent loads in flight per thread
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = k0 + u * per < K ? f(li, k0 + u * per) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = max(mx, exp2_of(x[u]));
+        }
     scratch[threadIdx.x] = mx;
     __syncthreads();
     if (threadIdx.x < lines) {
