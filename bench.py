@@ -209,24 +209,29 @@ class ClockSampler:
 
 def profile_traffic(name: str) -> tuple[float | None, str | None]:
     """DRAM bytes per launch recorded under profiles/<name>.md by an ncu
-    capture, if the kernel sources are unchanged since (same source hash)."""
+    capture, if the kernel's sources are unchanged since: the summary lists
+    them (`source_files:`, names under the package's csrc/) with their hash
+    (`source_sha256:`); without a list the hash covers every source."""
     path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
         return None, None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != source_hash():
+    f = re.search(r"source_files:\s*([^\n]+)", txt)
+    files = f.group(1).split() if f else None
+    if not m or not h or h.group(1) != source_hash(files):
         return None, path
     return float(m.group(1)), path
 
 
-def source_hash() -> str:
+def source_hash(files: list[str] | None = None) -> str:
     d = os.path.join(ROOT, "paper_2608_28952_gb300", "csrc")
+    names = sorted(files) if files else sorted(f for f in os.listdir(d) if f.endswith((".cu", ".cpp", ".h", ".cuh")))
     hsh = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cpp", ".h", ".cuh")):
-            hsh.update(open(os.path.join(d, f), "rb").read())
+    for f in names:
+        p = os.path.join(d, f)
+        hsh.update(open(p, "rb").read() if os.path.exists(p) else b"missing:" + f.encode())
     return hsh.hexdigest()[:16]
 
 

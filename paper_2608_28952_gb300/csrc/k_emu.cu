@@ -54,11 +54,11 @@ __device__ __forceinline__ int exp2_of(double x)
     return -1075 + (64 - __clzll((long long)(b & 0xFFFFFFFFFFFFFull)));   // subnormal
 }
 
-// The eight slices of x for the row/column scale 2^E (|x| < 2^E): the signed
-// fixed-point value Xs = x 2^{56-E} (rounded to nearest where x is more than
+// The eight slices of x for the row/column scale 2^E (|x| < 2^E): the
+// fixed-point value X = |x| 2^{56-E} (rounded to nearest where x is more than
 // four binades below the scale; exact otherwise) written with balanced
-// base-2^7 digits, Xs = sum_p d_p 2^{56-7p}, d_1 in [-128, 128], the others in
-// [-64, 64] (each rounded to nearest, the last one the exact remainder).
+// base-2^7 digits, X = sum_p d_p 2^{56-7p}, d_1 in [0, 128], the others in
+// [-64, 63], and the sign of x on every digit.
 // Balanced digits keep the discarded low-order products unbiased; with
 // truncated digits they always shrink |a b| and the bias builds up over the
 // hundreds of update steps of a solve.
@@ -72,23 +72,22 @@ __device__ __forceinline__ void slice8(double x, int E, __nv_bfloat16 (&s)[ENS])
         M |= 1ull << 52;
         e = ea - 1023;
     }
-    const int sh = e - E + 4;   // |Xs| = M 2^sh < 2^56
+    const int sh = e - E + 4;   // |X| = M 2^sh < 2^56
     uint64_t X;
     if (sh >= 0) X = M << sh;
     else if (sh > -54) X = (M + (1ull << (-sh - 1))) >> -sh;
     else X = 0ull;
-    long long r = (b >> 63) ? -(long long)X : (long long)X;
+    // Balanced digits by one offset: with H = 64 sum_{p=2..8} 2^{56-7p},
+    // the base-128 digits u_p of Y = X + H give d_p = u_p - 64 (p >= 2) and
+    // d_1 = Y >> 49; the sign of x is applied to every digit.
+    const uint64_t H = 64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+    const uint64_t Y = X + H;
+    const bool neg = (b >> 63) != 0;
 #pragma unroll
     for (int p = 1; p <= ENS; ++p) {
-        long long d;
-        if (p < ENS) {
-            const int shp = 56 - 7 * p;
-            d = (r + (1ll << (shp - 1))) >> shp;   // round half up (arithmetic shift)
-            r -= d << shp;
-        } else {
-            d = r;
-        }
-        s[p - 1] = __float2bfloat16_rn(__int2float_rn((int)d) * __int_as_float((127 - 7 * (p - 1)) << 23));
+        int d = p == 1 ? (int)(Y >> 49) : (int)((Y >> (56 - 7 * p)) & 127ull) - 64;
+        if (neg) d = -d;
+        s[p - 1] = __float2bfloat16_rn(__int2float_rn(d) * __int_as_float((127 - 7 * (p - 1)) << 23));
     }
 }
 

@@ -180,11 +180,11 @@ def test_mixed_edge_cases(jg):
     Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
     rc, _ = jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=MIXED))
     assert rc == jg.ERR_NONFINITE
-    # warm start and the other low-precision kinds are not offered
+    # warm start is not offered with the mixed form; precision codes past FP64_EMU are rejected
     A[7, 3] = 0.0
     Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
     assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=MIXED, warm_start=1))[0] == jg.ERR_UNSUPPORTED
-    assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=5))[0] == -7
+    assert jg.jacobi_syev(Ad, w, Qd, jg.params(b=8, precision=6))[0] == -7
 
 
 def test_mixed_deterministic(jg):
