@@ -111,6 +111,16 @@ WORKLOADS = {
                           desc="mixed-precision two-sided block Jacobi EVD (tf32 big/small x3 tensor-core "
                                "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, b=128, "
                                "lam ~ U[-1,1], eigenvalues + full Q"),
+    "mixed4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=13,
+                         refine_steps=2, fp64_products=1,
+                         desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
+                              "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
+                              "on the bf16 tensor cores), n=4096, b=64, lam ~ U[-1,1], eigenvalues + full Q"),
+    "mixed8192emu": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14,
+                         refine_steps=1, fp64_products=1,
+                         desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
+                              "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
+                              "on the bf16 tensor cores), n=8192, b=128, lam ~ U[-1,1], eigenvalues + full Q"),
     "evd8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, ref_sweeps=14,
                     desc="plain FP64 two-sided block Jacobi EVD, n=8192, b=128, round-robin, "
                          "lam ~ U[-1,1], eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
@@ -382,7 +392,9 @@ def evd_kernel_classes(stats, wl, peaks):
     lowp_steps = sum(st.sweeps_lowp for st in stats) * S
     tot = lambda f: sum(getattr(st, f) for st in stats)
     bf16 = peaks.get("bf16_tflops_sustained")
-    emu = wl.get("precision", 0) == 5
+    emu = wl.get("precision", 0) == 5 or wl.get("fp64_products", 0) == 1
+    # an emulated FP64 product issues 36 bf16 slice products per FP64 product
+    emu_slice = 36 * tot("flops_update") if emu else 0
     cls = {
         "pivot": dict(kernel="k_pivot / k_pivot_cluster", ms=tot("ms_pivot"),
                       launches=tot("pivot_launches"),
@@ -393,13 +405,14 @@ def evd_kernel_classes(stats, wl, peaks):
         # FP64-accurate products from bf16 slices: the roofline is the bf16
         # tensor pipe on the issued slice products; the FP64-equivalent rate
         # is reported beside it
+        ms_emu = tot("ms_update") - tot("ms_update_lowp")
         cls["update_emu"] = dict(kernel="k_emu_upd1 + k_emu_upd2 (tcgen05, FP64-accurate)",
-                                 ms=tot("ms_update"), launches=tot("update_launches"),
-                                 flops=tot("flops_lowp"), bound="tensor", peak=bf16,
+                                 ms=ms_emu, launches=tot("update_launches") - 3 * lowp_steps,
+                                 flops=emu_slice, bound="tensor", peak=bf16,
                                  peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
                                             "flops = the 36 bf16 slice products issued",
-                                 fp64_equiv_tflops=(tot("flops_update") / (tot("ms_update") / 1e3) / 1e12
-                                                    if tot("ms_update") > 0 else None))
+                                 fp64_equiv_tflops=(tot("flops_update") / (ms_emu / 1e3) / 1e12
+                                                    if ms_emu > 0 else None))
     else:
         cls["update_fp64"] = dict(kernel="k_update_evd", ms=tot("ms_update") - tot("ms_update_lowp"),
                                   launches=tot("update_launches") - 3 * lowp_steps,
@@ -407,12 +420,22 @@ def evd_kernel_classes(stats, wl, peaks):
                                   peak_basis=FP64_BASIS)
     if tot("sweeps_lowp") > 0:
         cls["update_lowp"] = dict(kernel="k_tc_split_v + k_tc_upd1 + k_tc_upd2 (tcgen05)",
-                                  ms=tot("ms_update_lowp"), launches=3 * lowp_steps, flops=tot("flops_lowp"), bound="tensor",
+                                  ms=tot("ms_update_lowp"), launches=3 * lowp_steps,
+                                  flops=tot("flops_lowp") - emu_slice, bound="tensor",
                                   peak=bf16, peak_basis="measured bf16 dense, sustained "
                                   "(MEASURED_PEAKS.json); flops = the three bf16 products issued")
-        cls["refine"] = dict(kernel="k_gemm64 (+ elementwise)", ms=tot("ms_refine"),
-                             launches=None, flops=tot("flops_refine"), bound="alu",
-                             peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS)
+        if emu:
+            cls["refine"] = dict(kernel="k_emu_gemm_big (tcgen05, FP64-accurate; + elementwise)",
+                                 ms=tot("ms_refine"), launches=None, flops=36 * tot("flops_refine"),
+                                 bound="tensor", peak=bf16,
+                                 peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
+                                            "flops = the 36 bf16 slice products issued",
+                                 fp64_equiv_tflops=(tot("flops_refine") / (tot("ms_refine") / 1e3) / 1e12
+                                                    if tot("ms_refine") > 0 else None))
+        else:
+            cls["refine"] = dict(kernel="k_gemm64 (+ elementwise)", ms=tot("ms_refine"),
+                                 launches=None, flops=tot("flops_refine"), bound="alu",
+                                 peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS)
     for c in cls.values():
         c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
         c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
@@ -450,7 +473,7 @@ def run_gpu(args, wl):
     X, ref = make_input(wl)
     b = wl["b"]
     prec = wl.get("precision", 0)
-    extra = {"refine_steps": wl["refine_steps"]} if "refine_steps" in wl else {}
+    extra = {k: wl[k] for k in ("refine_steps", "fp64_products") if k in wl}
     p = jg.params(b=b, inner_max_sweeps=args.inner_max_sweeps, precision=prec, **extra)
     Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
     Wd = torch.empty_like(Xd.t()).t()  # column-major work copy

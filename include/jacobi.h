@@ -108,6 +108,12 @@ typedef struct {
                              Algorithms 1, 2 and 6); 1 = sorted by descending
                              eigenvalue over the pivot's non-padding rows
                              (default; far fewer sweeps on graded spectra)    */
+    int fp64_products;    /* how the FP64 sweeps form their update products:
+                             0 = FP64 FMA (default); 1 = FP64-accurate products
+                             on the bf16 tensor cores as in
+                             JACOBI_PREC_FP64_EMU (b <= 128).  Applies to the
+                             plain FP64 solve and to the closing sweeps of the
+                             mixed forms                                       */
 } jacobi_params;
 
 typedef struct {
@@ -311,6 +317,22 @@ void jacobi_plan_destroy(jacobi_plan* plan);
  */
 int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
                              const jacobi_params* p, int step, void* stream);
+
+/*
+ * jacobi_rotation_params -- diagnostic: the 2x2 symmetric Schur rotation of
+ * the scalar Jacobi solves inside every FP64 pivot solve (Sec. 2.1,
+ * Algorithm 1 applied with b = 1), for `count` triples (app[i], aqq[i],
+ * apq[i]) in device memory.  For each i, out[8 i .. 8 i + 7] (device) gets
+ * t, s, tau and the rotation test (1.0 rotate, 0.0 skip) as the pivot solves
+ * compute them (FP32 seeds refined by Newton steps in FP64), then t, s, tau
+ * and the test by the textbook formulas in correctly rounded FP64 operations
+ * (zeta = (aqq - app)/(2 apq), t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
+ * c = 1/sqrt(1 + t^2), s = t c, tau = s/(1 + c); rotate when
+ * |apq| > tol sqrt|app| sqrt|aqq|).  Returns 0, -k for an invalid
+ * argument k, JACOBI_ERR_CUDA.
+ */
+int jacobi_rotation_params(int count, const double* app, const double* aqq, const double* apq, double tol,
+                           double* out, void* stream);
 
 /*
  * jacobi_lowp_gemm -- the split-precision tensor-core product used by the

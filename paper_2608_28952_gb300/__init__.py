@@ -41,7 +41,7 @@ class jacobi_params(C.Structure):
                 ("inner_max_sweeps", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("precision", C.c_int), ("conv", C.c_int), ("want_vectors", C.c_int),
                 ("warm_start", C.c_int), ("switch_tol", C.c_double), ("refine_steps", C.c_int),
-                ("pivot_order", C.c_int)]
+                ("pivot_order", C.c_int), ("fp64_products", C.c_int)]
 
 
 class jacobi_stats(C.Structure):
@@ -126,6 +126,7 @@ SIGNATURES = {
     "jacobi_lowp_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
     "jacobi_syev_step_lowp": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_f64emu_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
+    "jacobi_rotation_params": (_I, [_I, _P, _P, _P, _D, _P, _P]),
 }
 
 _LIB = None
@@ -284,6 +285,14 @@ def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
     M = C.shape[0]
     return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
                                   _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
+
+
+def jacobi_rotation_params(app, aqq, apq, tol: float, out, stream=None):
+    """C ``jacobi_rotation_params``: for each triple, out[i] = (t, s, tau,
+    rotate) as the FP64 pivot solves compute them, then the same four by the
+    textbook formulas (contiguous FP64 CUDA tensors; out is count x 8)."""
+    return lib().jacobi_rotation_params(app.numel(), _ptr(app), _ptr(aqq), _ptr(apq), float(tol), _ptr(out),
+                                        _stream_ptr(stream))
 
 
 def jacobi_f64emu_gemm(A, B, C, transA: bool = False, stream=None):

@@ -198,7 +198,7 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         int* rank = ws.get<int>(n);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
-        if (p.precision == JACOBI_PREC_FP64_EMU) {
+        if (p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
         }
@@ -573,7 +573,7 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         E.cnt = ws.get<DevCounters>(1);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
-        if (p.precision == JACOBI_PREC_FP64_EMU) {
+        if (p.precision == JACOBI_PREC_FP64_EMU || (p.precision == JACOBI_PREC_FP64 && p.fp64_products == 1)) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
         } else if (p.precision != JACOBI_PREC_FP64) {
@@ -724,4 +724,17 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         if (relmax_out) *relmax_out = h;
     }
     return 0;
+}
+
+extern "C" int jacobi_rotation_params(int count, const double* app, const double* aqq, const double* apq,
+                                      double tol, double* out, void* stream)
+{
+    if (count < 0) return -1;
+    if (count > 0 && !app) return -2;
+    if (count > 0 && !aqq) return -3;
+    if (count > 0 && !apq) return -4;
+    if (!(tol >= 0.0)) return -5;
+    if (count > 0 && !out) return -6;
+    return launch_rotation_params(count, app, aqq, apq, tol, out, (cudaStream_t)stream) == cudaSuccess
+               ? 0 : JACOBI_ERR_CUDA;
 }

@@ -229,6 +229,12 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.tmax = ws.get<unsigned>(tc_update_tmax_words(E.ord.dev_per_step, k));
     L.kind = p.precision == JACOBI_PREC_MIXED_FP16X3 ? 1 : (p.precision == JACOBI_PREC_MIXED_TF32 ? 2 : 0);
     L.err = ws.get<int>(1);
+    int* xexp = nullptr;          // line exponents of the emulated refinement products
+    if (p.fp64_products == 1) {   // refinement and closing sweeps with FP64-accurate tensor-core products
+        E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, k));
+        E.err = L.err;
+        xexp = ws.get<int>(2 * (size_t)np);
+    }
     if (ws.failed) return JACOBI_ERR_ALLOC;
     L.pcl = E.pcl;
     L.qtab = E.qtab;
@@ -293,22 +299,29 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         bool ok = launch_f32_to_f64((long long)np2, L.Qw[c32], X, s) == cudaSuccess;
         st->launches += 1;
         const double nn = (double)np, n3 = nn * nn * nn;
+        // C = op(Am) Bm (+ C when acc): FP64 FMA, or FP64-accurate on the tensor cores
+        auto g64 = [&](const double* Am, int transA, const double* Bm, int acc, double* Cm, int lower) {
+            if (xexp)
+                return launch_emu_gemm_big(np, np, np, Am, np, transA, Bm, np, acc, Cm, np, lower, xexp, xexp + np,
+                                           L.err, s) == cudaSuccess;
+            return launch_gemm64(np, np, np, 1.0, Am, np, transA, Bm, np, acc ? 1.0 : 0.0, Cm, np, s, lower) ==
+                   cudaSuccess;
+        };
         // X^T B for a symmetric result: the tiles meeting the lower triangle,
         // then mirrored (about half the flops of the full product)
         auto sym_xtb = [&](const double* B, double* out) {
-            return launch_gemm64(np, np, np, 1.0, X, np, 1, B, np, 0.0, out, np, s, 1) == cudaSuccess &&
-                   launch_mirror_lower(np, out, np, s) == cudaSuccess;
+            return g64(X, 1, B, 0, out, 1) && launch_mirror_lower(np, out, np, s) == cudaSuccess;
         };
         const double sym_flops = n3 + 2.0 * nn * nn * 128.0;  // lower tiles incl. the diagonal band
         double fl = 0.0;
         for (int it = 0; ok && it < p.refine_steps; ++it) {
             ok = sym_xtb(X, G) &&
-                 launch_gemm64(np, np, np, 1.0, A0p, np, 0, X, np, 0.0, W, np, s) == cudaSuccess &&
+                 g64(A0p, 0, X, 0, W, 0) &&
                  sym_xtb(W, Xn) &&
                  // Xn holds S now; E overwrites G
                  launch_oa_step_elementwise(np, Xn, G, lam, 1e-2, s) == cudaSuccess &&
                  cudaMemcpyAsync(Xn, X, np2 * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
-                 launch_gemm64(np, np, np, 1.0, X, np, 0, G, np, 1.0, Xn, np, s) == cudaSuccess;
+                 g64(X, 0, G, 1, Xn, 0);
             std::swap(X, Xn);
             fl += 2.0 * sym_flops + 4.0 * n3;
             st->launches += 8;
@@ -333,7 +346,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
             }
             if (rnorm <= orth_goal) break;
             ok = cudaMemcpyAsync(Xn, X, np2 * sizeof(double), cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
-                 launch_gemm64(np, np, np, 1.0, X, np, 0, G, np, 1.0, Xn, np, s) == cudaSuccess;
+                 g64(X, 0, G, 1, Xn, 0);
             std::swap(X, Xn);
             fl += 2.0 * n3;
             st->launches += 1;
@@ -342,8 +355,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         // S = X^T A0 X into the A buffer paired with X (its lower tiles, mirrored)
         cur = X == E.Qw[0] ? 0 : 1;
         double* Wt = E.Aw[cur ^ 1];
-        ok = ok && launch_gemm64(np, np, np, 1.0, A0p, np, 0, X, np, 0.0, Wt, np, s) == cudaSuccess &&
-             sym_xtb(Wt, E.Aw[cur]);
+        ok = ok && g64(A0p, 0, X, 0, Wt, 0) && sym_xtb(Wt, E.Aw[cur]);
         fl += 2.0 * n3 + sym_flops;
         st->launches += 3;
         st->flops_fp64 += fl;
@@ -393,9 +405,12 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
                             lda, rank, s) != cudaSuccess)
         return JACOBI_ERR_CUDA;
     st->launches += 2;
+    int h_err = 0;
     if (cudaMemcpyAsync(&hc, E.cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h_err, L.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return JACOBI_ERR_CUDA;
+    if (h_err) return JACOBI_ERR_TIMEOUT;
     const double host_fp64 = st->flops_fp64;
     fill_counters(st, hc);
     st->flops_fp64 += host_fp64;

@@ -139,6 +139,8 @@ cudaError_t launch_load_svd(int m, int n, int np, const double* G, int ldg, doub
                             double* Vw, DevCounters* cnt, cudaStream_t s);
 // Max over pairs of relmax[0..npairs) into *out (max with its prior value).
 cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaStream_t s);
+cudaError_t launch_rotation_params(int count, const double* app, const double* aqq, const double* apq, double tol,
+                                   double* out, cudaStream_t s);
 
 // ----------------------------------------------------------------- mixed form (tensor cores)
 // One low-precision step's updates on FP32 working copies: stage 1
@@ -168,6 +170,13 @@ size_t tc_update_tmax_words(int npairs, int k);
 // C (M x N) = op(A) B, column-major FP64.
 cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
                             double* C, int ldc, int* err, cudaStream_t s);
+// The same product for any K (exact FP32 accumulation per 256 K values,
+// 64-bit integer running sums): C = op(A) B, or C += op(A) B when
+// accumulate; tiles wholly above the diagonal skipped when lower.  xA, xB:
+// int workspace of M and N entries (line exponents).
+cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                int accumulate, double* C, int ldc, int lower, int* xA, int* xB, int* err,
+                                cudaStream_t s);
 // The step update of the FP64 path with every product FP64-accurate on the
 // tensor cores (stage 1 T = A_{P1P2} V2 and Q V_P, stage 2 V1^T T mirrored).
 struct EmuUpdArgs {

@@ -47,7 +47,7 @@ struct Lim<float> {
 // with diagonal (app - t apq, aqq + t apq).  Every operation is rounded
 // separately (no contraction).  Returns s, t and tau = s/(1+c).
 template <typename T>
-__device__ __forceinline__ void schur2(T app, T aqq, T apq, T& s, T& t, T& tau)
+__device__ __forceinline__ void schur2_ref(T app, T aqq, T apq, T& s, T& t, T& tau)
 {
     const T zeta = rn_div(rn_sub(aqq, app), rn_mul(T(2), apq));
     if (fabs(zeta) > Lim<T>::big) {
@@ -62,9 +62,87 @@ __device__ __forceinline__ void schur2(T app, T aqq, T apq, T& s, T& t, T& tau)
 }
 
 template <typename T>
+__device__ __forceinline__ void schur2(T app, T aqq, T apq, T& s, T& t, T& tau)
+{
+    schur2_ref(app, aqq, apq, s, t, tau);
+}
+
+template <typename T>
 __device__ __forceinline__ bool rotation_wanted(T app, T aqq, T apq, T tol)
 {
     if (apq == T(0)) return false;
+    return fabs(apq) > rn_mul(rn_mul(tol, rn_sqrt(fabs(app))), rn_sqrt(fabs(aqq)));
+}
+
+// ---------------------------------------------------------------- FP64 with few FP64 instructions
+// On this part FP64 runs at 1/64 of the FP32 rate, and a correctly rounded
+// FP64 division or square root is a chain of about ten dependent FP64
+// instructions; the textbook rotation has four divisions and two square
+// roots in series.  The FP64 overloads below take FP32 seeds (FP32 runs on
+// the fast pipe) and refine them with Newton's method in FP64:
+//   * t is the root of g(t) = apq t^2 + (aqq - app) t - apq with |t| <= 1
+//     (the same root the textbook formula picks); the FP32 seed comes from
+//     t = sgn(zeta) |2 apq| / (|d| + sqrt(d^2 + 4 apq^2)), d = aqq - app,
+//     evaluated on d and apq scaled by a power of two, and Newton steps
+//     t <- t - g(t) r on the scaled g use the seed's r ~ 1/g'(t) (each step
+//     squares the relative error, 2^-22 -> 2^-44 -> below 2^-53);
+//   * c = 1/sqrt(1 + t^2) from an FP32 reciprocal square root y0 and one
+//     second-order step y = y0 (1 + h/2 + 3h^2/8), h = 1 - x y0^2;
+//   * tau = s/(1 + c) with 1/(1 + c) from an FP32 reciprocal r0 and one
+//     second-order step r = r0 (1 + e + e^2), e = 1 - (1 + c) r0.
+// The results agree with the textbook ones to a few units in the last
+// place, and c^2 + s^2 = 1 to the same order, so the rotation applied in
+// Rutishauser's form stays orthogonal to working precision.
+__device__ __forceinline__ int f64_biased_exp(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+
+__device__ __forceinline__ void schur2(double app, double aqq, double apq, double& s, double& t, double& tau)
+{
+    const double d = rn_sub(aqq, app);
+    // scale d and apq by 2^(1022 - E'), E' = clamp(max exponent, 2, 2044): the larger lands in [0.5, 4)
+    int E = max(f64_biased_exp(d), f64_biased_exp(apq));
+    E = min(max(E, 2), 2044);
+    // (t depends on the ratio only: the Newton steps run on the scaled values,
+    // so 1/g' stays in range even for subnormal apq)
+    const double sc = __hiloint2double((2045 - E) << 20, 0);
+    const double ds = d * sc, as = apq * sc;
+    const float d32 = (float)ds, a2 = 2.0f * (float)as;
+    const bool dzero = (__double_as_longlong(d) << 1) == 0;
+    const bool dneg = __double2hiint(d) < 0, aneg = __double2hiint(apq) < 0;
+    const float R = sqrtf(fmaf(d32, d32, a2 * a2));
+    const float sgz = (dzero || dneg == aneg) ? 1.0f : -1.0f;          // sgn(zeta), sgn(0) = +1
+    const float t32 = sgz * __fdividef(fabsf(a2), fabsf(d32) + R);
+    const float sgg = dzero ? (aneg ? -1.0f : 1.0f) : (dneg ? -1.0f : 1.0f);   // sign of g'(t)
+    const double r = (double)__fdividef(sgg, R);                       // ~ 1/g_s'(t), g_s = g sc
+    double tt = (double)t32;
+    tt = fma(-fma(fma(as, tt, ds), tt, -as), r, tt);
+    tt = fma(-fma(fma(as, tt, ds), tt, -as), r, tt);
+    if (fabsf(a2) < 1e-30f)   // the seed lost bits (FP32 subnormal range): one more step
+        tt = fma(-fma(fma(as, tt, ds), tt, -as), r, tt);
+    t = tt;
+    const double x = fma(tt, tt, 1.0);                                 // in [1, 2]
+    const double y0 = (double)rsqrtf((float)x);
+    const double h = fma(-(x * y0), y0, 1.0);
+    const double c = fma(y0 * h, fma(0.375, h, 0.5), y0);
+    s = tt * c;
+    const double u = 1.0 + c;                                          // in (1.7, 2]
+    const double r0 = (double)__fdividef(1.0f, (float)u);
+    const double e = fma(-u, r0, 1.0);
+    tau = s * fma(r0, fma(e, e, e), r0);
+}
+
+// |apq| > tol sqrt|app| sqrt|aqq| as apq^2 > tol^2 |app| |aqq| where every
+// operand lies in [2^-400, 2^400] (no overflow or underflow in the squares;
+// nonnegative doubles compare like their bit patterns), else the square-root
+// form.
+__device__ __forceinline__ bool rotation_wanted(double app, double aqq, double apq, double tol)
+{
+    if ((__double_as_longlong(apq) << 1) == 0) return false;
+    const int ep = f64_biased_exp(apq), e1 = f64_biased_exp(app), e2 = f64_biased_exp(aqq);
+    const bool safe = ep >= 623 && ep <= 1423 && e1 >= 623 && e1 <= 1423 && e2 >= 623 && e2 <= 1423;
+    if (safe) {
+        const double lhs = apq * apq, rhs = (tol * tol) * (fabs(app) * fabs(aqq));
+        return __double_as_longlong(lhs) > __double_as_longlong(rhs);
+    }
     return fabs(apq) > rn_mul(rn_mul(tol, rn_sqrt(fabs(app))), rn_sqrt(fabs(aqq)));
 }
 

@@ -38,6 +38,7 @@ namespace jac {
 namespace {
 
 constexpr int EM = 128, EN = 64, EK = 32, ENS = 8, ENACC = 6, E_T = 256;
+constexpr int E_KSUPER = 256;   // K values per exact FP32 accumulation
 constexpr int E_ATILE = EM * EK * 2;                      // one A slice tile (8 KB)
 constexpr int E_BTILE = EN * EK * 2;                      // one B slice tile (4 KB)
 constexpr int E_STAGE = ENS * (E_ATILE + E_BTILE);        // 96 KB
@@ -111,11 +112,34 @@ __device__ __forceinline__ void store_slices(unsigned char* base, int tile_bytes
 
 }  // namespace
 
-// C tile (128 x 64) = Aop (128 x K) * Bop (K x 64) in FP64 accuracy, K <= 256.
+// S 2^e in FP64, rounded to nearest even, by integer operations (the FP64
+// pipe runs at 1/64 rate); the ldexp path is for results outside the normal
+// range (not met in Jacobi updates).
+__device__ __forceinline__ double i64_scaled(long long sv, int e)
+{
+    if (sv == 0) return 0.0;
+    const uint64_t sg = sv < 0 ? (1ull << 63) : 0ull;
+    const uint64_t mag = sv < 0 ? (uint64_t)(-sv) : (uint64_t)sv;
+    const int lz = __clzll((long long)mag);
+    const uint64_t mm = mag << lz;                    // leading one at bit 63
+    uint64_t mant = mm >> 11;                         // 53 bits
+    const uint64_t low = mm & 0x7FFull;
+    if (low > 0x400ull || (low == 0x400ull && (mant & 1ull))) ++mant;
+    const int ex = 63 - lz + e + 1023;               // biased exponent of the result
+    if (ex > 0 && ex < 2047)
+        return __longlong_as_double((long long)(sg | (((uint64_t)ex << 52) + (mant - (1ull << 52)))));
+    return ldexp(__ll2double_rn(sv), e);
+}
+
+// C tile (128 x 64) = Aop (128 x K) * Bop (K x 64) in FP64 accuracy.
 // fa(m, k), fb(k, n): FP64 operand values (0 outside); eA[m], eB[n]: the
 // row / column scale exponents in shared memory (filled by the caller, all
-// threads synchronised); st(m, n, v) stores.
-template <class FA, class FB, class ST>
+// threads synchronised); st(m, n, v) stores.  K <= 256 unless BIG: then the
+// accumulators are drained every 256 K values (so every level sum stays
+// exact in FP32) into 64-bit integer running sums held in registers, in
+// units of 2^{sh - 35} with sh = the shift that keeps |sum| below 2^63
+// (sh = 0 up to K = 8192).
+template <bool BIG, class FA, class FB, class ST>
 __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST st, int* err)
 {
     extern __shared__ __align__(1024) unsigned char esm[];
@@ -142,6 +166,56 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = idesc_bf16(EM, EN);
     const int nchk = (K + EK - 1) / EK;
+    constexpr int CH = E_KSUPER / EK;   // chunks per exact accumulation
+    int sh = 0;
+    if (BIG)
+        while ((long long)K > (8192ll << sh)) ++sh;
+    // epilogue mapping: thread (quadrant qd, half h) owns row m, columns h*32 .. h*32+31
+    const int qd = warp & 3, h = warp >> 2, m = qd * 32 + lane;
+    long long R[BIG ? 32 : 1];
+#pragma unroll
+    for (int u = 0; u < (BIG ? 32 : 1); ++u) R[u] = 0;
+    // The exact levels hold integers I_l 2^{-7l} (|I_l| < 2^24): their sum is
+    // the integer S = sum_l I_l 2^{7(5-l)} in units of 2^-35 (|S| < 2^58 for
+    // K <= 256), formed exactly in 64-bit integers; the shared low levels
+    // (weights 2^-35 .. 2^-49) are rounded to that unit, 2^-57 of the level-0
+    // unit.  One conversion to FP64, the scale 2^{E_m + F_n - 49} in the
+    // exponent field.
+    auto drain = [&](bool last) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int j0 = h * 32 + g * 8;
+            long long S[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) S[u] = 0;
+#pragma unroll
+            for (int l = 0; l < ENACC; ++l) {
+                uint32_t v[8];
+                const uint32_t addr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(l * EN + j0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // 2^{7 l} for the exact levels, 2^{35 - sh} for the shared one
+                const float up = __int_as_float((127 + (l < ENACC - 1 ? 7 * l : 7 * l - sh)) << 23);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int x = __float2int_rn(__uint_as_float(v[u]) * up);   // |x| < 2^24 (2^17 for the shared one)
+                    S[u] += l < ENACC - 1 ? ((long long)x << (7 * (ENACC - 1 - l) - sh)) : (long long)x;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (BIG) {
+                    R[g * 8 + u] += S[u];
+                    if (last) st(m, j0 + u, i64_scaled(R[g * 8 + u], eA[m] + eB[j0 + u] - 49 + sh));
+                } else {
+                    st(m, j0 + u, i64_scaled(S[u], eA[m] + eB[j0 + u] - 49));
+                }
+            }
+        }
+    };
     uint32_t uses[2] = {0, 0};
     // operand registers of one chunk: A items (r, g) = tid, tid + 256 (rows
     // r = it % 128, eight K values g * 8 ..), B item (n, g) = tid; the next
@@ -180,6 +254,7 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(st_a), b0 = smem_u32(st_b);
+            const bool first = (c % CH) == 0;   // the first chunk of an exact accumulation
 #pragma unroll
             for (int ks = 0; ks < EK / 16; ++ks) {
                 const uint32_t koff = ks * 256;
@@ -190,7 +265,7 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
                     for (int q = 1; q <= ENS + 1 - p; ++q) {
                         const uint64_t db = smem_desc(b0 + (q - 1) * E_BTILE + koff, 128, 512);
                         const int l = p + q - 2 < ENACC - 1 ? p + q - 2 : ENACC - 1;
-                        const uint32_t acc = (c > 0 || ks > 0 || p > 1 || q > ENACC) ? 1u : 0u;
+                        const uint32_t acc = (!first || ks > 0 || p > 1 || q > ENACC) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(tmem + (uint32_t)(l * EN)),
@@ -203,6 +278,16 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
                          : "memory");
         }
         uses[s]++;
+        if (BIG && (c + 1) % CH == 0 && c + 1 < nchk) {
+            // drain this exact accumulation before the next one overwrites it
+            if (!mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+            __syncthreads();
+            if (s_fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain(false);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
     }
     __syncthreads();
     if (!s_fail)
@@ -210,60 +295,10 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
             if (uses[s] > 0 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!s_fail) {
-        const int qd = warp & 3, h = warp >> 2, m = qd * 32 + lane;
-        for (int j0 = h * 32; j0 < h * 32 + 32; j0 += 8) {
-            // The exact levels hold integers I_l 2^{-7l} (|I_l| < 2^24): their sum
-            // is the integer S = sum_l I_l 2^{7(5-l)} in units of 2^-35 (|S| <
-            // 2^58), formed exactly in 64-bit integers; the shared low levels
-            // (weights 2^-35 .. 2^-49) are rounded to that unit, 2^-57 of the
-            // level-0 unit.  One conversion to FP64, and the scale
-            // 2^{E_m + F_n - 49} goes into the exponent field.
-            long long S[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) S[u] = 0;
-#pragma unroll
-            for (int l = 0; l < ENACC; ++l) {
-                uint32_t v[8];
-                const uint32_t addr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(l * EN + j0);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                    : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const float up = __int_as_float((127 + 7 * l) << 23);   // 2^{7 l} (2^35 for the shared one)
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int x = __float2int_rn(__uint_as_float(v[u]) * up);   // |x| < 2^24 (2^17 for the shared one)
-                    S[u] += l < ENACC - 1 ? (long long)x * (1ll << (7 * (ENACC - 1 - l))) : (long long)x;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                // S 2^{E_m + F_n - 49} in FP64, rounded to nearest even, by integer operations
-                const long long sv = S[u];
-                const int e = eA[m] + eB[j0 + u] - 49;
-                double d = 0.0;
-                if (sv != 0) {
-                    const uint64_t sg = sv < 0 ? (1ull << 63) : 0ull;
-                    const uint64_t mag = sv < 0 ? (uint64_t)(-sv) : (uint64_t)sv;
-                    const int lz = __clzll((long long)mag);
-                    const uint64_t mm = mag << lz;                    // leading one at bit 63
-                    uint64_t mant = mm >> 11;                         // 53 bits
-                    const uint64_t low = mm & 0x7FFull;
-                    if (low > 0x400ull || (low == 0x400ull && (mant & 1ull))) ++mant;
-                    const int ex = 63 - lz + e + 1023;               // biased exponent of the result
-                    if (ex > 0 && ex < 2047)
-                        d = __longlong_as_double((long long)(sg | (((uint64_t)ex << 52) + (mant - (1ull << 52)))));
-                    else
-                        d = ldexp(__ll2double_rn(sv), e);             // out of the normal range (not met in Jacobi updates)
-                }
-                st(m, j0 + u, d);
-            }
-        }
-    } else if (tid == 0) {
+    if (!s_fail)
+        drain(true);
+    else if (tid == 0)
         atomicExch(err, 1);
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -317,11 +352,84 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_gemm(int M, int N, int K, const 
     };
     line_exponents(EM, K, fa, s_eA, s_scr);
     line_exponents(EN, K, [&](int n, int k) { return fb(k, n); }, s_eB, s_scr);
-    emu_tile(K, fa, fb, s_eA, s_eB,
+    emu_tile<false>(K, fa, fb, s_eA, s_eB,
              [&](int m, int n, double v) {
                  if (m0 + m < M && n0 + n < N) C[(m0 + m) + (size_t)ldc * (n0 + n)] = v;
              },
              err);
+}
+
+// Line exponents of a whole matrix for the products with K > 256: out[i] =
+// max over line i of (exponent + 2048), 0 for an all-zero line (out zeroed
+// by the caller; atomicMax over K ranges).  by_row: line i = row i of the
+// column-major X (X[i + ld k]); else column i (X[k + ld i]).
+__global__ void k_emu_line_exps(int lines, int K, const double* __restrict__ X, int ld, int by_row, int* out)
+{
+    if (by_row) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x, k0 = blockIdx.y * 64;
+        if (i >= lines) return;
+        int mx = -1100;
+        for (int kk = k0; kk < min(K, k0 + 64); kk += 8) {
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = kk + u < K ? X[i + (size_t)ld * (kk + u)] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = max(mx, exp2_of(x[u]));
+        }
+        if (mx > -1100) atomicMax(&out[i], mx + 2048);
+    } else {
+        const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+        if (i >= lines) return;
+        const int k0 = blockIdx.y * 256;
+        int mx = -1100;
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kk = k0 + lane + 32 * u;
+            x[u] = kk < K ? X[kk + (size_t)ld * i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = max(mx, exp2_of(x[u]));
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx > -1100) atomicMax(&out[i], mx + 2048);
+    }
+}
+
+// C = op(A) B (+ C when accumulate) for any K, FP64-accurate; tiles wholly
+// above the diagonal are skipped when lower (the caller mirrors).
+__global__ void __launch_bounds__(E_T, 1) k_emu_gemm_big(int M, int N, int K, const double* __restrict__ A, int lda,
+                                                         int transA, const double* __restrict__ B, int ldb,
+                                                         int accumulate, double* __restrict__ C, int ldc, int lower,
+                                                         const int* __restrict__ xA, const int* __restrict__ xB,
+                                                         int* err)
+{
+    __shared__ int s_eA[EM], s_eB[EN];
+    const int m0 = blockIdx.x * EM, n0 = blockIdx.y * EN;
+    if (lower && m0 + EM - 1 < n0) return;
+    for (int i = threadIdx.x; i < EM + EN; i += E_T) {
+        const int v = i < EM ? (m0 + i < M ? xA[m0 + i] : 0) : (n0 + i - EM < N ? xB[n0 + i - EM] : 0);
+        const int e = v == 0 ? 0 : v - 2048 + 1;
+        if (i < EM) s_eA[i] = e;
+        else s_eB[i - EM] = e;
+    }
+    __syncthreads();
+    auto fa = [&](int m, int k) -> double {
+        const int mm = m0 + m;
+        if (mm >= M || k >= K) return 0.0;
+        return transA ? A[k + (size_t)lda * mm] : A[mm + (size_t)lda * k];
+    };
+    auto fb = [&](int k, int n) -> double {
+        const int nn = n0 + n;
+        return (nn < N && k < K) ? B[k + (size_t)ldb * nn] : 0.0;
+    };
+    emu_tile<true>(K, fa, fb, s_eA, s_eB,
+                   [&](int m, int n, double v) {
+                       if (m0 + m < M && n0 + n < N) {
+                           double* c = C + (m0 + m) + (size_t)ldc * (n0 + n);
+                           *c = accumulate ? *c + v : v;
+                       }
+                   },
+                   err);
 }
 
 }  // namespace
@@ -333,6 +441,27 @@ cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int t
     if (e != cudaSuccess) return e;
     dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
     k_emu_gemm<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, C, ldc, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                int accumulate, double* C, int ldc, int lower, int* xA, int* xB, int* err,
+                                cudaStream_t s)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xA, 0, sizeof(int) * M, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(xB, 0, sizeof(int) * N, s)) != cudaSuccess)
+        return e;
+    if (transA)   // rows of A^T: columns of A
+        k_emu_line_exps<<<dim3((M + 7) / 8, (K + 255) / 256), 256, 0, s>>>(M, K, A, lda, 0, xA);
+    else
+        k_emu_line_exps<<<dim3((M + 255) / 256, (K + 63) / 64), 256, 0, s>>>(M, K, A, lda, 1, xA);
+    k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
+    dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
+    k_emu_gemm_big<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, accumulate, C, ldc, lower, xA, xB,
+                                             err);
     return cudaGetLastError();
 }
 
@@ -388,7 +517,7 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
         auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? V2t[(n0 + n) + (size_t)k * kk] : 0.0; };
         line_exponents(EM, k, fa, s_eA, s_scr);
         line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-        emu_tile(k, fa, fb, s_eA, s_eB,
+        emu_tile<false>(k, fa, fb, s_eA, s_eB,
                  [&](int m, int n, double v) {
                      if (m0 + m < k && n0 + n < k) T[(m0 + m) + (size_t)k * (n0 + n)] = v;
                  },
@@ -422,7 +551,7 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
     auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? Vt[(n0 + n) + (size_t)k * kk] : 0.0; };
     line_exponents(EM, k, fa, s_eA, s_scr);
     line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-    emu_tile(k, fa, fb, s_eA, s_eB,
+    emu_tile<false>(k, fa, fb, s_eA, s_eB,
              [&](int m, int n, double v) {
                  if (r0 + m < u.qrows && n0 + n < k) u.Qout[(r0 + m) + (size_t)u.ldq * emap(I, J, b, n0 + n)] = v;
              },
@@ -467,7 +596,7 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
     auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? T[kk + (size_t)k * (n0 + n)] : 0.0; };
     line_exponents(EM, k, fa, s_eA, s_scr);
     line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-    emu_tile(k, fa, fb, s_eA, s_eB,
+    emu_tile<false>(k, fa, fb, s_eA, s_eB,
              [&](int m, int n, double v) {
                  if (m0 + m < k && n0 + n < k) put(m0 + m, n0 + n, v);
              },
@@ -506,7 +635,7 @@ extern "C" int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda,
                                   int ldb, double* C, int ldc, void* stream)
 {
     if (M < 0 || N < 0 || K < 0) return -1;
-    if (K > 256) return JACOBI_ERR_UNSUPPORTED;
+    if (K > (8192 << 7)) return JACOBI_ERR_UNSUPPORTED;
     if (!A || !B || !C) return -5;
     if ((!transA && lda < M) || (transA && lda < K) || ldb < K || ldc < M) return -5;
     if (M == 0 || N == 0) return 0;
@@ -518,10 +647,12 @@ extern "C" int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda,
         return 0;
     }
     int* err = nullptr;
-    if (cudaMallocAsync(&err, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_ALLOC;
+    const bool big = K > 256;
+    if (cudaMallocAsync(&err, sizeof(int) * (1 + (big ? M + N : 0)), s) != cudaSuccess) return JACOBI_ERR_ALLOC;
     int h = 0, rc = 0;
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
-        jac::launch_emu_gemm(M, N, K, A, lda, transA, B, ldb, C, ldc, err, s) != cudaSuccess ||
+        (big ? jac::launch_emu_gemm_big(M, N, K, A, lda, transA, B, ldb, 0, C, ldc, 0, err + 1, err + 1 + M, err, s)
+             : jac::launch_emu_gemm(M, N, K, A, lda, transA, B, ldb, C, ldc, err, s)) != cudaSuccess ||
         cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         rc = JACOBI_ERR_CUDA;

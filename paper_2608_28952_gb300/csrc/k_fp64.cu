@@ -955,4 +955,36 @@ cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaS
     return cudaGetLastError();
 }
 
+// ======================================================================== rotation diagnostic
+__global__ void k_rotation_params(int count, const double* __restrict__ app, const double* __restrict__ aqq,
+                                  const double* __restrict__ apq, double tol, double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double p = app[i], q = aqq[i], x = apq[i];
+    double* o = out + (size_t)8 * i;
+    double s = 0.0, t = 0.0, tau = 0.0;
+    const bool on = rotation_wanted(p, q, x, tol);
+    if (x != 0.0) schur2(p, q, x, s, t, tau);
+    o[0] = t;
+    o[1] = s;
+    o[2] = tau;
+    o[3] = on ? 1.0 : 0.0;
+    s = t = tau = 0.0;
+    const bool on_ref = x != 0.0 && fabs(x) > rn_mul(rn_mul(tol, rn_sqrt(fabs(p))), rn_sqrt(fabs(q)));
+    if (x != 0.0) schur2_ref(p, q, x, s, t, tau);
+    o[4] = t;
+    o[5] = s;
+    o[6] = tau;
+    o[7] = on_ref ? 1.0 : 0.0;
+}
+
+cudaError_t launch_rotation_params(int count, const double* app, const double* aqq, const double* apq, double tol,
+                                   double* out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_rotation_params<<<(count + 255) / 256, 256, 0, s>>>(count, app, aqq, apq, tol, out);
+    return cudaGetLastError();
+}
+
 }  // namespace jac

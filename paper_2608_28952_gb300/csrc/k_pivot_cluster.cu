@@ -44,8 +44,8 @@ size_t pivot_cluster_smem(int k, int C)
     const int half = k / 2;
     const size_t chunk = (size_t)split_max_chunk(k, C);
     const size_t vrows = (size_t)(k / C) * k;
-    return (chunk + vrows + 2 * (size_t)k + 4 * (size_t)half) * sizeof(double) +
-           3 * (size_t)half * sizeof(int) + 64;
+    return (chunk + vrows + 2 * (size_t)k + 8 * (size_t)half) * sizeof(double) +
+           6 * (size_t)half * sizeof(int) + 64;
 }
 
 __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, const unsigned* qtab)
@@ -77,14 +77,14 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     double* Vl = my_chunk + chunk_max;       // rows x k (ld rows): V(r_lo + i, j) at Vl[i + rows j]
     double* dhi = Vl + (size_t)rows * k;     // diagonal replica
     double* dlo = dhi + k;
-    double* rtau = dlo + k;
-    double* rs = rtau + half;
-    double* rt = rs + half;
-    double* rapq = rt + half;
-    int* rp = (int*)(rapq + half);
-    int* rq = rp + half;
-    int* ron = rq + half;
-    __shared__ int s_cnt;
+    double* rtau = dlo + k;                  // rotation parameters, two slots of half each
+    double* rs = rtau + 2 * half;
+    double* rt = rs + 2 * half;
+    double* rapq = rt + 2 * half;
+    int* rp = (int*)(rapq + 2 * half);
+    int* rq = rp + 2 * half;
+    int* ron = rq + 2 * half;
+    __shared__ int s_cnt[2];   // rotations chosen per sweep (by sweep parity)
     __shared__ double s_red[PC_T / 32];
     __shared__ double s_part[PC_MAXC8];
     __shared__ int s_dest[256];
@@ -148,94 +148,123 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     }
     __syncthreads();
 
-    // ---- inner sweeps
+    // ---- inner sweeps, software-pipelined over the rounds (global round
+    // index g = sweep * (k - 1) + round; parameters of round g in slot g & 1):
+    //   phase A(g): rank 0 zeroes the pivot entries a_pq of round g (every
+    //     CTA read them while choosing round g), the quads of round g over
+    //     the cluster, the diagonal replica (threads < half);
+    //   phase B(g): threads < half choose round g + 1 (it reads the a_pq the
+    //     quads of round g left and the updated diagonal) while the others
+    //     rotate this CTA's rows of V by round g.
+    // A full cluster barrier ends phase A; phase B ends with a CTA barrier
+    // and a cluster arrive whose wait comes before the next zeroing.
     const double tol = a.tol_rel;
     const int max_sweeps = frozen ? 0 : a.max_sweeps;
+    const int nr = k - 1;
     int total_rot = 0, sweeps = 0;
-    for (int sw = 0; sw < max_sweeps; ++sw) {
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
-        for (int rd = 0; rd < k - 1; ++rd) {
-            // rotations of the round, from the local diagonal and the shared a_pq
-            for (int ee = tid; ee < half; ee += nt) {
-                const int pa = ee, pb = k - 1 - ee;
-                const int ia = pa == 0 ? 0 : 1 + (pa - 1 + rd) % (k - 1);
-                const int ib = 1 + (pb - 1 + rd) % (k - 1);
-                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
-                const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
-                const bool on = rotation_wanted(app, aqq, apq, tol);
-                rp[ee] = p;
-                rq[ee] = q;
-                ron[ee] = on;
-                if (on) {
-                    double s, t, tau;
-                    schur2(app, aqq, apq, s, t, tau);
-                    rtau[ee] = tau;
-                    rs[ee] = s;
-                    rt[ee] = t;
-                    rapq[ee] = apq;
-                    atomicAdd(&s_cnt, 1);
-                }
+    auto choose = [&](int g, int slot) {
+        const int rd = g % nr;
+        int* cnt = &s_cnt[(g / nr) & 1];
+        for (int ee = tid; ee < half; ee += nt) {
+            const int pa = ee, pb = k - 1 - ee;
+            const int ia = pa == 0 ? 0 : 1 + (pa - 1 + rd) % (k - 1);
+            const int ib = 1 + (pb - 1 + rd) % (k - 1);
+            const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+            const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
+            const bool on = rotation_wanted(app, aqq, apq, tol);
+            const int o = slot * half + ee;
+            rp[o] = p;
+            rq[o] = q;
+            ron[o] = on;
+            if (on) {
+                double sv, tv, tauv;
+                schur2(app, aqq, apq, sv, tv, tauv);
+                rtau[o] = tauv;
+                rs[o] = sv;
+                rt[o] = tv;
+                rapq[o] = apq;
+                atomicAdd(cnt, 1);
             }
-            __syncthreads();
-            asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-            // quads over the whole cluster
+        }
+    };
+    if (max_sweeps > 0) {
+        if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
+        __syncthreads();
+        if (tid < half) choose(0, 0);
+        __syncthreads();
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    }
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        for (int rd = 0; rd < nr; ++rd) {
+            const int g = sw * nr + rd, so = (g & 1) * half;
+            // phase A: quads over the whole cluster
             for (int qi = gtid; qi < nq; qi += gnt) {
                 int e1, e2;
                 quad_of(qtab, qi, e1, e2);
-                const int on1 = ron[e1], on2 = ron[e2];
+                const int on1 = ron[so + e1], on2 = ron[so + e2];
                 if (!(on1 | on2)) continue;
-                const int p1 = rp[e1], q1 = rq[e1], p2 = rp[e2], q2 = rq[e2];
+                const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
                 double* a00 = ap.at(p1, p2);
                 double* a01 = ap.at(p1, q2);
                 double* a10 = ap.at(q1, p2);
                 double* a11 = ap.at(q1, q2);
                 double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
                 if (on1) {
-                    const double s = rs[e1], tau = rtau[e1];
-                    rot2(s, tau, x00, x10);
-                    rot2(s, tau, x01, x11);
+                    const double sv = rs[so + e1], tauv = rtau[so + e1];
+                    rot2(sv, tauv, x00, x10);
+                    rot2(sv, tauv, x01, x11);
                 }
                 if (on2) {
-                    const double s = rs[e2], tau = rtau[e2];
-                    rot2(s, tau, x00, x01);
-                    rot2(s, tau, x10, x11);
+                    const double sv = rs[so + e2], tauv = rtau[so + e2];
+                    rot2(sv, tauv, x00, x01);
+                    rot2(sv, tauv, x10, x11);
                 }
                 *a00 = x00;
                 *a01 = x01;
                 *a10 = x10;
                 *a11 = x11;
             }
-            // diagonal replica (every CTA)
+            // diagonal replica (every CTA): the exact 2x2 diagonal form
             for (int ee = tid; ee < half; ee += nt) {
-                if (!ron[ee]) continue;
-                const int p = rp[ee], q = rq[ee];
-                dd_add_prod(dhi[p], dlo[p], rt[ee], rapq[ee], -1.0);
-                dd_add_prod(dhi[q], dlo[q], rt[ee], rapq[ee], 1.0);
+                if (!ron[so + ee]) continue;
+                const int p = rp[so + ee], q = rq[so + ee];
+                const double tv = rt[so + ee], apq = rapq[so + ee];
+                dd_add_prod(dhi[p], dlo[p], tv, -apq, 1.0);
+                dd_add_prod(dhi[q], dlo[q], tv, apq, 1.0);
             }
-            // local rows of V
-            for (int it = tid; it < half * rows; it += nt) {
-                const int ee = it / rows, i = it - ee * rows;
-                if (!ron[ee]) continue;
-                const int p = rp[ee], q = rq[ee];
-                double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
-                rot2(rs[ee], rtau[ee], vp, vq);
-                Vl[i + (size_t)rows * p] = vp;
-                Vl[i + (size_t)rows * q] = vq;
-            }
-            // every CTA has read this round's a_pq: rank 0 may zero them now
+            // every CTA has read round g's a_pq: rank 0 zeroes them
+            __syncwarp();
             asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
             if (r == 0)
                 for (int ee = tid; ee < half; ee += nt)
-                    if (ron[ee]) *ap.at(rq[ee], rp[ee]) = 0.0;
+                    if (ron[so + ee]) *ap.at(rq[so + ee], rp[so + ee]) = 0.0;
             cluster.sync();
+            // phase B
+            if (tid < half) {
+                if (!(rd == nr - 1 && sw + 1 == max_sweeps)) choose(g + 1, (g + 1) & 1);
+            } else {
+                for (int it = tid - half; it < half * rows; it += nt - half) {
+                    const int ee = it / rows, i = it - ee * rows;
+                    if (!ron[so + ee]) continue;
+                    const int p = rp[so + ee], q = rq[so + ee];
+                    double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                    rot2(rs[so + ee], rtau[so + ee], vp, vq);
+                    Vl[i + (size_t)rows * p] = vp;
+                    Vl[i + (size_t)rows * q] = vq;
+                }
+            }
+            __syncthreads();
+            asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
         }
-        const int cnt = s_cnt;
+        const int cnt = s_cnt[sw & 1];
         total_rot += cnt;
         sweeps = sw + 1;
         __syncthreads();
+        if (tid == 0) s_cnt[sw & 1] = 0;   // reused by sweep sw + 2 (chosen after further barriers)
         if (cnt == 0) break;
     }
+    __syncwarp();
+    if (max_sweeps > 0) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
     for (int x = tid; x < k; x += nt) dhi[x] += dlo[x];  // hi + lo, rounded once
     __syncthreads();
 

@@ -41,7 +41,10 @@ def _exact(A, B):
 
 
 @pytest.mark.parametrize("M,N,K,trans", [(128, 64, 32, False), (128, 64, 256, False), (300, 200, 128, False),
-                                          (256, 130, 77, True), (1, 5, 3, False), (129, 65, 200, True)])
+                                          (256, 130, 77, True), (1, 5, 3, False), (129, 65, 200, True),
+                                          # K > 256: exact FP32 accumulation per 256 K, 64-bit running sums
+                                          (128, 64, 300, False), (200, 130, 1000, True), (128, 64, 4096, False),
+                                          (64, 40, 9000, True)])
 def test_emu_gemm_is_fp64_accurate(jg, M, N, K, trans):
     import torch
     r = np.random.default_rng(M * 7 + N + K)
@@ -79,8 +82,16 @@ def test_emu_gemm_special_values(jg):
     assert jg.jacobi_f64emu_gemm(Ad, Bd, Cd) == 0
     C = Cd.cpu().numpy()
     assert np.array_equal(C, A @ B)          # integers and powers of two are exact
-    assert jg.jacobi_f64emu_gemm(Ad, jg.colmajor(np.zeros((300, 4)), device="cuda", dtype=torch.float64),
-                                 jg.colmajor_empty(M, 4, torch.float64, "cuda")) == jg.ERR_UNSUPPORTED
+    # the same across exact accumulations (K > 256): integer entries stay exact
+    K2 = 700
+    A2 = np.zeros((M, K2))
+    A2[:, ::7] = np.arange(1, M + 1)[:, None]
+    B2 = np.zeros((K2, 4))
+    B2[::5, :] = -3.0
+    Cd2 = jg.colmajor_empty(M, 4, torch.float64, "cuda")
+    assert jg.jacobi_f64emu_gemm(jg.colmajor(A2, device="cuda", dtype=torch.float64),
+                                 jg.colmajor(B2, device="cuda", dtype=torch.float64), Cd2) == 0
+    assert np.array_equal(Cd2.cpu().numpy(), A2 @ B2)
 
 
 # ------------------------------------------------------------------ the FP64 method with emulated products
@@ -135,4 +146,24 @@ def test_emu_n4096_b64(jg):
     A, lam = gen.sym_known(n, "uniform", seed=gen.SEEDS["c2u"])
     w, Q, _, st = jg.syev(A, b=b, precision=EMU)
     assert st.status == 0
+    _check(A, w.cpu().numpy(), Q.cpu().numpy(), np.sort(lam))
+
+
+def test_fp64_products_flag_is_the_emulated_path(jg):
+    """precision FP64 with fp64_products = 1 runs the same solve as FP64_EMU."""
+    A, lam = gen.sym_known(384, "uniform", seed=5300)
+    w1, Q1, _, s1 = jg.syev(A, b=32, precision=EMU)
+    w2, Q2, _, s2 = jg.syev(A, b=32, precision=0, fp64_products=1)
+    assert s1.status == 0 and s2.status == 0 and s1.sweeps == s2.sweeps
+    assert np.array_equal(w1.cpu().numpy(), w2.cpu().numpy()) and np.array_equal(Q1.cpu().numpy(), Q2.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [2, 3, 4])
+def test_mixed_with_emulated_fp64_products_meets_the_fp64_gates(jg, prec):
+    """The mixed forms with the refinement products and the closing sweeps'
+    updates on the tensor cores (fp64_products = 1): the FP64 gates."""
+    n = 1024
+    A, lam = gen.sym_known(n, "uniform", seed=5400 + prec)
+    w, Q, _, st = jg.syev(A, b=64, precision=prec, fp64_products=1)
+    assert st.status == 0 and st.sweeps_lowp > 0
     _check(A, w.cpu().numpy(), Q.cpu().numpy(), np.sort(lam))
