@@ -114,6 +114,11 @@ typedef struct {
                              JACOBI_PREC_FP64_EMU (b <= 128).  Applies to the
                              plain FP64 solve and to the closing sweeps of the
                              mixed forms                                       */
+    int svd_qr;           /* jacobi_gesvd: 1 = factor G = QR first (Householder,
+                             blocked) and run the one-sided method on R^T,
+                             U = Q times its rotations, V = its normalised
+                             columns (Sec. 6, "Preprocessing with QR");
+                             0 = directly on G (default)                       */
 } jacobi_params;
 
 typedef struct {
@@ -151,6 +156,10 @@ typedef struct {
                                 sweeps (tensor-core update kernels)            */
     double flops_refine;     /* mixed forms: of flops_fp64, in the refinement
                                 GEMMs                                          */
+    double ms_precond;       /* gesvd with svd_qr: device time of the QR
+                                factorisation and of forming U = Q W           */
+    double flops_precond;    /* the FP64 flops issued there (also counted in
+                                flops_fp64)                                    */
 } jacobi_stats;
 
 /* Fill *p with the defaults above.  Returns 0. */
@@ -203,6 +212,11 @@ int jacobi_syev_h(int n, double* h_A, int lda, double* h_w, double* h_Q, int ldq
  * tol_eff = max(p->tol, sqrt(m) * 2^-53): a sweep whose largest normalised
  * Gram off-diagonal |a_ij| / sqrt(a_ii a_jj) is <= tol_eff ends the
  * iteration.  p->conv is ignored.
+ * With p->svd_qr = 1 (Sec. 6, "Preprocessing with QR"): G = QR by blocked
+ * Householder QR (FP64), the method above on X = R^T (n x n, so tol_eff uses
+ * sqrt(n)), X W = U_X Sigma, and G = (Q W) Sigma U_X^T: U = Q W (always
+ * computed), V = U_X.  An exactly zero singular value then gives a zero
+ * column of V instead of U.  st->ms_precond holds the QR time.
  */
 int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, double* V, int ldv,
                  const jacobi_params* p, jacobi_stats* st, void* stream);

@@ -275,6 +275,26 @@ def gesvd(G: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float | None
     return G, s, V, _stats(st), status
 
 
+def gesvd_qr(G: np.ndarray, b: int = 16, *, transpose: bool = True, **kw):
+    """One-sided SVD preconditioned by a reduced QR factorisation (Sec. 6,
+    subsection "Preprocessing with QR"): G = QR, the blocked one-sided method
+    on X = R^T (transpose, default) or on R, and the SVD of G from Q times the
+    left singular vectors of R.  The QR factorisation is LAPACK's Householder
+    QR through numpy (a library step).  On X = R^T: X W = U_X Sigma, so
+    R = W Sigma U_X^T and G = (Q W) Sigma U_X^T.  Returns (U, sigma
+    descending, V, Stats, status) like gesvd."""
+    G = _f64F(G)
+    Q, R = np.linalg.qr(G, mode="reduced")
+    R = np.triu(R)
+    kw = dict(kw)
+    kw["want_vectors"] = True
+    if transpose:
+        UX, s, W, st, status = gesvd(np.asfortranarray(R.T), b=b, **kw)
+        return np.asfortranarray(Q @ W), s, UX, st, status
+    UR, s, VR, st, status = gesvd(np.asfortranarray(R), b=b, **kw)
+    return np.asfortranarray(Q @ UR), s, VR, st, status
+
+
 # ---------------------------------------------------------------- split precision
 def split_bf16(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """hi = bf16_rn(x), lo = bf16_rn(x - hi), both returned as float32."""

@@ -41,7 +41,7 @@ class jacobi_params(C.Structure):
                 ("inner_max_sweeps", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("precision", C.c_int), ("conv", C.c_int), ("want_vectors", C.c_int),
                 ("warm_start", C.c_int), ("switch_tol", C.c_double), ("refine_steps", C.c_int),
-                ("pivot_order", C.c_int), ("fp64_products", C.c_int)]
+                ("pivot_order", C.c_int), ("fp64_products", C.c_int), ("svd_qr", C.c_int)]
 
 
 class jacobi_stats(C.Structure):
@@ -57,7 +57,8 @@ class jacobi_stats(C.Structure):
                 ("flops_fp32", C.c_double), ("flops_lowp", C.c_double),
                 ("ms_lowp", C.c_double), ("ms_refine", C.c_double),
                 ("ms_pivot_lowp", C.c_double), ("ms_update_lowp", C.c_double),
-                ("flops_refine", C.c_double)]
+                ("flops_refine", C.c_double), ("ms_precond", C.c_double),
+                ("flops_precond", C.c_double)]
 
 
 @dataclass
@@ -88,6 +89,8 @@ class Stats:
     ms_pivot_lowp: float
     ms_update_lowp: float
     flops_refine: float
+    ms_precond: float
+    flops_precond: float
     off_hist: list = field(default_factory=list)
 
 
@@ -97,7 +100,7 @@ def _stats(s: jacobi_stats) -> Stats:
                  s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
                  s.update_launches, s.flops_fp64, s.flops_update, s.flops_fp32, s.flops_lowp,
                  s.ms_lowp, s.ms_refine, s.ms_pivot_lowp, s.ms_update_lowp, s.flops_refine,
-                 list(s.off_hist)[: max(0, min(64, s.sweeps))])
+                 s.ms_precond, s.flops_precond, list(s.off_hist)[: max(0, min(64, s.sweeps))])
 
 
 # Every symbol include/jacobi.h declares, with its ctypes signature.

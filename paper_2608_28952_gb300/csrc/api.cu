@@ -434,6 +434,89 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
     return rc;
 }
 
+// One-sided SVD preconditioned by a reduced QR factorisation (Sec. 6,
+// "Preprocessing with QR"): G = QR (blocked Householder, in place), the
+// one-sided method on X = R^T, X W = U_X Sigma, then U = Q [W; 0] (the
+// reflectors applied last panel first) and V = U_X.
+static int gesvd_qr(int m, int n, double* G, int ldg, double* sigma, double* V, int ldv,
+                    const jacobi_params& p, jacobi_stats* st, cudaStream_t s)
+{
+    Timer timer(s);
+    const int nb = QR_NB, npan = (n + nb - 1) / nb;
+    int rc = 0;
+    {
+        Workspace ws(s);
+        double* Y = ws.get<double>((size_t)m * n);
+        double* tau = ws.get<double>(n);
+        double* S = ws.get<double>((size_t)nb * nb);
+        double* T = ws.get<double>((size_t)npan * nb * nb);
+        double* Tt = ws.get<double>((size_t)npan * nb * nb);
+        double* Wpart = ws.get<double>(qr_wpart_doubles(m, n));
+        double* W = ws.get<double>((size_t)nb * n);
+        double* YT = ws.get<double>((size_t)m * nb);
+        double* X = ws.get<double>((size_t)n * n);
+        double* Wv = ws.get<double>((size_t)n * n);
+        if (ws.failed) return JACOBI_ERR_ALLOC;
+        cudaEvent_t ev[4];
+        for (auto& e : ev) cudaEventCreate(&e);
+        auto destroy = [&] {
+            for (auto& e : ev) cudaEventDestroy(e);
+        };
+        double fl = 0.0;
+        bool ok = cudaEventRecord(ev[0], s) == cudaSuccess;
+        for (int pi = 0; ok && pi < npan; ++pi) {
+            const int j0 = pi * nb, nbp = std::min(nb, n - j0), rows = m - j0, nc = n - j0 - nbp;
+            double* Tp = T + (size_t)pi * nb * nb;
+            double* Ttp = Tt + (size_t)pi * nb * nb;
+            ok = launch_house_panel(m, G, ldg, j0, nbp, Y, m, tau, S, Tp, Ttp, s) == cudaSuccess &&
+                 launch_house_update(m, j0, nbp, Y, m, Tp, Ttp, 1, G + (size_t)ldg * (j0 + nbp), ldg, nc, Wpart, W,
+                                     YT, s) == cudaSuccess;
+            fl += 5.0 * rows * nbp * nbp + 4.0 * rows * nbp * nc;   // panel 3 r nb^2, Y T^T 2 r nb^2, update
+            st->launches += 2 * nbp + 1 + (nc > 0 ? 4 : 0);
+        }
+        ok = ok && launch_qr_rt(n, G, ldg, X, s) == cudaSuccess && cudaEventRecord(ev[1], s) == cudaSuccess;
+        if (!ok) {
+            destroy();
+            return JACOBI_ERR_CUDA;
+        }
+        jacobi_params pin = p;
+        pin.want_vectors = 1;
+        pin.svd_qr = 0;
+        rc = gesvd_fp64(n, n, X, n, sigma, Wv, n, pin, st, s);
+        if (rc < 0) {
+            destroy();
+            return rc;
+        }
+        ok = cudaEventRecord(ev[2], s) == cudaSuccess;
+        if (ok && p.want_vectors)
+            ok = cudaMemcpy2DAsync(V, (size_t)ldv * sizeof(double), X, (size_t)n * sizeof(double),
+                                   (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+        ok = ok && launch_qr_fill(m, n, Wv, G, ldg, s) == cudaSuccess;
+        for (int pi = npan - 1; ok && pi >= 0; --pi) {
+            const int j0 = pi * nb, nbp = std::min(nb, n - j0), rows = m - j0;
+            ok = launch_house_update(m, j0, nbp, Y, m, T + (size_t)pi * nb * nb, Tt + (size_t)pi * nb * nb, 0, G,
+                                     ldg, n, Wpart, W, YT, s) == cudaSuccess;
+            fl += 2.0 * rows * nbp * nbp + 4.0 * rows * nbp * n;
+            st->launches += 4;
+        }
+        ok = ok && cudaEventRecord(ev[3], s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+        if (!ok) {
+            destroy();
+            return JACOBI_ERR_CUDA;
+        }
+        float t01 = 0.f, t23 = 0.f;
+        cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        cudaEventElapsedTime(&t23, ev[2], ev[3]);
+        destroy();
+        st->ms_precond = (double)t01 + (double)t23;
+        st->flops_precond = fl;
+        st->flops_fp64 += fl;
+        st->launches += 2;
+    }
+    st->ms_total = timer.stop();
+    return rc;
+}
+
 extern "C" int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, double* V, int ldv,
                             const jacobi_params* pin, jacobi_stats* stout, void* stream)
 {
@@ -451,7 +534,8 @@ extern "C" int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, dou
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;
     jacobi_stats st;
     memset(&st, 0, sizeof(st));
-    int rc = gesvd_fp64(m, n, G, ldg, sigma, V, ldv, p, &st, (cudaStream_t)stream);
+    int rc = p.svd_qr ? gesvd_qr(m, n, G, ldg, sigma, V, ldv, p, &st, (cudaStream_t)stream)
+                      : gesvd_fp64(m, n, G, ldg, sigma, V, ldv, p, &st, (cudaStream_t)stream);
     st.status = rc;
     if (stout) *stout = st;
     return rc;

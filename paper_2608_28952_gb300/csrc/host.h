@@ -155,6 +155,7 @@ inline int check_params(const jacobi_params& p)
     if (p.pivot_order != 0 && p.pivot_order != 1) return -7;
     if (p.precision < JACOBI_PREC_FP64 || p.precision > JACOBI_PREC_FP64_EMU) return -7;
     if (p.fp64_products != 0 && p.fp64_products != 1) return -7;
+    if (p.svd_qr != 0 && p.svd_qr != 1) return -7;
     return 0;
 }
 

@@ -139,6 +139,20 @@ cudaError_t launch_load_svd(int m, int n, int np, const double* G, int ldg, doub
                             double* Vw, DevCounters* cnt, cudaStream_t s);
 // Max over pairs of relmax[0..npairs) into *out (max with its prior value).
 cudaError_t launch_max_into(const double* relmax, int npairs, double* out, cudaStream_t s);
+// Householder QR (blocked, compact WY; panels of QR_NB columns), see k_qr.cu.
+constexpr int QR_NB = 32;
+size_t qr_wpart_doubles(int m, int n);
+// Panel [j0, j0 + nbp) of A (m rows): reflectors into Y (ld ldy), tau, the
+// panel's T and T^T (QR_NB x QR_NB); S: QR_NB x QR_NB scratch.
+cudaError_t launch_house_panel(int m, double* A, int lda, int j0, int nbp, double* Y, int ldy, double* tau,
+                               double* S, double* T, double* Tt, cudaStream_t s);
+// X(j0:m, 0:ncol) <- X - Y_p M (Y_p^T X): M = T^T (trans) or T.  Wpart:
+// qr_wpart_doubles(m, ncol); W: QR_NB x ncol; YT: m x QR_NB.
+cudaError_t launch_house_update(int m, int j0, int nbp, const double* Y, int ldy, const double* T,
+                                const double* Tt, int trans, double* X, int ldx, int ncol, double* Wpart,
+                                double* W, double* YT, cudaStream_t s);
+cudaError_t launch_qr_rt(int n, const double* A, int lda, double* X, cudaStream_t s);
+cudaError_t launch_qr_fill(int m, int n, const double* W, double* G, int ldg, cudaStream_t s);
 cudaError_t launch_rotation_params(int count, const double* app, const double* aqq, const double* apq, double tol,
                                    double* out, cudaStream_t s);
 

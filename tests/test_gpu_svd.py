@@ -33,7 +33,7 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def check_svd(G, U, s, V, s_ref, abs_tol=1e-13, rel_tol=1e-12):
+def check_svd(G, U, s, V, s_ref, abs_tol=1e-13, rel_tol=1e-12, v_orth=1e-13):
     n = G.shape[1]
     smax = s_ref[0]
     assert np.abs(s - s_ref).max() <= abs_tol * smax, np.abs(s - s_ref).max() / smax
@@ -41,7 +41,7 @@ def check_svd(G, U, s, V, s_ref, abs_tol=1e-13, rel_tol=1e-12):
     assert (np.abs(s - s_ref)[big] / s_ref[big]).max() <= rel_tol
     nz = s > 0
     assert np.linalg.norm(U[:, nz].T @ U[:, nz] - np.eye(nz.sum())) <= 1e-12 * n
-    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= v_orth * n
     assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G) * np.sqrt(n)
 
 
@@ -133,4 +133,49 @@ def test_full_size_16384x2048_b64(jg):
     big = sig >= 1e-3 * sig[0]
     assert (np.abs(s - sig)[big] / sig[big]).max() <= 1e-12
     assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+
+
+# ------------------------------------------------------------------ QR preconditioning (svd_qr = 1)
+@pytest.mark.parametrize("m,n,b", [(500, 96, 16), (300, 45, 8), (64, 64, 8), (1030, 130, 32), (2000, 256, 32)])
+def test_qr_preconditioned_known_singular_values(jg, m, n, b):
+    """G = QR on the GPU (blocked Householder, ragged panels and row splits),
+    the one-sided method on R^T, U = Q W: the oracle's QR-preconditioned
+    singular values, orthonormal U and V, G V = U Sigma."""
+    G, sig = gen.svd_known(m, n, seed=4500 + n, decades=10.0)
+    _, s_or, _, _, rc_or = oracle.gesvd_qr(G, b=b)
+    U, s, V, st = jg.gesvd(G, b=b, svd_qr=1)
+    U, s, V = _np(U), _np(s), _np(V)
+    assert st.status == 0 and rc_or == 0 and st.ms_precond > 0
+    # V holds the normalised columns of the rotated R^T (orthogonal to the stop tolerance)
+    check_svd(G, U, s, V, s_or, v_orth=1e-12)
+    assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+
+
+def test_qr_preconditioned_rank_deficiency(jg):
+    G = gen.tall_gaussian(160, 40, 4600, dtype=np.float64)
+    G[:, 3] = 0.0
+    G[:, 17] = G[:, 5]
+    U, s, V, st = jg.gesvd(G, b=8, svd_qr=1)
+    U, s, V = _np(U), _np(s), _np(V)
+    s_or = oracle.gesvd_qr(G, b=8)[1]
+    assert st.status == 0 and np.all(np.isfinite(U)) and np.all(np.isfinite(V))
+    assert np.abs(s - s_or).max() <= 1e-13 * s_or[0]
+    assert np.linalg.norm(U.T @ U - np.eye(40)) <= 1e-12 * 40      # U = Q W keeps orthonormal columns
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G) * np.sqrt(40)
+
+
+def test_qr_preconditioned_full_size_16384x2048_b64(jg):
+    """The one-sided workload at full size through the QR form: the same
+    gates as the direct form."""
+    m, n, b = 16384, 2048, 64
+    G, sig = gen.svd_known(m, n, seed=gen.SEEDS["c3"], decades=10.0)
+    U, s, V, st = jg.gesvd(G, b=b, svd_qr=1)
+    U, s, V = _np(U), _np(s), _np(V)
+    assert st.status == 0
+    assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+    big = sig >= 1e-3 * sig[0]
+    assert (np.abs(s - sig)[big] / sig[big]).max() <= 1e-12
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-12 * n
     assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n

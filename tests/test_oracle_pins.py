@@ -527,6 +527,35 @@ def test_known_singular_values(scalar, b):
     assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
 
 
+@pytest.mark.parametrize("transpose,m,n,b", [(True, 200, 40, 4), (False, 200, 40, 4), (True, 60, 60, 6),
+                                             (True, 150, 33, 5)])
+def test_qr_preconditioned_svd_known_singular_values(transpose, m, n, b):
+    """G = QR, the one-sided method on R^T (or R), U = Q times the left
+    singular vectors of R: the constructed sigma, orthonormal U and V, and
+    G V = U Sigma."""
+    G, sig = gen.svd_known(m, n, seed=85, decades=6.0)
+    U, s, V, st, status = oracle.gesvd_qr(G, b=b, transpose=transpose)
+    assert status == 0
+    assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+    big = sig >= 1e-3 * sig[0]
+    assert (np.abs(s - sig)[big] / sig[big]).max() <= 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
+    s_direct = oracle.gesvd(G, b=b)[1]
+    assert np.abs(s - s_direct).max() <= 1e-13 * sig[0]
+
+
+def test_qr_preconditioned_svd_on_graded_columns_keeps_lapack_values():
+    # columns scaled over 8 decades: the factor R inherits the grading
+    m, n = 120, 24
+    G = gen.tall_gaussian(m, n, 86, dtype=np.float64) * (10.0 ** -np.linspace(0, 8, n))[None, :]
+    U, s, V, st, status = oracle.gesvd_qr(G, b=4)
+    sl = np.linalg.svd(G, compute_uv=False)
+    assert status == 0 and np.abs(s - sl).max() <= 1e-13 * sl[0]
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
+
+
 def test_svd_lapack_witness_and_zero_column():
     m, n = 90, 30
     G = gen.tall_gaussian(m, n, 82, dtype=np.float64)
