@@ -307,7 +307,8 @@ def cpu_oracle_sample(wl, sweeps: int, budget_s: float = 10.0, start_step: int =
         Ak[:, :n] = A
         Qk = np.eye(N * b)
         tol = oracle.svd_tol(m)
-        run = lambda s, X, Y: oracle.gesvd_step(X, Y, b, tab[s], tol_rel=tol)[:2]
+        cap = 2 if wl.get("svd_qr") else 30   # the library's automatic inner-sweep caps
+        run = lambda s, X, Y: oracle.gesvd_step(X, Y, b, tab[s], tol_rel=tol, inner_max=cap)[:2]
     S = len(tab)
     done, t0 = 0, time.perf_counter()
     times = []
@@ -582,33 +583,45 @@ def run_gpu(args, wl):
                     "share_of_step": kc["ms"] / ms if ms else None,
                     "profile": os.path.relpath(prof, ROOT) if prof else None}
     else:
-        ms_update = sum(st.ms_update for st in stats)
-        n_upd = sum(st.update_launches for st in stats)
-        upd_flops = sum(st.flops_update for st in stats)
-        kernels = {"update": {"ms": ms_update, "launches": n_upd},
-                   "pivot": {"ms": sum(st.ms_pivot for st in stats),
-                             "launches": sum(st.pivot_launches for st in stats)}}
+        tot = lambda f: sum(getattr(st, f) for st in stats)
         m, n_ = wl["m"], wl["n"]
-        if wl.get("svd_qr"):
-            kernels["precond"] = {"ms": sum(st.ms_precond for st in stats), "launches": None,
-                                  "kernel": "k_house_vec + k_house_apply + k_qr_ytx + k_gemm64 "
-                                            "(Householder QR and U = Q W, FP64)",
-                                  "flops": sum(st.flops_precond for st in stats)}
-            m = n_   # the one-sided sweeps run on R^T
+        qr = bool(wl.get("svd_qr"))
+        m_eff = n_ if qr else m   # with QR preconditioning the sweeps run on R^T
+        kernels = {"update": dict(kernel="k_gram + k_update_cols", ms=tot("ms_update"),
+                                  launches=tot("update_launches"), flops=tot("flops_update")),
+                   "pivot": dict(kernel="k_pivot / k_pivot_cluster (Gram pivots)", ms=tot("ms_pivot"),
+                                 launches=tot("pivot_launches"),
+                                 flops=tot("flops_fp64") - tot("flops_update") - tot("flops_precond"))}
+        if qr:
+            kernels["precond"] = dict(kernel="k_house_vec + k_house_apply + k_qr_ytx + k_gemm64 "
+                                             "(Householder QR and U = Q W, FP64)",
+                                      ms=tot("ms_precond"), launches=None, flops=tot("flops_precond"))
+        for c in kernels.values():
+            c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
+            c["frac"] = c["achieved"] / FP64_PEAK_TFLOPS if c["achieved"] else None
+            c.update(bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS, unit="TFLOP/s")
+        dom = max(kernels, key=lambda c: kernels[c]["ms"])
+        kc = kernels[dom]
         k = 2 * b
         P = ((n_ + b - 1) // b + 1) // 2
         npd = 2 * P * b
         # Gram (lower triangle, split-K) + column update of G and V, per step
-        alg = P * (m * k * k + 2 * m * k * k + 2 * npd * k * k)
-        avg_ms = ms_update / max(n_upd // 2, 1)
-        alg_issued = upd_flops / max(n_upd // 2, 1)
-        achieved = alg_issued / (avg_ms / 1e3) / 1e12
-        roofline = {"kernel": "k_gram + k_update_cols", "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_basis": FP64_BASIS, "alg_flops_per_launch_full": alg,
-                    "flops_per_launch_issued": alg_issued, "avg_launch_ms": avg_ms,
-                    "share_of_step": ms_update / ms if ms else None}
+        alg = P * (m_eff * k * k + 2 * m_eff * k * k + 2 * npd * k * k)
+        if kc["launches"]:
+            # the update class counts two launches per step (Gram, columns)
+            per = kc["launches"] // 2 if dom == "update" else kc["launches"]
+            avg_ms, per_launch = kc["ms"] / max(per, 1), kc["flops"] / max(per, 1)
+        else:
+            avg_ms, per_launch = kc["ms"], kc["flops"]
+        prof_name = {"update": f"svd_update_m{m_eff}_n{n_}_b{b}", "pivot": f"pivot_svd_n{n_}_b{b}",
+                     "precond": f"qr_m{m}_n{n_}"}[dom]
+        traffic, prof = profile_traffic(prof_name)
+        roofline = {"kernel": kc["kernel"], "class": dom, "bound": "alu", "achieved": kc["achieved"],
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kc["frac"], "traffic": traffic,
+                    "peak_basis": FP64_BASIS, "alg_update_flops_per_step_full": alg,
+                    "flops_per_launch_issued": per_launch, "avg_launch_ms": avg_ms,
+                    "share_of_step": kc["ms"] / ms if ms else None,
+                    "profile": os.path.relpath(prof, ROOT) if prof else None}
 
     # end to end: the same calls with host buffers, copies inside the timing
     e2e = None
@@ -937,6 +950,10 @@ def run_ncu_case(args, wl):
         print(json.dumps({"ncu_case": wl["desc"], "matrices": len(shapes)}))
         return 0
     X, _ = make_input(wl)
+    if wl.get("svd_qr"):
+        # the sweeps of the QR form run on R^T (n x n): the same step kernels
+        import numpy as np
+        X = np.asfortranarray(np.triu(np.linalg.qr(X, mode="r")).T)
     dev = torch.device("cuda", 0)
     mixed = wl.get("precision", 0) in (2, 3, 4)
     dt = torch.float32 if mixed else torch.float64

@@ -89,7 +89,9 @@ typedef struct {
                              (Sec. 3, after Algorithm 3).  0 (default) =
                              automatic: 1 for the two-sided EVD (same outer
                              sweep count, half the time at n = 4096), 30 for
-                             the one-sided SVD (a cap there costs sweeps)      */
+                             the one-sided SVD on G (a cap there costs
+                             sweeps), 2 for the SVD on R^T (svd_qr: the same
+                             sweeps with half the inner sweeps)              */
     double tol;           /* outer tolerance (default 1e-14; SVD: see gesvd)    */
     double inner_tol;     /* a scalar rotation inside a pivot solve is skipped
                              when |a_pq| <= inner_tol sqrt|a_pp| sqrt|a_qq|

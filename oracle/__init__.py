@@ -288,6 +288,7 @@ def gesvd_qr(G: np.ndarray, b: int = 16, *, transpose: bool = True, **kw):
     R = np.triu(R)
     kw = dict(kw)
     kw["want_vectors"] = True
+    kw.setdefault("inner_max_sweeps", 2)   # on R^T: the same sweeps with half the inner work
     if transpose:
         UX, s, W, st, status = gesvd(np.asfortranarray(R.T), b=b, **kw)
         return np.asfortranarray(Q @ W), s, UX, st, status

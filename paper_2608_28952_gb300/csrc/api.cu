@@ -531,7 +531,7 @@ extern "C" int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, dou
     if (p.want_vectors && ldv < n) return -7;
     int e = check_params(p);
     if (e) return e == -7 ? -8 : e;
-    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;
+    if (p.inner_max_sweeps == 0) p.inner_max_sweeps = p.svd_qr ? 2 : 30;
     jacobi_stats st;
     memset(&st, 0, sizeof(st));
     int rc = p.svd_qr ? gesvd_qr(m, n, G, ldg, sigma, V, ldv, p, &st, (cudaStream_t)stream)
