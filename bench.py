@@ -85,6 +85,15 @@ WORKLOADS = {
                             desc="one-sided block Jacobi SVD preconditioned by a reduced QR factorisation "
                                  "(blocked Householder QR in FP64, the one-sided method on R^T, U = Q W), "
                                  "16384 x 2048, b=64, sigma_i = 10^(-10 i/(n-1)), U, sigma, V"),
+    "svd16384x2048qremu": dict(kind="svd", m=16384, n=2048, b=64, seed=5, svd_qr=1, precision=5,
+                               desc="one-sided block Jacobi SVD preconditioned by a reduced QR factorisation "
+                                    "(blocked Householder QR in FP64), the sweeps on R^T with the Gram and "
+                                    "column products FP64-accurate on the bf16 tensor cores, FP64 pivots, "
+                                    "16384 x 2048, b=64, sigma_i = 10^(-10 i/(n-1)), U, sigma, V"),
+    "svd16384x2048emu": dict(kind="svd", m=16384, n=2048, b=64, seed=5, precision=5,
+                             desc="one-sided block Jacobi SVD with the Gram and column products FP64-accurate "
+                                  "on the bf16 tensor cores, FP64 pivots, 16384 x 2048, b=64, "
+                                  "sigma_i = 10^(-10 i/(n-1)), U, sigma, V"),
     "mixed4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=13,
                       refine_steps=2,
                       desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
@@ -587,19 +596,31 @@ def run_gpu(args, wl):
         m, n_ = wl["m"], wl["n"]
         qr = bool(wl.get("svd_qr"))
         m_eff = n_ if qr else m   # with QR preconditioning the sweeps run on R^T
+        emu = prec == 5 or wl.get("fp64_products", 0) == 1
         kernels = {"update": dict(kernel="k_gram + k_update_cols", ms=tot("ms_update"),
                                   launches=tot("update_launches"), flops=tot("flops_update")),
                    "pivot": dict(kernel="k_pivot / k_pivot_cluster (Gram pivots)", ms=tot("ms_pivot"),
                                  launches=tot("pivot_launches"),
-                                 flops=tot("flops_fp64") - tot("flops_update") - tot("flops_precond"))}
+                                 flops=tot("flops_fp64") - (0 if emu else tot("flops_update"))
+                                 - tot("flops_precond"))}
         if qr:
             kernels["precond"] = dict(kernel="k_house_vec + k_house_apply + k_qr_ytx + k_gemm64 "
                                              "(Householder QR and U = Q W, FP64)",
                                       ms=tot("ms_precond"), launches=None, flops=tot("flops_precond"))
         for c in kernels.values():
-            c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
-            c["frac"] = c["achieved"] / FP64_PEAK_TFLOPS if c["achieved"] else None
             c.update(bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS, unit="TFLOP/s")
+        if emu:
+            # FP64-accurate products from bf16 slices: the tensor pipe on the
+            # issued slice products, the FP64-equivalent rate beside it
+            u = kernels["update"]
+            u.update(kernel="k_emu_gram + k_emu_cols (tcgen05, FP64-accurate)", flops=36 * tot("flops_update"),
+                     bound="tensor", peak=peaks.get("bf16_tflops_sustained"),
+                     peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
+                                "flops = the 36 bf16 slice products issued",
+                     fp64_equiv_tflops=(tot("flops_update") / (u["ms"] / 1e3) / 1e12 if u["ms"] > 0 else None))
+        for c in kernels.values():
+            c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
+            c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
         dom = max(kernels, key=lambda c: kernels[c]["ms"])
         kc = kernels[dom]
         k = 2 * b
@@ -616,9 +637,12 @@ def run_gpu(args, wl):
         prof_name = {"update": f"svd_update_m{m_eff}_n{n_}_b{b}", "pivot": f"pivot_svd_n{n_}_b{b}",
                      "precond": f"qr_m{m}_n{n_}"}[dom]
         traffic, prof = profile_traffic(prof_name)
-        roofline = {"kernel": kc["kernel"], "class": dom, "bound": "alu", "achieved": kc["achieved"],
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kc["frac"], "traffic": traffic,
-                    "peak_basis": FP64_BASIS, "alg_update_flops_per_step_full": alg,
+        if emu and dom == "update":
+            prof_name = f"emu_svd_update_m{m_eff}_n{n_}_b{b}"
+            traffic, prof = profile_traffic(prof_name)
+        roofline = {"kernel": kc["kernel"], "class": dom, "bound": kc["bound"], "achieved": kc["achieved"],
+                    "peak": kc["peak"], "unit": "TFLOP/s", "frac": kc["frac"], "traffic": traffic,
+                    "peak_basis": kc["peak_basis"], "alg_update_flops_per_step_full": alg,
                     "flops_per_launch_issued": per_launch, "avg_launch_ms": avg_ms,
                     "share_of_step": kc["ms"] / ms if ms else None,
                     "profile": os.path.relpath(prof, ROOT) if prof else None}

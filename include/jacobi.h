@@ -214,6 +214,10 @@ int jacobi_syev_h(int n, double* h_A, int lda, double* h_w, double* h_Q, int ldq
  * tol_eff = max(p->tol, sqrt(m) * 2^-53): a sweep whose largest normalised
  * Gram off-diagonal |a_ij| / sqrt(a_ii a_jj) is <= tol_eff ends the
  * iteration.  p->conv is ignored.
+ * p->precision: JACOBI_PREC_FP64, or JACOBI_PREC_FP64_EMU (or
+ * p->fp64_products = 1) for the Gram blocks and the column updates formed
+ * FP64-accurately on the bf16 tensor cores; the mixed precisions return
+ * JACOBI_ERR_UNSUPPORTED.
  * With p->svd_qr = 1 (Sec. 6, "Preprocessing with QR"): G = QR by blocked
  * Householder QR (FP64), the method above on X = R^T (n x n, so tol_eff uses
  * sqrt(n)), X W = U_X Sigma, and G = (Q W) Sigma U_X^T: U = Q W (always
@@ -373,9 +377,12 @@ int jacobi_lowp_gemm(int M, int N, int K, const float* A, int lda, int transA, c
  * applied with bf16 slices).  Error below about (9 K + 64) 2^-56 2^{E_m + F_n}
  * per entry, where 2^{E_m} > max |op(A)(m, :)| and 2^{F_n} > max |B(:, n)|.
  * Column-major FP64 on the device: A is M x K (transA = 0, lda >= M) or
- * K x M (transA = 1, lda >= K), B K x N (ldb >= K), C M x N (ldc >= M);
- * K <= 256 (JACOBI_ERR_UNSUPPORTED above).  Returns 0, -k for an invalid
- * argument, JACOBI_ERR_TIMEOUT if a bounded tensor-core wait ran out.
+ * K x M (transA = 1, lda >= K), B K x N (ldb >= K), C M x N (ldc >= M).
+ * Beyond K = 256 the exact FP32 level sums are drained every 256 K values
+ * into 64-bit integer running sums (the scales then cover whole rows and
+ * columns); K <= 2^20 (JACOBI_ERR_UNSUPPORTED above).  Returns 0, -k for
+ * an invalid argument, JACOBI_ERR_ALLOC, JACOBI_ERR_TIMEOUT if a bounded
+ * tensor-core wait ran out.
  */
 int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda, int transA, const double* B,
                        int ldb, double* C, int ldc, void* stream);

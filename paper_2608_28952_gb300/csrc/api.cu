@@ -314,11 +314,14 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
         DevCounters* cnt = ws.get<DevCounters>(1);
         const int pcl = choose_pivot_cluster(k, ord.dev_per_step);
         unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        const bool emu = p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1;
+        int* err = emu ? ws.get<int>(1) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
         if (qtab && launch_quad_table(qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(dpairs, ord.dev_pairs.data(), ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s) != cudaSuccess)
+            cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s) != cudaSuccess ||
+            (err && cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess))
             return JACOBI_ERR_CUDA;
         if (launch_load_svd(m, n, np, G, ldg, Gw[0], Vw[0], cnt, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         DevCounters hc;
@@ -342,7 +345,11 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                 int c = start;
                 for (int si = 0; si < ord.S; ++si) {
                     const int nps = ord.dev_per_step, p0 = si * nps;
-                    if (launch_gram(Gw[c], m, m, dpairs + p0, nps, b, k, part, cnt, cs) != cudaSuccess) return false;
+                    EmuSvdArgs sa{Gw[c], Gw[c ^ 1], m, m, Vw[c], Vw[c ^ 1], np, np, dpairs + p0, nps, b, k,
+                                  Vb, rot, part, npanels, gram_panel_rows(), err, cnt};
+                    if ((emu ? launch_emu_gram(sa, cs)
+                             : launch_gram(Gw[c], m, m, dpairs + p0, nps, b, k, part, cnt, cs)) != cudaSuccess)
+                        return false;
                     if (cudaEventRecordWithFlags(pe.ev[3 * si + 1], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     PivotArgs pa{};
                     pa.ld = np;
@@ -381,7 +388,7 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                     ca.Vh = Vb;
                     ca.rot = rot;
                     ca.cnt = cnt;
-                    if (launch_update_cols(ca, cs) != cudaSuccess) return false;
+                    if ((emu ? launch_emu_cols(sa, cs) : launch_update_cols(ca, cs)) != cudaSuccess) return false;
                     if (cudaEventRecordWithFlags(pe.ev[3 * si + 3], cs, cudaEventRecordExternal) != cudaSuccess) return false;
                     c ^= 1;
                 }
@@ -425,9 +432,12 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                                 vec ? V : nullptr, ldv, norms, rank, s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
         st->launches += 4;  // load, column norms, rank, finalise
+        int h_err = 0;
         if (cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            (err && cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
+        if (h_err) return JACOBI_ERR_TIMEOUT;
         fill_counters(st, hc);
     }
     st->ms_total = timer.stop();
@@ -531,6 +541,7 @@ extern "C" int jacobi_gesvd(int m, int n, double* G, int ldg, double* sigma, dou
     if (p.want_vectors && ldv < n) return -7;
     int e = check_params(p);
     if (e) return e == -7 ? -8 : e;
+    if (p.precision != JACOBI_PREC_FP64 && p.precision != JACOBI_PREC_FP64_EMU) return JACOBI_ERR_UNSUPPORTED;
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = p.svd_qr ? 2 : 30;
     jacobi_stats st;
     memset(&st, 0, sizeof(st));
@@ -702,6 +713,7 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
     if (pin) p = *pin; else jacobi_params_default(&p);
     int e = check_params(p);
     if (e) return e == -7 ? -7 : e;
+    if (p.precision != JACOBI_PREC_FP64 && p.precision != JACOBI_PREC_FP64_EMU) return JACOBI_ERR_UNSUPPORTED;
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 30;
     if (m < 1) return -1;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2 || np > m) return -2;
@@ -732,7 +744,10 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         DevCounters* cnt = ws.get<DevCounters>(1);
         const int pcl = choose_pivot_cluster(k, nps);
         unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        const bool emu = p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1;
+        int* err = emu ? ws.get<int>(1) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (err && cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (qtab && launch_quad_table(qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (cudaMemcpyAsync(dpairs, ord.dev_pairs.data(), ord.dev_pairs.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -744,7 +759,10 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         if (V && cudaMemcpy2DAsync(Vw[0], (size_t)np * 8, V, (size_t)ldv * 8, (size_t)np * 8, np,
                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
-        if (launch_gram(Gw[0], m, m, dpairs + p0, nps, b, k, part, cnt, s) != cudaSuccess)
+        EmuSvdArgs sa{Gw[0], Gw[1], m, m, Vw[0], Vw[1], np, np, dpairs + p0, nps, b, k,
+                      Vb, rot, part, npanels, gram_panel_rows(), err, cnt};
+        if ((emu ? launch_emu_gram(sa, s) : launch_gram(Gw[0], m, m, dpairs + p0, nps, b, k, part, cnt, s)) !=
+            cudaSuccess)
             return JACOBI_ERR_CUDA;
         PivotArgs pa{};
         pa.ld = np;
@@ -782,7 +800,7 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         ca.Vh = Vb;
         ca.rot = rot;
         ca.cnt = cnt;
-        if (launch_update_cols(ca, s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        if ((emu ? launch_emu_cols(sa, s) : launch_update_cols(ca, s)) != cudaSuccess) return JACOBI_ERR_CUDA;
         // columns of pairs outside this step are unchanged: copy them through
         if (cudaMemcpy2DAsync(G, (size_t)ldg * 8, Gw[0], (size_t)m * 8, (size_t)m * 8, np,
                               cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -802,9 +820,12 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
             }
         }
         double h;
+        int h_err = 0;
         if (cudaMemcpyAsync(&h, smax, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            (err && cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return JACOBI_ERR_CUDA;
+        if (h_err) return JACOBI_ERR_TIMEOUT;
         if (relmax_out) *relmax_out = h;
     }
     return 0;

@@ -199,6 +199,21 @@ struct EmuUpdArgs {
     int* err;       // set on a timed-out tensor-core wait
 };
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s);
+// The one-sided step's products FP64-accurate on the tensor cores: Gram
+// partials per pair and row panel (the layout the pivot kernel reads), and
+// the column update of G and V.
+struct EmuSvdArgs {
+    const double* Gin; double* Gout; int ldg; int m;
+    const double* Vin; double* Vout; int ldv; int vrows;
+    const int2* pairs; int npairs;
+    int b, k;
+    const double* Vh; const int* rot;
+    double* part; int npanels; int panel_rows;
+    int* err;
+    DevCounters* cnt;
+};
+cudaError_t launch_emu_gram(const EmuSvdArgs& a, cudaStream_t s);
+cudaError_t launch_emu_cols(const EmuSvdArgs& a, cudaStream_t s);
 size_t emu_update_tbuf_doubles(int npairs, int k);
 cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
                              double* result, cudaStream_t s);

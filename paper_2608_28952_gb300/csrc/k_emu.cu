@@ -25,7 +25,9 @@
 // columns); K is streamed in chunks of 32 through two 96 KB stages (8 slices
 // of A, 128 x 32, and of B, 64 x 32, in the canonical no-swizzle K-major
 // layout); one thread issues the 72 MMAs of a chunk (2 K steps x 36 slice
-// products) and commits them to the stage's mbarrier (bounded waits).
+// products) and commits them to the stage's mbarrier (bounded waits).  For
+// K > 256 the accumulators are drained into 64-bit integer running sums
+// every 256 K values (emu_tile<true>).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -607,6 +609,132 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
     }
 }
 
+// ---------------------------------------------------------------- one-sided step (Algorithm 6)
+// Gram partials: item (pair e, row panel r, tile mt, nt) of
+// part[e][r] = G(rows_r, P)^T G(rows_r, P) (k x k), K = the panel's rows
+// (<= 512: two exact accumulations); tiles wholly above the diagonal are
+// skipped (the pivot reads the lower triangle).
+__global__ void __launch_bounds__(E_T, 1) k_emu_gram(EmuSvdArgs a, int nmt, int nnt)
+{
+    __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
+    const int k = a.k, b = a.b;
+    int item = blockIdx.x;
+    const int nt = item % nnt;
+    item /= nnt;
+    const int mt = item % nmt;
+    item /= nmt;
+    const int r = item % a.npanels, e = item / a.npanels;
+    const int m0 = mt * EM, n0 = nt * EN;
+    if (m0 + EM - 1 < n0) return;
+    int I, J;
+    eentry(a.pairs, e, I, J);
+    const int r0 = r * a.panel_rows, K = min(a.panel_rows, a.m - r0);
+    const double* G = a.Gin;
+    const size_t ld = (size_t)a.ldg;
+    double* out = a.part + ((size_t)e * a.npanels + r) * k * k;
+    auto fa = [&](int mm, int kk) -> double {
+        return m0 + mm < k && kk < K ? G[(r0 + kk) + ld * emap(I, J, b, m0 + mm)] : 0.0;
+    };
+    auto fb = [&](int kk, int nn) -> double {
+        return n0 + nn < k && kk < K ? G[(r0 + kk) + ld * emap(I, J, b, n0 + nn)] : 0.0;
+    };
+    line_exponents(EM, K, fa, s_eA, s_scr);
+    line_exponents(EN, K, [&](int nn, int kk) { return fb(kk, nn); }, s_eB, s_scr);
+    emu_tile<true>(K, fa, fb, s_eA, s_eB,
+                   [&](int mm, int nn, double v) {
+                       if (m0 + mm < k && n0 + nn < k) out[(m0 + mm) + (size_t)k * (n0 + nn)] = v;
+                   },
+                   a.err);
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.cnt->flops_update, 2ull * EM * EN * K);
+        atomicAdd(&a.cnt->flops_lowp, 72ull * EM * EN * K);
+    }
+}
+
+// x 2^-c for a power-of-two shift by integer operations on the exponent
+// field (exact; the FP64 path only where the result leaves the normal range).
+__device__ __forceinline__ double pow2_shift(double x, int c)
+{
+    const long long bits = __double_as_longlong(x);
+    const int ea = (int)((bits >> 52) & 0x7FF);
+    if (ea == 0 || c == 0) return ea == 0 && c != 0 ? ldexp(x, -c) : x;
+    if (ea - c >= 1 && ea - c <= 2046) return __longlong_as_double(bits - (long long)c * (1ll << 52));
+    return ldexp(x, -c);
+}
+
+// Column update: items [0, n_g): tile (rt, nt) of G'(:, P) = G(:, P) V_P;
+// beyond: the same for V.  V^T (stored after V) gives coalesced loads.
+// The columns of G(:, P) can differ by many orders of magnitude (the
+// singular values of the graded inputs span ten decades); a row scale taken
+// across them would leave a small column with errors relative to the large
+// ones.  So G(:, P) = (G(:, P) 2^-c) (2^c V_P): column kk of G is scaled by
+// 2^-c_kk, c_kk from the step's Gram diagonal (~ its norm), and row kk of V_P
+// by 2^c_kk (both exact), and the row / column scales of the product are
+// taken on the balanced operands, as the FP64 rounding of the sum would.
+__global__ void __launch_bounds__(E_T, 1) k_emu_cols(EmuSvdArgs a, int n_g)
+{
+    __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
+    __shared__ int s_cs[256];   // column shifts (k <= 256)
+    const int k = a.k, b = a.b, nnt = (k + EN - 1) / EN;
+    int item = blockIdx.x;
+    const double* Min = a.Gin;
+    double* Mout = a.Gout;
+    size_t ld = (size_t)a.ldg;
+    int rows = a.m;
+    if (item >= n_g) {
+        item -= n_g;
+        Min = a.Vin;
+        Mout = a.Vout;
+        ld = (size_t)a.ldv;
+        rows = a.vrows;
+    }
+    const int nrt = (rows + EM - 1) / EM;
+    const int e = item / (nrt * nnt), rem = item % (nrt * nnt), rt = rem / nnt, nt = rem % nnt;
+    int I, J;
+    eentry(a.pairs, e, I, J);
+    const int r0 = rt * EM, n0 = nt * EN;
+    if (a.rot[e] == 0) {
+        for (int idx = threadIdx.x; idx < EM * EN; idx += E_T) {
+            const int mm = r0 + idx % EM, j = n0 + idx / EM;
+            if (mm < rows && j < k) {
+                const size_t o = mm + ld * emap(I, J, b, j);
+                Mout[o] = Min[o];
+            }
+        }
+        return;
+    }
+    const double* Vt = a.Vh + (size_t)e * 2 * k * k + (size_t)k * k;
+    const bool gitem = blockIdx.x < (unsigned)n_g;
+    for (int kk = threadIdx.x; kk < k; kk += E_T) {
+        int c = 0;
+        if (gitem) {
+            double d = 0.0;   // ||G(:, kk)||^2, the Gram diagonal summed over the panels
+            for (int r = 0; r < a.npanels; ++r) d += a.part[((size_t)e * a.npanels + r) * k * k + (size_t)kk * (k + 1)];
+            const int ed = exp2_of(d);
+            c = ed <= -1100 ? 0 : (ed >> 1);
+        }
+        s_cs[kk] = c;
+    }
+    __syncthreads();
+    auto fa = [&](int mm, int kk) -> double {
+        return r0 + mm < rows && kk < k ? pow2_shift(Min[(r0 + mm) + ld * emap(I, J, b, kk)], s_cs[kk]) : 0.0;
+    };
+    auto fb = [&](int kk, int nn) -> double {
+        return n0 + nn < k && kk < k ? pow2_shift(Vt[(n0 + nn) + (size_t)k * kk], -s_cs[kk]) : 0.0;
+    };
+    line_exponents(EM, k, fa, s_eA, s_scr);
+    line_exponents(EN, k, [&](int nn, int kk) { return fb(kk, nn); }, s_eB, s_scr);
+    emu_tile<false>(k, fa, fb, s_eA, s_eB,
+                    [&](int mm, int nn, double v) {
+                        if (r0 + mm < rows && n0 + nn < k) Mout[(r0 + mm) + ld * emap(I, J, b, n0 + nn)] = v;
+                    },
+                    a.err);
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.cnt->flops_update, 2ull * EM * EN * k);
+        atomicAdd(&a.cnt->flops_lowp, 72ull * EM * EN * k);
+    }
+}
+
 }  // namespace
 
 size_t emu_update_tbuf_doubles(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
@@ -625,6 +753,29 @@ cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
     if (n_sand + n_q > 0) k_emu_upd1<<<n_sand + n_q, E_T, E_SMEM, s>>>(a, n_sand);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n_sand > 0) k_emu_upd2<<<n_sand, E_T, E_SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_gram(const EmuSvdArgs& a, cudaStream_t s)
+{
+    const int nmt = (a.k + EM - 1) / EM, nnt = (a.k + EN - 1) / EN;
+    const long long items = (long long)a.npairs * a.npanels * nmt * nnt;
+    if (items <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    k_emu_gram<<<(unsigned)items, E_T, E_SMEM, s>>>(a, nmt, nnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emu_cols(const EmuSvdArgs& a, cudaStream_t s)
+{
+    const int nnt = (a.k + EN - 1) / EN;
+    const int n_g = a.npairs * ((a.m + EM - 1) / EM) * nnt;
+    const int n_v = a.Vin ? a.npairs * ((a.vrows + EM - 1) / EM) * nnt : 0;
+    if (n_g + n_v == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    k_emu_cols<<<n_g + n_v, E_T, E_SMEM, s>>>(a, n_g);
     return cudaGetLastError();
 }
 

@@ -322,15 +322,16 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
 }
 
 // Cluster size for a step with npairs pairs on an sms-SM GPU: the largest
-// power of two C <= 8 with npairs * C <= sms whose per-CTA share fits the
-// shared-memory limit, or 1 (use the one-CTA kernel).  Small pivots gain
-// nothing from a cluster (two cluster barriers per round cost more than the
-// round's work): k <= 32 uses one CTA, k <= 64 at most 4 (measured on GB300:
-// n = 256, b = 16: 32 ms with one CTA, 37 ms with clusters of 4; n = 1024,
-// b = 32: best with 4).
+// power of two C <= cmax with npairs * C <= sms whose per-CTA share fits the
+// shared-memory limit, or 1 (use the one-CTA kernel).  A round's FP64 work
+// per CTA shrinks with C while its cluster barrier does not, so small pivots
+// gain nothing from large clusters: k <= 32 uses one CTA, k <= 128 at most 4
+// (measured on GB300: n = 256, b = 16: 32 ms with one CTA, 37 ms with
+// clusters of 4; the 16 Gram pivots (k = 128) of a step of the 2048-column
+// SVD: 524 ms per solve with C = 4, 592 ms with 8, 758 ms with 2).
 int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
 {
-    const int cmax = k <= 32 ? 1 : (k <= 64 ? 4 : PC_MAXC8);
+    const int cmax = k <= 32 ? 1 : (k <= 128 ? 4 : PC_MAXC8);
     int best = 1;
     for (int C = 2; C <= cmax; C *= 2) {
         if (k % C || k / C < 8 || npairs * C > sms) break;

@@ -167,3 +167,45 @@ def test_mixed_with_emulated_fp64_products_meets_the_fp64_gates(jg, prec):
     w, Q, _, st = jg.syev(A, b=64, precision=prec, fp64_products=1)
     assert st.status == 0 and st.sweeps_lowp > 0
     _check(A, w.cpu().numpy(), Q.cpu().numpy(), np.sort(lam))
+
+
+# ------------------------------------------------------------------ the one-sided method with emulated products
+@pytest.mark.parametrize("m,np_,b", [(300, 64, 8), (1100, 96, 16), (700, 256, 64), (40, 12, 3)])
+def test_emu_svd_step_matches_oracle(jg, m, np_, b):
+    """One one-sided step (Gram partials over 512-row panels and the column
+    update on the tensor cores, FP64 pivots) gives the oracle's FP64 step to
+    the DFMA path's tolerances."""
+    import torch
+    G0 = gen.tall_gaussian(m, np_, 5500 + m, dtype=np.float64)
+    tol = oracle.svd_tol(m)
+    tab = oracle.ordering(0, np_ // b)
+    for s in (0, len(tab) - 1):
+        G_or, V_or, r_or = oracle.gesvd_step(G0, np.eye(np_), b, tab[s], tol_rel=tol, inner_max=30)
+        Gd = jg.colmajor(G0, device="cuda", dtype=torch.float64)
+        Vd = jg.colmajor(np.eye(np_), device="cuda", dtype=torch.float64)
+        rc, r = jg.jacobi_gesvd_step(Gd, Vd, s, jg.params(b=b, tol=1e-15, precision=EMU))
+        assert rc == 0 and abs(r - r_or) <= 1e-13
+        assert np.abs(Gd.cpu().numpy() - G_or).max() <= 1e-12 * np.abs(G0).max()
+        assert np.abs(Vd.cpu().numpy() - V_or).max() <= 1e-12
+
+
+@pytest.mark.parametrize("m,n,b,qr", [(500, 96, 16, 0), (1030, 130, 32, 1), (2048, 256, 64, 0), (2048, 256, 64, 1)])
+def test_emu_svd_meets_the_fp64_gates(jg, m, n, b, qr):
+    G, sig = gen.svd_known(m, n, seed=5600 + n, decades=10.0)
+    U, s, V, st = jg.gesvd(G, b=b, precision=EMU, svd_qr=qr)
+    U, s, V = U.cpu().numpy(), s.cpu().numpy(), V.cpu().numpy()
+    assert st.status == 0
+    assert np.abs(s - sig).max() <= 1e-13 * sig[0]
+    big = sig >= 1e-3 * sig[0]
+    assert (np.abs(s - sig)[big] / sig[big]).max() <= 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G) * np.sqrt(n)
+
+
+def test_svd_rejects_the_mixed_precisions(jg):
+    import torch
+    G = gen.tall_gaussian(64, 16, 5700, dtype=np.float64)
+    s = torch.empty(16, dtype=torch.float64, device="cuda")
+    assert jg.jacobi_gesvd(jg.colmajor(G, device="cuda", dtype=torch.float64), s, None,
+                           jg.params(b=4, want_vectors=0, precision=2))[0] == jg.ERR_UNSUPPORTED
