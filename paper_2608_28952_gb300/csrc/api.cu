@@ -466,7 +466,16 @@ static int gesvd_qr(int m, int n, double* G, int ldg, double* sigma, double* V, 
         double* YT = ws.get<double>((size_t)m * nb);
         double* X = ws.get<double>((size_t)n * n);
         double* Wv = ws.get<double>((size_t)n * n);
+        const bool emu = p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1;
+        int* xexp = emu ? ws.get<int>((size_t)m + n + 1) : nullptr;   // line exponents + the timeout word
         if (ws.failed) return JACOBI_ERR_ALLOC;
+        if (xexp && cudaMemsetAsync(xexp + m + n, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
+        auto update = [&](int j0, int nbp, const double* Tp, const double* Ttp, int trans, double* Xm, int ncol) {
+            if (emu)
+                return launch_house_update_emu(m, j0, nbp, Y, m, Tp, Ttp, trans, Xm, ldg, ncol, Wpart, W, YT, xexp,
+                                               xexp + m, xexp + m + n, s);
+            return launch_house_update(m, j0, nbp, Y, m, Tp, Ttp, trans, Xm, ldg, ncol, Wpart, W, YT, s);
+        };
         cudaEvent_t ev[4];
         for (auto& e : ev) cudaEventCreate(&e);
         auto destroy = [&] {
@@ -479,8 +488,7 @@ static int gesvd_qr(int m, int n, double* G, int ldg, double* sigma, double* V, 
             double* Tp = T + (size_t)pi * nb * nb;
             double* Ttp = Tt + (size_t)pi * nb * nb;
             ok = launch_house_panel(m, G, ldg, j0, nbp, Y, m, tau, S, Tp, Ttp, s) == cudaSuccess &&
-                 launch_house_update(m, j0, nbp, Y, m, Tp, Ttp, 1, G + (size_t)ldg * (j0 + nbp), ldg, nc, Wpart, W,
-                                     YT, s) == cudaSuccess;
+                 update(j0, nbp, Tp, Ttp, 1, G + (size_t)ldg * (j0 + nbp), nc) == cudaSuccess;
             fl += 5.0 * rows * nbp * nbp + 4.0 * rows * nbp * nc;   // panel 3 r nb^2, Y T^T 2 r nb^2, update
             st->launches += 2 * nbp + 1 + (nc > 0 ? 4 : 0);
         }
@@ -504,8 +512,7 @@ static int gesvd_qr(int m, int n, double* G, int ldg, double* sigma, double* V, 
         ok = ok && launch_qr_fill(m, n, Wv, G, ldg, s) == cudaSuccess;
         for (int pi = npan - 1; ok && pi >= 0; --pi) {
             const int j0 = pi * nb, nbp = std::min(nb, n - j0), rows = m - j0;
-            ok = launch_house_update(m, j0, nbp, Y, m, T + (size_t)pi * nb * nb, Tt + (size_t)pi * nb * nb, 0, G,
-                                     ldg, n, Wpart, W, YT, s) == cudaSuccess;
+            ok = update(j0, nbp, T + (size_t)pi * nb * nb, Tt + (size_t)pi * nb * nb, 0, G, n) == cudaSuccess;
             fl += 2.0 * rows * nbp * nbp + 4.0 * rows * nbp * n;
             st->launches += 4;
         }
@@ -513,6 +520,15 @@ static int gesvd_qr(int m, int n, double* G, int ldg, double* sigma, double* V, 
         if (!ok) {
             destroy();
             return JACOBI_ERR_CUDA;
+        }
+        int h_err = 0;
+        if (xexp && cudaMemcpy(&h_err, xexp + m + n, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            destroy();
+            return JACOBI_ERR_CUDA;
+        }
+        if (h_err) {
+            destroy();
+            return JACOBI_ERR_TIMEOUT;
         }
         float t01 = 0.f, t23 = 0.f;
         cudaEventElapsedTime(&t01, ev[0], ev[1]);

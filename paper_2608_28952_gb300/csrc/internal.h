@@ -151,6 +151,10 @@ cudaError_t launch_house_panel(int m, double* A, int lda, int j0, int nbp, doubl
 cudaError_t launch_house_update(int m, int j0, int nbp, const double* Y, int ldy, const double* T,
                                 const double* Tt, int trans, double* X, int ldx, int ncol, double* Wpart,
                                 double* W, double* YT, cudaStream_t s);
+// The same with FP64-accurate tensor-core products (xA, xB: m + n ints; err: timeout word).
+cudaError_t launch_house_update_emu(int m, int j0, int nbp, const double* Y, int ldy, const double* T,
+                                    const double* Tt, int trans, double* X, int ldx, int ncol, double* part,
+                                    double* W, double* YT, int* xA, int* xB, int* err, cudaStream_t s);
 cudaError_t launch_qr_rt(int n, const double* A, int lda, double* X, cudaStream_t s);
 cudaError_t launch_qr_fill(int m, int n, const double* W, double* G, int ldg, cudaStream_t s);
 cudaError_t launch_rotation_params(int count, const double* app, const double* aqq, const double* apq, double tol,
@@ -191,6 +195,11 @@ cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int t
 cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
                                 int accumulate, double* C, int ldc, int lower, int* xA, int* xB, int* err,
                                 cudaStream_t s);
+// W (N x M, ld ldw) = (op(A) B)^T with K split into chunks of kchunk: the
+// partials (part: ceil(K / kchunk) x M x N doubles) summed in a fixed order.
+cudaError_t launch_emu_gemm_tsplit(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                   double* W, int ldw, int kchunk, double* part, int* xA, int* xB, int* err,
+                                   cudaStream_t s);
 // The step update of the FP64 path with every product FP64-accurate on the
 // tensor cores (stage 1 T = A_{P1P2} V2 and Q V_P, stage 2 V1^T T mirrored).
 struct EmuUpdArgs {

@@ -399,15 +399,25 @@ __global__ void k_emu_line_exps(int lines, int K, const double* __restrict__ X, 
 
 // C = op(A) B (+ C when accumulate) for any K, FP64-accurate; tiles wholly
 // above the diagonal are skipped when lower (the caller mirrors).
+// With kchunk > 0 (split K): block z takes K values [z kchunk, (z+1) kchunk)
+// and writes its M x N partial to C + z M N (ld M); the caller sums them.
 __global__ void __launch_bounds__(E_T, 1) k_emu_gemm_big(int M, int N, int K, const double* __restrict__ A, int lda,
                                                          int transA, const double* __restrict__ B, int ldb,
                                                          int accumulate, double* __restrict__ C, int ldc, int lower,
                                                          const int* __restrict__ xA, const int* __restrict__ xB,
-                                                         int* err)
+                                                         int* err, int kchunk)
 {
     __shared__ int s_eA[EM], s_eB[EN];
     const int m0 = blockIdx.x * EM, n0 = blockIdx.y * EN;
     if (lower && m0 + EM - 1 < n0) return;
+    int kb = 0;
+    if (kchunk > 0) {   // this block's K range and partial
+        kb = blockIdx.z * kchunk;
+        K = min(K - kb, kchunk);
+        C += (size_t)blockIdx.z * M * N;
+        ldc = M;
+        accumulate = 0;
+    }
     for (int i = threadIdx.x; i < EM + EN; i += E_T) {
         const int v = i < EM ? (m0 + i < M ? xA[m0 + i] : 0) : (n0 + i - EM < N ? xB[n0 + i - EM] : 0);
         const int e = v == 0 ? 0 : v - 2048 + 1;
@@ -418,11 +428,11 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_gemm_big(int M, int N, int K, co
     auto fa = [&](int m, int k) -> double {
         const int mm = m0 + m;
         if (mm >= M || k >= K) return 0.0;
-        return transA ? A[k + (size_t)lda * mm] : A[mm + (size_t)lda * k];
+        return transA ? A[kb + k + (size_t)lda * mm] : A[mm + (size_t)lda * (kb + k)];
     };
     auto fb = [&](int k, int n) -> double {
         const int nn = n0 + n;
-        return (nn < N && k < K) ? B[k + (size_t)ldb * nn] : 0.0;
+        return (nn < N && k < K) ? B[kb + k + (size_t)ldb * nn] : 0.0;
     };
     emu_tile<true>(K, fa, fb, s_eA, s_eB,
                    [&](int m, int n, double v) {
@@ -463,7 +473,44 @@ cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, i
     k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
     dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
     k_emu_gemm_big<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, accumulate, C, ldc, lower, xA, xB,
-                                             err);
+                                             err, 0);
+    return cudaGetLastError();
+}
+
+namespace {
+// W(a, c) = sum_z part_z(c, a), fixed order: the transposed sum of the
+// split-K partials (each M x N, ld M) into W (N x M, ld ldw).
+__global__ void k_emu_sum_t(int M, int N, int nsplit, const double* __restrict__ part, double* __restrict__ W, int ldw)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)M * N) return;
+    const int c = (int)(i % M), a = (int)(i / M);
+    double v = 0.0;
+    for (int z = 0; z < nsplit; ++z) v += part[(size_t)z * M * N + i];
+    W[a + (size_t)ldw * c] = v;
+}
+}  // namespace
+
+cudaError_t launch_emu_gemm_tsplit(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                   double* W, int ldw, int kchunk, double* part, int* xA, int* xB, int* err,
+                                   cudaStream_t s)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xA, 0, sizeof(int) * M, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(xB, 0, sizeof(int) * N, s)) != cudaSuccess)
+        return e;
+    if (transA)
+        k_emu_line_exps<<<dim3((M + 7) / 8, (K + 255) / 256), 256, 0, s>>>(M, K, A, lda, 0, xA);
+    else
+        k_emu_line_exps<<<dim3((M + 255) / 256, (K + 63) / 64), 256, 0, s>>>(M, K, A, lda, 1, xA);
+    k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
+    const int nsplit = (K + kchunk - 1) / kchunk;
+    dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN, nsplit);
+    k_emu_gemm_big<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, 0, part, M, 0, xA, xB, err, kchunk);
+    const long long total = (long long)M * N;
+    k_emu_sum_t<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, nsplit, part, W, ldw);
     return cudaGetLastError();
 }
 

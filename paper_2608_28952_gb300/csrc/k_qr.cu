@@ -243,6 +243,27 @@ cudaError_t launch_house_update(int m, int j0, int nbp, const double* Y, int ldy
     return launch_gemm64(rows, ncol, nbp, -1.0, YT, m, 0, W, QR_NB, 1.0, Xp, ldx, s);
 }
 
+// The same update with FP64-accurate products on the tensor cores:
+// W = (X^T Y_p)^T split over K (rows), then X += (-Y_p M) W.
+cudaError_t launch_house_update_emu(int m, int j0, int nbp, const double* Y, int ldy, const double* T,
+                                    const double* Tt, int trans, double* X, int ldx, int ncol, double* part,
+                                    double* W, double* YT, int* xA, int* xB, int* err, cudaStream_t s)
+{
+    if (ncol <= 0) return cudaSuccess;
+    const int rows = m - j0;
+    const double* Yp = Y + j0 + (size_t)ldy * j0;
+    double* Xp = X + j0;
+    const int tiles = (ncol + 127) / 128, want = (3 * 152 + tiles - 1) / tiles;
+    int kchunk = (rows + want - 1) / want;
+    kchunk = ((kchunk + 255) / 256) * 256;
+    if (kchunk < QR_KR) kchunk = QR_KR;   // the partial buffer holds ceil(rows / QR_KR) splits
+    cudaError_t e = launch_emu_gemm_tsplit(ncol, nbp, rows, Xp, ldx, 1, Yp, ldy, W, QR_NB, kchunk, part, xA, xB, err, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_gemm64(rows, nbp, nbp, -1.0, Yp, ldy, 0, trans ? Tt : T, QR_NB, 0.0, YT, m, s)) != cudaSuccess)
+        return e;
+    return launch_emu_gemm_big(rows, ncol, nbp, YT, m, 0, W, QR_NB, 1, Xp, ldx, 0, xA, xB, err, s);
+}
+
 cudaError_t launch_qr_rt(int n, const double* A, int lda, double* X, cudaStream_t s)
 {
     k_qr_rt<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, s>>>(n, A, lda, X);
