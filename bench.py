@@ -71,6 +71,10 @@ WORKLOADS = {
                        desc="two-sided block Jacobi EVD with FP64-accurate update products on the bf16 "
                             "tensor cores (eight 7-bit slices per operand), FP64 pivots and off-norm, "
                             "n=4096, b=64, round-robin, eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
+    "evd4096qrcp": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, ref_sweeps=13, pivot_order=2,
+                        desc="plain FP64 two-sided block Jacobi EVD with the pivoting step of Sec. 2.1 (QRCP "
+                             "of the leading rows of each pivot's eigenvectors), n=4096, b=64, round-robin, "
+                             "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
     "evd256": dict(kind="evd", n=256, b=16, spectrum="uniform", seed=1,
                    desc="plain FP64 two-sided block Jacobi EVD, n=256, b=16, round-robin, "
                         "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
@@ -502,7 +506,7 @@ def run_gpu(args, wl):
     X, ref = make_input(wl)
     b = wl["b"]
     prec = wl.get("precision", 0)
-    extra = {k: wl[k] for k in ("refine_steps", "fp64_products", "svd_qr") if k in wl}
+    extra = {k: wl[k] for k in ("refine_steps", "fp64_products", "svd_qr", "pivot_order") if k in wl}
     p = jg.params(b=b, inner_max_sweeps=args.inner_max_sweeps, precision=prec, **extra)
     Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
     Wd = torch.empty_like(Xd.t()).t()  # column-major work copy
@@ -690,6 +694,7 @@ def run_gpu(args, wl):
                            "n": wl["n"], **({"m": wl["m"]} if "m" in wl else {}),
                            "seed": wl["seed"], "parallelism": f"replicas x{world}",
                            **({"svd_qr": True} if wl.get("svd_qr") else {}),
+                           **({"pivot_order": wl["pivot_order"]} if "pivot_order" in wl else {}),
                            **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3",
                                              5: "fp64 emulated products"}[prec],
                                "refine_steps": wl.get("refine_steps")} if prec else {}),

@@ -109,7 +109,11 @@ typedef struct {
                              0 = eigenpairs as solved (the pseudocode of
                              Algorithms 1, 2 and 6); 1 = sorted by descending
                              eigenvalue over the pivot's non-padding rows
-                             (default; far fewer sweeps on graded spectra)    */
+                             (default; far fewer sweeps on graded spectra);
+                             2 = the order column-pivoted QR picks on the
+                             leading rows of Qhat (the pivoting step of
+                             Sec. 2.1, the condition of Drmac's convergence
+                             proof)                                            */
     int fp64_products;    /* how the FP64 sweeps form their update products:
                              0 = FP64 FMA (default); 1 = FP64-accurate products
                              on the bf16 tensor cores as in

@@ -110,6 +110,8 @@ def lib():
         L.oracle_gesvd_step.restype = C.c_double
         L.oracle_split_bf16.argtypes = [C.c_int, _FP, _FP, _FP]
         L.oracle_split_bf16.restype = None
+        L.oracle_qrcp_perm.argtypes = [C.c_int, C.c_int, _DP, _IP]
+        L.oracle_qrcp_perm.restype = C.c_int
         _LIB = L
     return _LIB
 
@@ -186,10 +188,24 @@ def _params(b, ordering, max_sweeps, inner_max_sweeps, conv, tol, inner_tol, wan
                    int(want_vectors), threads, pivot_order)
 
 
+def qrcp_perm(X: np.ndarray) -> np.ndarray:
+    """The column order chosen by column-pivoted QR of X (Businger-Golub,
+    norms recomputed at every step, ties to the smaller index): the rule of
+    the pivoting step (Sec. 2.1) applied to the leading rows of Vhat."""
+    X = _f64F(X)
+    r, c = X.shape
+    perm = np.zeros(c, dtype=np.int32)
+    if lib().oracle_qrcp_perm(r, c, _dp(X), perm.ctypes.data_as(_IP)) != 0:
+        raise ValueError("oracle qrcp: bad argument")
+    return perm
+
+
 def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U64,
               inner_max=1, pivot_order=1):
     """One parallel step (Algorithm 2 structure) on a full np x np matrix;
-    pivot_order 1 sorts each pivot's eigenpairs descending (Qhat <- Qhat P).
+    pivot_order 1 sorts each pivot's eigenpairs descending, 2 orders them by
+    QRCP of Vhat's leading rows (the pivoting step of Sec. 2.1); either way
+    Qhat <- Qhat P.
 
     Returns (A', Q', rotations)."""
     A = _f64F(A)

@@ -95,7 +95,7 @@ typedef struct {
     double inner_tol;     /* relative threshold of one scalar rotation            */
     int want_vectors;     /* accumulate Q (EVD) / V (SVD)                         */
     int threads;          /* OpenMP threads (0 = runtime default)                 */
-    int pivot_order;      /* 0: eigenpairs as solved; 1: sorted descending        */
+    int pivot_order;      /* 0: as solved; 1: sorted descending; 2: QRCP (Sec. 2.1) */
 } orc_params;
 
 typedef struct {
@@ -452,6 +452,105 @@ static void sort_pivot_desc(int k, double *Ah, double *V, double *tmp, int *idx,
     memcpy(V, B, sizeof(double) * (size_t)k * k);
 }
 
+/* Column-pivoted QR (Businger-Golub) of the r x c matrix M (column-major, ld
+ * r, overwritten): at step t the remaining column of largest norm over rows
+ * t.. (recomputed, not downdated; ties to the smaller index) is swapped to
+ * position t, and a Householder reflection clears it below row t.  perm
+ * (c entries, in: identity) records the column order. */
+static void qrcp_steps(int r, int c, double *M, int *perm)
+{
+    double *v = (double *)malloc(sizeof(double) * (size_t)(r > 0 ? r : 1));
+    int steps = r < c ? r : c;
+    for (int t = 0; t < steps; t++) {
+        int best = t;
+        double bn = -1.0;
+        for (int j = t; j < c; j++) {
+            double s = 0.0;
+            for (int i = t; i < r; i++) s += M[i + (size_t)r * j] * M[i + (size_t)r * j];
+            if (s > bn) { bn = s; best = j; }
+        }
+        if (best != t) {
+            int ti = perm[t]; perm[t] = perm[best]; perm[best] = ti;
+            for (int i = 0; i < r; i++) {
+                double tv = M[i + (size_t)r * t];
+                M[i + (size_t)r * t] = M[i + (size_t)r * best];
+                M[i + (size_t)r * best] = tv;
+            }
+        }
+        double alpha = M[t + (size_t)r * t], xn = 0.0;
+        for (int i = t + 1; i < r; i++) xn += M[i + (size_t)r * t] * M[i + (size_t)r * t];
+        xn = sqrt(xn);
+        if (xn == 0.0) continue; /* H = I */
+        double beta = -copysign(hypot(alpha, xn), alpha);
+        double tau = (beta - alpha) / beta, sc = 1.0 / (alpha - beta);
+        v[t] = 1.0;
+        for (int i = t + 1; i < r; i++) v[i] = M[i + (size_t)r * t] * sc;
+        for (int j = t + 1; j < c; j++) {
+            double w = 0.0;
+            for (int i = t; i < r; i++) w += v[i] * M[i + (size_t)r * j];
+            w *= tau;
+            for (int i = t; i < r; i++) M[i + (size_t)r * j] -= w * v[i];
+        }
+        M[t + (size_t)r * t] = beta;
+        for (int i = t + 1; i < r; i++) M[i + (size_t)r * t] = 0.0;
+    }
+    free(v);
+}
+
+/* The QRCP column order of the r x c matrix X alone (for the pins). */
+int oracle_qrcp_perm(int r, int c, const double *X, int *perm_out)
+{
+    if (r < 0 || c < 0 || !X || !perm_out) return -1;
+    double *M = (double *)malloc(sizeof(double) * (size_t)(r > 0 ? r : 1) * (c > 0 ? c : 1));
+    for (int j = 0; j < c; j++) {
+        perm_out[j] = j;
+        for (int i = 0; i < r; i++) M[i + (size_t)r * j] = X[i + (size_t)r * j];
+    }
+    qrcp_steps(r, c, M, perm_out);
+    free(M);
+    return 0;
+}
+
+/* The pivoting step of Sec. 2.1 (the condition of Drmac's convergence
+ * proof): QRCP of the leading rows of Vhat -- its rows at the real positions
+ * of block I -- over the real positions.  The chosen columns take the front
+ * real positions in the order chosen, the others follow in the order QRCP
+ * left them; padding positions stay put.  Vhat <- Vhat P, Dhat <- P^T Dhat P. */
+static void qrcp_pivot(int k, double *Ah, double *V, int I, int J, int b, int n_real)
+{
+    int *pos = (int *)malloc(sizeof(int) * (size_t)k);
+    int *perm = (int *)malloc(sizeof(int) * (size_t)k);
+    int *idx = (int *)malloc(sizeof(int) * (size_t)k);
+    int nr = 0, r1 = 0;
+    for (int x = 0; x < k; x++) {
+        int g = x < b ? I * b + x : J * b + (x - b);
+        idx[x] = x;
+        if (g < n_real) {
+            if (x < b) r1++;
+            pos[nr++] = x;
+        }
+    }
+    double *M = (double *)malloc(sizeof(double) * (size_t)(r1 > 0 ? r1 : 1) * (nr > 0 ? nr : 1));
+    for (int j = 0; j < nr; j++) {
+        perm[j] = j;
+        for (int i = 0; i < r1; i++) M[i + (size_t)r1 * j] = AT(V, k, pos[i], pos[j]);
+    }
+    qrcp_steps(r1, nr, M, perm);
+    for (int t = 0; t < nr; t++) idx[pos[t]] = pos[perm[t]];
+    double *B = (double *)malloc(sizeof(double) * (size_t)k * k);
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) AT(B, k, i, j) = AT(Ah, k, idx[i], idx[j]);
+    memcpy(Ah, B, sizeof(double) * (size_t)k * k);
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) AT(B, k, i, j) = AT(V, k, i, idx[j]);
+    memcpy(V, B, sizeof(double) * (size_t)k * k);
+    free(B);
+    free(M);
+    free(idx);
+    free(perm);
+    free(pos);
+}
+
 /* ------------------------------------------------------------------ */
 /* Blocked two-sided step (Algorithm 2 structure, one group of pairs)      */
 /* ------------------------------------------------------------------ */
@@ -490,6 +589,8 @@ static void evd_step(int np, int n_real, int b, double *A, double *Q, int npairs
             sort_pivot_desc(k, Ah, ws[e].V, t, ix, I, J, b, n_real);
             free(t);
             free(ix);
+        } else if (order == 2 && ws[e].rot > 0) {
+            qrcp_pivot(k, Ah, ws[e].V, I, J, b, n_real);
         }
         rot += ws[e].rot;
         isw += sw;
@@ -794,6 +895,8 @@ static double svd_step(int m, int np, int n_real, int b, double *G, int ldg, dou
             sort_pivot_desc(k, ws[e].Ah, ws[e].V, t, ix, I, J, b, n_real);
             free(t);
             free(ix);
+        } else if (order == 2 && ws[e].rot > 0) {
+            qrcp_pivot(k, ws[e].Ah, ws[e].V, I, J, b, n_real);
         }
         rot += ws[e].rot;
         isw += sw;

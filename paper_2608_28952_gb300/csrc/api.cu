@@ -79,6 +79,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     pa.order = order;
     pa.n_real = E.n_real;
     pa.gscratch = E.gscratch;
+    pa.qrws = E.qrws;
     pa.cnt = E.cnt;
     cudaError_t e = E.pcl > 1 ? launch_pivot_cluster(pa, E.pcl, E.qtab, cs) : launch_pivot(pa, cs);
     if (e != cudaSuccess) return e;
@@ -198,6 +199,7 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         int* rank = ws.get<int>(n);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        if (p.pivot_order == 2) E.qrws = ws.get<double>((size_t)E.ord.max_pairs * E.b * E.k);
         if (p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
@@ -314,6 +316,7 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
         DevCounters* cnt = ws.get<DevCounters>(1);
         const int pcl = choose_pivot_cluster(k, ord.dev_per_step);
         unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        double* qrws = p.pivot_order == 2 ? ws.get<double>((size_t)ord.max_pairs * b * k) : nullptr;
         const bool emu = p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1;
         int* err = emu ? ws.get<int>(1) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
@@ -367,6 +370,7 @@ static int gesvd_fp64(int m, int n, double* G, int ldg, double* sigma, double* V
                     pa.order = p.pivot_order;
                     pa.n_real = n;
                     pa.gscratch = gscr;
+                    pa.qrws = qrws;
                     pa.cnt = cnt;
                     if ((pcl > 1 ? launch_pivot_cluster(pa, pcl, qtab, cs) : launch_pivot(pa, cs)) != cudaSuccess)
                         return false;
@@ -684,6 +688,7 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         E.cnt = ws.get<DevCounters>(1);
         E.pcl = choose_pivot_cluster(E.k, E.ord.dev_per_step);
         E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        if (p.pivot_order == 2) E.qrws = ws.get<double>((size_t)E.ord.max_pairs * E.b * E.k);
         if (p.precision == JACOBI_PREC_FP64_EMU || (p.precision == JACOBI_PREC_FP64 && p.fp64_products == 1)) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
@@ -760,6 +765,7 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         DevCounters* cnt = ws.get<DevCounters>(1);
         const int pcl = choose_pivot_cluster(k, nps);
         unsigned* qtab = pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+        double* qrws = p.pivot_order == 2 ? ws.get<double>((size_t)ord.max_pairs * b * k) : nullptr;
         const bool emu = p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1;
         int* err = emu ? ws.get<int>(1) : nullptr;
         if (ws.failed) return JACOBI_ERR_ALLOC;
@@ -796,6 +802,7 @@ extern "C" int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, i
         pa.order = p.pivot_order;
         pa.n_real = np;
         pa.gscratch = gscr;
+        pa.qrws = qrws;
         pa.cnt = cnt;
         if ((pcl > 1 ? launch_pivot_cluster(pa, pcl, qtab, s) : launch_pivot(pa, s)) != cudaSuccess ||
             launch_max_into(relmax, nps, smax, s) != cudaSuccess)

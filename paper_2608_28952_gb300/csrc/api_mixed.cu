@@ -45,6 +45,7 @@ struct LowpState {
     double* Vb;
     int* rot;
     double* gscratch;
+    double* qrws = nullptr;   // pivot_order == 2: the QRCP scratch
     double* partial;
     unsigned* ticket;
     double* result;
@@ -71,6 +72,7 @@ cudaError_t launch_step32(const LowpState& L, int s, int cur, cudaStream_t cs, d
     pa.order = order;
     pa.n_real = L.n_real;
     pa.gscratch = L.gscratch;
+    pa.qrws = L.qrws;
     pa.cnt = L.cnt;
     cudaError_t e = L.pcl > 1 ? launch_pivot_cluster(pa, L.pcl, L.qtab, cs) : launch_pivot(pa, cs);
     if (e != cudaSuccess) return e;
@@ -219,6 +221,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     int* rank = ws.get<int>(n);
     E.pcl = choose_pivot_cluster(k, E.ord.dev_per_step);
     E.qtab = E.pcl > 1 ? ws.get<unsigned>(128 * 127 / 2) : nullptr;
+    if (p.pivot_order == 2) E.qrws = ws.get<double>((size_t)E.ord.max_pairs * p.b * k);
     // FP32 state (low-precision sweeps); pivot scratch shared with E
     L.Aw[0] = ws.get<float>(np2);
     L.Aw[1] = ws.get<float>(np2);
@@ -242,6 +245,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.Vb = E.Vb;
     L.rot = E.rot;
     L.gscratch = E.gscratch;
+    L.qrws = E.qrws;
     L.partial = E.partial;
     L.ticket = E.ticket;
     L.result = E.result;
@@ -462,6 +466,7 @@ extern "C" int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ld
     L.rot = ws.get<int>(ord.max_pairs);
     const size_t gsz = pivot_gscratch_doubles(k);
     L.gscratch = gsz ? ws.get<double>(gsz * ord.max_pairs) : nullptr;
+    L.qrws = p.pivot_order == 2 ? ws.get<double>((size_t)ord.max_pairs * p.b * k) : nullptr;
     int2* dpairs = ws.get<int2>(ord.dev_pairs.size() / 2);
     L.dpairs = dpairs;
     L.err = ws.get<int>(1);

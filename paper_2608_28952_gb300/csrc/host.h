@@ -138,7 +138,7 @@ inline int choose_pivot_cluster(int k, int npairs)
         const int want = atoi(env);
         if (want == 1) C = 1;
         else if (want == 2 || want == 4 || want == 8) {
-            if (k % want == 0 && k / want >= 8 && pivot_cluster_smem(k, want) + 4096 <= (size_t)smem) C = want;
+            if (k % want == 0 && k / want >= 8 && pivot_cluster_smem(k, want) + 8192 <= (size_t)smem) C = want;
         }
     }
     return C;
@@ -152,7 +152,7 @@ inline int check_params(const jacobi_params& p)
     if (p.max_sweeps < 0 || p.max_sweeps > 1000 || p.inner_max_sweeps < 0) return -7;
     if (!(p.tol >= 0.0) || !(p.inner_tol >= 0.0)) return -7;
     if (p.conv != JACOBI_CONV_OFF_ABS && p.conv != JACOBI_CONV_REL) return -7;
-    if (p.pivot_order != 0 && p.pivot_order != 1) return -7;
+    if (p.pivot_order < 0 || p.pivot_order > 2) return -7;
     if (p.precision < JACOBI_PREC_FP64 || p.precision > JACOBI_PREC_FP64_EMU) return -7;
     if (p.fp64_products != 0 && p.fp64_products != 1) return -7;
     if (p.svd_qr != 0 && p.svd_qr != 1) return -7;
@@ -195,6 +195,8 @@ struct EvdState {
     // products and the timeout word
     double* T64 = nullptr;
     int* err = nullptr;
+    // pivot_order == 2: the per-pair QRCP scratch of the pivoting step
+    double* qrws = nullptr;
 };
 
 // Result of a run of sweeps: code 0 converged, 1 max_sweeps ran out, <0 error.

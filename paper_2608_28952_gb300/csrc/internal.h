@@ -82,6 +82,7 @@ struct PivotArgs {
     int order;                 // 1: sort eigenpairs descending over real rows
     int n_real;                // rows/columns >= n_real are zero padding
     double* gscratch;          // k > 128: per-pair global scratch (packed A + V)
+    double* qrws;              // order == 2: per-pair QRCP scratch, b x k doubles each
     DevCounters* cnt;
 };
 cudaError_t launch_pivot(const PivotArgs& a, cudaStream_t s);

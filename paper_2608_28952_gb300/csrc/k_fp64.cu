@@ -27,6 +27,7 @@
 
 #include "internal.h"
 #include "jacobi_core.cuh"
+#include "qrcp.cuh"
 
 namespace jac {
 
@@ -302,13 +303,37 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
 
     // ---- permutation Vhat <- Vhat P: eigenpair at position x moves to
     // s_dest[x]; with order == 1 the non-padding positions receive their
-    // eigenvalues in descending order (ties by position), padding stays put.
+    // eigenvalues in descending order (ties by position); with order == 2 the
+    // order QRCP picks on the leading rows of Vhat (Sec. 2.1); padding stays
+    // put.
+    __shared__ int s_nr, s_r1;
     if (tid == 0) {
-        int nr = 0;
+        int nr = 0, r1 = 0;
         for (int x = 0; x < k; ++x)
-            if (pair_map(I, J, b, x) < a.n_real) s_pos[nr++] = x;
+            if (pair_map(I, J, b, x) < a.n_real) {
+                r1 += x < b;
+                s_pos[nr++] = x;
+            }
+        s_nr = nr;
+        s_r1 = r1;
     }
     __syncthreads();
+    if (a.order == 2 && total_rot > 0) {
+        __shared__ int s_perm[256];
+        __shared__ double s_cn[256], s_vh[128];
+        const int nr = s_nr, r1 = s_r1;
+        double* M = a.qrws + (size_t)e * b * k;
+        for (int idx = tid; idx < r1 * nr; idx += PIV_T) {
+            const int i = idx % r1, j = idx / r1;
+            M[idx] = V[s_pos[i] + (size_t)k * s_pos[j]];
+        }
+        __syncthreads();
+        qrcp_order(r1, nr, M, s_perm, s_cn, s_vh);
+        for (int x = tid; x < k; x += PIV_T) s_dest[x] = x;
+        __syncthreads();
+        for (int t = tid; t < nr; t += PIV_T) s_dest[s_pos[s_perm[t]]] = s_pos[t];
+        __syncthreads();
+    } else {
     for (int x = tid; x < k; x += PIV_T) {
         int dest = x;
         if (a.order == 1 && total_rot > 0 && pair_map(I, J, b, x) < a.n_real) {
@@ -324,6 +349,7 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
         s_dest[x] = dest;
     }
     __syncthreads();
+    }
 
     // ---- outputs: V and V^T, D into the next A, counters
     double* Vo = a.V + (size_t)e * 2 * k * k;

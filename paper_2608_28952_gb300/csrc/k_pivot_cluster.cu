@@ -26,6 +26,7 @@
 #include "internal.h"
 #include "jacobi_core.cuh"
 #include "cluster_common.cuh"
+#include "qrcp.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -268,13 +269,46 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     for (int x = tid; x < k; x += nt) dhi[x] += dlo[x];  // hi + lo, rounded once
     __syncthreads();
 
-    // ---- permutation (identical in every CTA: same diagonal replica)
+    // ---- permutation (identical in every CTA: same diagonal replica; the
+    // QRCP order of Sec. 2.1's pivoting step is computed by rank 0 on the
+    // leading rows of Vhat, gathered from the CTAs that own them, and sent
+    // to every CTA)
+    __shared__ int s_nr, s_r1;
     if (tid == 0) {
-        int nr = 0;
+        int nr = 0, r1 = 0;
         for (int x = 0; x < k; ++x)
-            if (pc_pair_map(I, J, b, x) < a.n_real) s_pos[nr++] = x;
+            if (pc_pair_map(I, J, b, x) < a.n_real) {
+                r1 += x < b;
+                s_pos[nr++] = x;
+            }
+        s_nr = nr;
+        s_r1 = r1;
     }
     __syncthreads();
+    if (a.order == 2 && total_rot > 0) {
+        __shared__ int s_perm[256];
+        __shared__ double s_cn[256], s_vh[128];
+        const int nr = s_nr, r1 = s_r1;
+        double* M = a.qrws + (size_t)e * b * k;
+        for (int idx = tid; idx < r1 * nr; idx += nt) {   // this CTA's leading rows of Vhat
+            const int i = idx % r1, j = idx / r1, row = s_pos[i];
+            if (row >= r_lo && row < r_lo + rows) M[idx] = Vl[(row - r_lo) + (size_t)rows * s_pos[j]];
+        }
+        __threadfence();
+        cluster.sync();
+        if (r == 0) {
+            qrcp_order(r1, nr, M, s_perm, s_cn, s_vh);
+            for (int x = tid; x < k; x += nt) s_dest[x] = x;
+            __syncthreads();
+            for (int t = tid; t < nr; t += nt) s_dest[s_pos[s_perm[t]]] = s_pos[t];
+            __syncthreads();
+            for (int u = 1; u < C; ++u) {
+                int* rd = cluster.map_shared_rank(s_dest, u);
+                for (int x = tid; x < k; x += nt) rd[x] = s_dest[x];
+            }
+        }
+        cluster.sync();
+    } else {
     for (int x = tid; x < k; x += nt) {
         int dest = x;
         if (a.order == 1 && total_rot > 0 && pc_pair_map(I, J, b, x) < a.n_real) {
@@ -290,6 +324,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
         s_dest[x] = dest;
     }
     __syncthreads();
+    }
 
     // ---- outputs: this CTA's rows of V (and the matching columns of V^T)
     double* Vo = a.V + (size_t)e * 2 * k * k;
@@ -335,7 +370,7 @@ int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
     int best = 1;
     for (int C = 2; C <= cmax; C *= 2) {
         if (k % C || k / C < 8 || npairs * C > sms) break;
-        if (pivot_cluster_smem(k, C) + 4096 <= smem_cap) best = C;
+        if (pivot_cluster_smem(k, C) + 8192 <= smem_cap) best = C;   // + the static shared memory
     }
     return best;
 }

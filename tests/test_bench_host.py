@@ -119,3 +119,20 @@ def test_batch_shapes_follow_the_recipe():
     assert len(sh) == 20000 and all(m == n and 8 <= n <= 512 for m, n in sh)
     sv = bench.batch_shapes(bench.WORKLOADS["batched_svd_f32"])
     assert sv == [(1024, 64)] * 4096
+
+
+def test_cpu_sample_of_the_qr_form_runs_the_oracle_on_r_transpose():
+    """The CPU baseline of the QR-preconditioned SVD: numpy's QR once, then
+    the oracle's one-sided steps on the n x n R^T (small case)."""
+    wl = dict(kind="svd", m=120, n=24, b=4, seed=5, svd_qr=1, desc="small QR form")
+    times, S, extra = bench.cpu_oracle_sample(wl, sweeps=3, budget_s=0.01, max_steps=2)
+    assert S == 5 and len(times) >= 1 and extra > 0.0
+    wl_direct = dict(kind="svd", m=120, n=24, b=4, seed=5, desc="small direct form")
+    times2, S2, extra2 = bench.cpu_oracle_sample(wl_direct, sweeps=3, budget_s=0.01, max_steps=2)
+    assert S2 == 5 and extra2 == 0.0
+
+
+def test_new_workloads_carry_their_options():
+    assert bench.WORKLOADS["svd16384x2048qr"]["svd_qr"] == 1
+    assert bench.WORKLOADS["svd16384x2048qremu"]["precision"] == 5
+    assert bench.WORKLOADS["mixed8192emu"]["fp64_products"] == 1

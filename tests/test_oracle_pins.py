@@ -610,3 +610,58 @@ def test_bf16_split_definition():
     ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], np.float32)
     h, _ = oracle.split_bf16(ties)
     assert h[0] == 1.0 and h[1] == np.float32(1 + 2 ** -6)
+
+
+# ------------------------------------------------------------------ pivoting step (QRCP, Sec. 2.1)
+@pytest.mark.parametrize("r,c,seed", [(8, 16, 1), (5, 12, 2), (16, 32, 3), (7, 7, 4)])
+def test_qrcp_order_matches_lapack(r, c, seed):
+    """The QRCP rule against LAPACK's pivoted QR (scipy, dgeqp3) on generic
+    matrices: the same leading columns in the same order."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    X = np.random.default_rng(seed).standard_normal((r, c))
+    mine = oracle.qrcp_perm(X)
+    _, _, piv = scipy_linalg.qr(X, pivoting=True, mode="economic")
+    assert list(mine[:min(r, c)]) == list(piv[:min(r, c)])
+    assert sorted(mine) == list(range(c))
+
+
+def test_qrcp_pivoting_step_keeps_the_step_a_similarity():
+    """pivot_order = 2 permutes each pivot's eigenpairs only: the step is
+    still an orthogonal similarity (spectrum, Frobenius norm, Q orthogonal),
+    the leading b x b block of every Vhat P is well conditioned, and the
+    full solve meets the FP64 gates."""
+    n, b = 48, 6
+    A, lam = gen.sym_known(n, "uniform", seed=91)
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, n // b)
+    A2, Q2, rot = oracle.syev_step(A, np.eye(n), b, tab[0], pivot_order=2)
+    assert rot > 0
+    assert np.abs(np.linalg.eigvalsh(A2) - np.sort(lam)).max() <= 1e-14 * n
+    assert np.linalg.norm(Q2.T @ Q2 - np.eye(n)) <= 1e-14 * n
+    assert abs(np.linalg.norm(A2) - np.linalg.norm(A)) <= 1e-14 * np.linalg.norm(A)
+    w, Q, Af, st, status = oracle.syev(A, b=b, pivot_order=2)
+    assert status == 0
+    assert np.abs(w - np.sort(lam)).max() <= 1e-13
+    assert np.linalg.norm(A @ Q - Q * w[None, :]) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_qrcp_pivoting_one_sided():
+    G, sig = gen.svd_known(150, 30, seed=92, decades=6.0)
+    U, s, V, st, status = oracle.gesvd(G, b=5, pivot_order=2)
+    assert status == 0 and np.abs(s - sig).max() <= 1e-13 * sig[0]
+    assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
+
+
+def test_qrcp_selects_a_well_conditioned_leading_block():
+    """The point of the pivoting step: the leading rows of Vhat have
+    orthonormal rows, and the b columns QRCP moves to the front form a block
+    much better conditioned than the unpermuted leading block of a pivot
+    whose eigenvectors are scrambled."""
+    b = 8
+    r = np.random.default_rng(93)
+    Qh = np.linalg.qr(r.standard_normal((2 * b, 2 * b)))[0]
+    Ah = Qh @ np.diag(np.linspace(-1, 1, 2 * b)) @ Qh.T
+    _, V, _, _ = oracle.pivot_solve(Ah)
+    perm = oracle.qrcp_perm(V[:b, :])
+    s_sel = np.linalg.svd(V[:b, perm[:b]], compute_uv=False)[-1]
+    s_first = np.linalg.svd(V[:b, :b], compute_uv=False)[-1]
+    assert s_sel >= s_first and s_sel > 0.1
