@@ -100,7 +100,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     ua.rot = E.rot;
     ua.cnt = E.cnt;
     if (E.T64) {
-        EmuUpdArgs ea{ua, E.T64, E.err};
+        EmuUpdArgs ea{ua, E.T64, E.err, E.balance};
         return launch_emu_update(ea, cs);
     }
     return launch_update_evd(ua, cs);
@@ -204,6 +204,7 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
         }
+        E.balance = p.conv == JACOBI_CONV_REL;
         if (ws.failed) return JACOBI_ERR_ALLOC;
         if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (E.err && cudaMemsetAsync(E.err, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
@@ -695,6 +696,7 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         } else if (p.precision != JACOBI_PREC_FP64) {
             return JACOBI_ERR_UNSUPPORTED;
         }
+        E.balance = p.conv == JACOBI_CONV_REL;
         if (ws.failed) return JACOBI_ERR_ALLOC;
         if (E.err && cudaMemsetAsync(E.err, 0, sizeof(int), s) != cudaSuccess) return JACOBI_ERR_CUDA;
         if (E.qtab && launch_quad_table(E.qtab, 128, s) != cudaSuccess) return JACOBI_ERR_CUDA;

@@ -236,6 +236,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     if (p.fp64_products == 1) {   // refinement and closing sweeps with FP64-accurate tensor-core products
         E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, k));
         E.err = L.err;
+        E.balance = p.conv == JACOBI_CONV_REL;
         xexp = ws.get<int>(2 * (size_t)np);
     }
     if (ws.failed) return JACOBI_ERR_ALLOC;

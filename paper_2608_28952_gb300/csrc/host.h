@@ -197,6 +197,8 @@ struct EvdState {
     int* err = nullptr;
     // pivot_order == 2: the per-pair QRCP scratch of the pivoting step
     double* qrws = nullptr;
+    // emulated products: balance by the diagonal (relative stop criterion)
+    int balance = 0;
 };
 
 // Result of a run of sweeps: code 0 converged, 1 max_sweeps ran out, <0 error.

@@ -207,6 +207,9 @@ struct EmuUpdArgs {
     UpdateArgs u;
     double* T;      // [npb][k*k]
     int* err;       // set on a timed-out tensor-core wait
+    // 1: balance the pair-blocks' columns by powers of two from the diagonal
+    // (graded positive definite inputs under the relative stop criterion)
+    int balance = 0;
 };
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s);
 // The one-sided step's products FP64-accurate on the tensor cores: Gram

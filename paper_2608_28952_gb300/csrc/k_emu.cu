@@ -57,6 +57,18 @@ __device__ __forceinline__ int exp2_of(double x)
     return -1075 + (64 - __clzll((long long)(b & 0xFFFFFFFFFFFFFull)));   // subnormal
 }
 
+// x 2^-c for a power-of-two shift by integer operations on the exponent
+// field (exact; the FP64 path only where the result leaves the normal range).
+__device__ __forceinline__ double pow2_shift(double x, int c)
+{
+    const long long bits = __double_as_longlong(x);
+    const int ea = (int)((bits >> 52) & 0x7FF);
+    if (c == 0 || (bits << 1) == 0) return x;
+    if (ea == 0) return ldexp(x, -c);   // subnormal
+    if (ea - c >= 1 && ea - c <= 2046) return __longlong_as_double(bits - (long long)c * (1ll << 52));
+    return ldexp(x, -c);
+}
+
 // The eight slices of x for the row/column scale 2^E (|x| < 2^E): the
 // fixed-point value X = |x| 2^{56-E} (rounded to nearest where x is more than
 // four binades below the scale; exact otherwise) written with balanced
@@ -560,10 +572,25 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
             return;
         }
         const double* V2t = u.V + (size_t)e2 * 2 * k * k + (size_t)k * k;
+        // with a.balance: A_P1P2 V2 = (A_P1P2 2^-c)(2^c V2), c_kk ~ log2
+        // sqrt|a_jj| of column kk's diagonal entry: balanced operands for
+        // graded positive definite matrices (exact; for indefinite matrices
+        // a small diagonal entry says nothing about its column, so off)
+        __shared__ int s_cs[256];
+        for (int kk = threadIdx.x; kk < k; kk += E_T) {
+            const int g = emap(I2, J2, b, kk);
+            const int ed = a.balance ? exp2_of(u.Ain[g + (size_t)u.lda * g]) : -1100;
+            s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+        }
+        __syncthreads();
         auto fa = [&](int m, int kk) -> double {
-            return m0 + m < k && kk < k ? u.Ain[emap(I1, J1, b, m0 + m) + (size_t)u.lda * emap(I2, J2, b, kk)] : 0.0;
+            return m0 + m < k && kk < k
+                       ? pow2_shift(u.Ain[emap(I1, J1, b, m0 + m) + (size_t)u.lda * emap(I2, J2, b, kk)], s_cs[kk])
+                       : 0.0;
         };
-        auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? V2t[(n0 + n) + (size_t)k * kk] : 0.0; };
+        auto fb = [&](int kk, int n) -> double {
+            return n0 + n < k && kk < k ? pow2_shift(V2t[(n0 + n) + (size_t)k * kk], -s_cs[kk]) : 0.0;
+        };
         line_exponents(EM, k, fa, s_eA, s_scr);
         line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
         emu_tile<false>(k, fa, fb, s_eA, s_eB,
@@ -641,8 +668,21 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
         return;
     }
     const double* V1t = u.V + (size_t)e1 * 2 * k * k + (size_t)k * k;   // V1^T(m, kk) at V1t[m + k kk]
-    auto fa = [&](int m, int kk) -> double { return m0 + m < k && kk < k ? V1t[(m0 + m) + (size_t)k * kk] : 0.0; };
-    auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? T[kk + (size_t)k * (n0 + n)] : 0.0; };
+    // with a.balance: V1^T T = (V1^T 2^c)(2^-c T), c_kk from the diagonal of
+    // row kk of P1
+    __shared__ int s_cs[256];
+    for (int kk = threadIdx.x; kk < k; kk += E_T) {
+        const int g = emap(I1, J1, b, kk);
+        const int ed = a.balance ? exp2_of(u.Ain[g + lda * g]) : -1100;
+        s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+    }
+    __syncthreads();
+    auto fa = [&](int m, int kk) -> double {
+        return m0 + m < k && kk < k ? pow2_shift(V1t[(m0 + m) + (size_t)k * kk], -s_cs[kk]) : 0.0;
+    };
+    auto fb = [&](int kk, int n) -> double {
+        return n0 + n < k && kk < k ? pow2_shift(T[kk + (size_t)k * (n0 + n)], s_cs[kk]) : 0.0;
+    };
     line_exponents(EM, k, fa, s_eA, s_scr);
     line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
     emu_tile<false>(k, fa, fb, s_eA, s_eB,
@@ -696,17 +736,6 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_gram(EmuSvdArgs a, int nmt, int 
         atomicAdd(&a.cnt->flops_update, 2ull * EM * EN * K);
         atomicAdd(&a.cnt->flops_lowp, 72ull * EM * EN * K);
     }
-}
-
-// x 2^-c for a power-of-two shift by integer operations on the exponent
-// field (exact; the FP64 path only where the result leaves the normal range).
-__device__ __forceinline__ double pow2_shift(double x, int c)
-{
-    const long long bits = __double_as_longlong(x);
-    const int ea = (int)((bits >> 52) & 0x7FF);
-    if (ea == 0 || c == 0) return ea == 0 && c != 0 ? ldexp(x, -c) : x;
-    if (ea - c >= 1 && ea - c <= 2046) return __longlong_as_double(bits - (long long)c * (1ll << 52));
-    return ldexp(x, -c);
 }
 
 // Column update: items [0, n_g): tile (rt, nt) of G'(:, P) = G(:, P) V_P;

@@ -209,3 +209,28 @@ def test_svd_rejects_the_mixed_precisions(jg):
     s = torch.empty(16, dtype=torch.float64, device="cuda")
     assert jg.jacobi_gesvd(jg.colmajor(G, device="cuda", dtype=torch.float64), s, None,
                            jg.params(b=4, want_vectors=0, precision=2))[0] == jg.ERR_UNSUPPORTED
+
+
+def test_emu_graded_dhd_relative_criterion(jg):
+    """A = D H D (kappa(H) <= 10, eigenvalues over ~12 decades) with the
+    relative stop criterion: every eigenvalue to 1e-12 relative, as on the
+    FP64 path (the emulated products balance the pair-blocks' columns by
+    powers of two taken from the diagonal)."""
+    U = 2.0 ** -53
+    A, d, H = gen.graded_dhd(128, seed=gen.SEEDS["c2dhd"])
+    w_or, *_ = oracle.syev(A, b=16, conv=oracle.CONV_REL, tol=4 * U)
+    w, Q, _, st = jg.syev(A, b=16, conv=jg.CONV_REL, tol=4 * U, precision=EMU)
+    w = w.cpu().numpy()
+    assert st.status == 0
+    assert (np.abs(w - w_or) / np.abs(w_or)).max() <= 1e-12
+
+
+def test_emu_graded_spectrum_relative_gate(jg):
+    A, lam = gen.sym_known(512, "graded", seed=5800)
+    w_or, *_ = oracle.syev(A, b=32)
+    w, Q, _, st = jg.syev(A, b=32, precision=EMU)
+    w = w.cpu().numpy()
+    assert st.status == 0
+    assert np.abs(w - w_or).max() <= 1e-13 * np.abs(w_or).max()
+    big = np.abs(w_or) >= 1e-3 * np.abs(w_or).max()
+    assert (np.abs(w - w_or)[big] / np.abs(w_or[big])).max() <= 1e-12
