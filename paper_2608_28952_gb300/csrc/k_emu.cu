@@ -550,6 +550,7 @@ __device__ __forceinline__ void edecode_pb(int pb, int& e1, int& e2)
 // Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2 (FP64,
 // k x k per pair-block); items beyond: tile (rt, nt) of Q'(:,P) = Q(:,P) V_P.
 // V^T (stored after V by the pivot kernel) gives the coalesced operand loads.
+template <bool BAL>
 __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
 {
     __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
@@ -577,19 +578,25 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
         // graded positive definite matrices (exact; for indefinite matrices
         // a small diagonal entry says nothing about its column, so off)
         __shared__ int s_cs[256];
-        for (int kk = threadIdx.x; kk < k; kk += E_T) {
-            const int g = emap(I2, J2, b, kk);
-            const int ed = a.balance ? exp2_of(u.Ain[g + (size_t)u.lda * g]) : -1100;
-            s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+        if constexpr (BAL) {
+            for (int kk = threadIdx.x; kk < k; kk += E_T) {
+                const int g = emap(I2, J2, b, kk);
+                const int ed = exp2_of(u.Ain[g + (size_t)u.lda * g]);
+                s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         auto fa = [&](int m, int kk) -> double {
-            return m0 + m < k && kk < k
-                       ? pow2_shift(u.Ain[emap(I1, J1, b, m0 + m) + (size_t)u.lda * emap(I2, J2, b, kk)], s_cs[kk])
-                       : 0.0;
+            if (!(m0 + m < k && kk < k)) return 0.0;
+            const double x = u.Ain[emap(I1, J1, b, m0 + m) + (size_t)u.lda * emap(I2, J2, b, kk)];
+            if constexpr (BAL) return pow2_shift(x, s_cs[kk]);
+            return x;
         };
         auto fb = [&](int kk, int n) -> double {
-            return n0 + n < k && kk < k ? pow2_shift(V2t[(n0 + n) + (size_t)k * kk], -s_cs[kk]) : 0.0;
+            if (!(n0 + n < k && kk < k)) return 0.0;
+            const double x = V2t[(n0 + n) + (size_t)k * kk];
+            if constexpr (BAL) return pow2_shift(x, -s_cs[kk]);
+            return x;
         };
         line_exponents(EM, k, fa, s_eA, s_scr);
         line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
@@ -640,6 +647,7 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
 
 // Stage 2: tile (mt, nt) of O_pb = V1^T T_pb, written to A' at (P1 rows, P2
 // columns) and mirrored.
+template <bool BAL>
 __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
 {
     __shared__ int s_eA[EM], s_eB[EN], s_scr[E_T];
@@ -671,17 +679,25 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
     // with a.balance: V1^T T = (V1^T 2^c)(2^-c T), c_kk from the diagonal of
     // row kk of P1
     __shared__ int s_cs[256];
-    for (int kk = threadIdx.x; kk < k; kk += E_T) {
-        const int g = emap(I1, J1, b, kk);
-        const int ed = a.balance ? exp2_of(u.Ain[g + lda * g]) : -1100;
-        s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+    if constexpr (BAL) {
+        for (int kk = threadIdx.x; kk < k; kk += E_T) {
+            const int g = emap(I1, J1, b, kk);
+            const int ed = exp2_of(u.Ain[g + lda * g]);
+            s_cs[kk] = ed <= -1100 ? 0 : (ed >> 1);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     auto fa = [&](int m, int kk) -> double {
-        return m0 + m < k && kk < k ? pow2_shift(V1t[(m0 + m) + (size_t)k * kk], -s_cs[kk]) : 0.0;
+        if (!(m0 + m < k && kk < k)) return 0.0;
+        const double x = V1t[(m0 + m) + (size_t)k * kk];
+        if constexpr (BAL) return pow2_shift(x, -s_cs[kk]);
+        return x;
     };
     auto fb = [&](int kk, int n) -> double {
-        return n0 + n < k && kk < k ? pow2_shift(T[kk + (size_t)k * (n0 + n)], s_cs[kk]) : 0.0;
+        if (!(n0 + n < k && kk < k)) return 0.0;
+        const double x = T[kk + (size_t)k * (n0 + n)];
+        if constexpr (BAL) return pow2_shift(x, s_cs[kk]);
+        return x;
     };
     line_exponents(EM, k, fa, s_eA, s_scr);
     line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
@@ -822,13 +838,15 @@ cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
     const int npb = u.npairs * (u.npairs - 1) / 2;
     const int n_sand = npb * nmt * nnt;
     const int n_q = u.Qin ? u.npairs * ((u.qrows + EM - 1) / EM) * nnt : 0;
-    cudaError_t e = cudaFuncSetAttribute(k_emu_upd1, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    auto u1 = a.balance ? k_emu_upd1<true> : k_emu_upd1<false>;
+    auto u2 = a.balance ? k_emu_upd2<true> : k_emu_upd2<false>;
+    cudaError_t e = cudaFuncSetAttribute(u1, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
     if (e != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_emu_upd2, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(u2, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM)) != cudaSuccess)
         return e;
-    if (n_sand + n_q > 0) k_emu_upd1<<<n_sand + n_q, E_T, E_SMEM, s>>>(a, n_sand);
+    if (n_sand + n_q > 0) u1<<<n_sand + n_q, E_T, E_SMEM, s>>>(a, n_sand);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_sand > 0) k_emu_upd2<<<n_sand, E_T, E_SMEM, s>>>(a);
+    if (n_sand > 0) u2<<<n_sand, E_T, E_SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
