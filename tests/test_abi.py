@@ -51,6 +51,7 @@ def test_params_default_matches_header(jg):
     assert p.tol == 1e-14 and p.inner_tol == 4 * 2.0 ** -53
     assert p.precision == jg.PREC_FP64 and p.conv == jg.CONV_OFF_ABS
     assert p.want_vectors == 1 and p.warm_start == 0 and p.pivot_order == 1
+    assert p.fp64_products == 0 and p.svd_qr == 0   # DFMA products, the direct one-sided SVD
 
 
 def test_status_strings(jg):
