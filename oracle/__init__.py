@@ -12,7 +12,9 @@ silent.
 
 Pinned by ``tests/test_oracle_pins.py`` against closed forms, invariants,
 brute force (exact characteristic polynomial at n <= 4), the paper's printed
-ordering tables, and LAPACK as an independent witness.
+ordering tables, and LAPACK as an independent witness (singular values, the
+QRCP column order of the pivoting step).  ``gesvd_qr`` composes LAPACK's QR
+(a library step) with the pinned one-sided method.
 """
 from __future__ import annotations
 

@@ -47,7 +47,10 @@
  *     slot of the pivoting step of Sec. 2.1, items 1-2 after Algorithm 1); the
  *     permutation used here sorts the pivot's eigenvalues in descending order
  *     (ties keep their index order) over the pivot's real rows, leaving the
- *     zero padding rows where they are; the GPU path applies the same rule;
+ *     zero padding rows where they are (pivot_order 1); pivot_order 2 is the
+ *     pivoting step itself: the column order that column-pivoted QR
+ *     (Businger-Golub, norms recomputed, ties to the smaller index) picks on
+ *     the leading real rows of Vhat; the GPU path applies the same rules;
  *   - the outer loop stops when off(A) <= tol*||A||_F (or, for the relative
  *     criterion, max |a_ij|/sqrt|a_ii a_jj| <= tol), or when the measure is
  *     already <= 100*tol and did not halve over the last sweep (stall).
