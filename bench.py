@@ -486,6 +486,40 @@ def evd_kernel_classes(stats, wl, peaks):
     return cls
 
 
+def svd_kernel_classes(stats, wl, peaks):
+    """Device time, issued flops and roofline of the one-sided solve's kernel
+    classes (summed over the timed steps): Gram + column update, the Gram
+    pivots and, for the QR form, the QR preconditioning."""
+    tot = lambda f: sum(getattr(st, f) for st in stats)
+    qr = bool(wl.get("svd_qr"))
+    emu = wl.get("precision", 0) == 5 or wl.get("fp64_products", 0) == 1
+    kernels = {"update": dict(kernel="k_gram + k_update_cols", ms=tot("ms_update"),
+                              launches=tot("update_launches"), flops=tot("flops_update")),
+               "pivot": dict(kernel="k_pivot / k_pivot_cluster (Gram pivots)", ms=tot("ms_pivot"),
+                             launches=tot("pivot_launches"),
+                             flops=tot("flops_fp64") - (0 if emu else tot("flops_update"))
+                             - tot("flops_precond"))}
+    if qr:
+        kernels["precond"] = dict(kernel="k_house_vec + k_house_apply + k_qr_ytx + k_gemm64 "
+                                         "(Householder QR and U = Q W, FP64)",
+                                  ms=tot("ms_precond"), launches=None, flops=tot("flops_precond"))
+    for c in kernels.values():
+        c.update(bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS, unit="TFLOP/s")
+    if emu:
+        # FP64-accurate products from bf16 slices: the tensor pipe on the
+        # issued slice products, the FP64-equivalent rate beside it
+        u = kernels["update"]
+        u.update(kernel="k_emu_gram + k_emu_cols (tcgen05, FP64-accurate)", flops=36 * tot("flops_update"),
+                 bound="tensor", peak=peaks.get("bf16_tflops_sustained"),
+                 peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
+                            "flops = the 36 bf16 slice products issued",
+                 fp64_equiv_tflops=(tot("flops_update") / (u["ms"] / 1e3) / 1e12 if u["ms"] > 0 else None))
+    for c in kernels.values():
+        c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
+        c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
+    return kernels
+
+
 def run_gpu(args, wl):
     if wl["kind"] in ("batched_evd", "batched_svd"):
         return run_batched(args, wl)
@@ -596,35 +630,10 @@ def run_gpu(args, wl):
                     "share_of_step": kc["ms"] / ms if ms else None,
                     "profile": os.path.relpath(prof, ROOT) if prof else None}
     else:
-        tot = lambda f: sum(getattr(st, f) for st in stats)
         m, n_ = wl["m"], wl["n"]
-        qr = bool(wl.get("svd_qr"))
-        m_eff = n_ if qr else m   # with QR preconditioning the sweeps run on R^T
+        m_eff = n_ if wl.get("svd_qr") else m   # with QR preconditioning the sweeps run on R^T
         emu = prec == 5 or wl.get("fp64_products", 0) == 1
-        kernels = {"update": dict(kernel="k_gram + k_update_cols", ms=tot("ms_update"),
-                                  launches=tot("update_launches"), flops=tot("flops_update")),
-                   "pivot": dict(kernel="k_pivot / k_pivot_cluster (Gram pivots)", ms=tot("ms_pivot"),
-                                 launches=tot("pivot_launches"),
-                                 flops=tot("flops_fp64") - (0 if emu else tot("flops_update"))
-                                 - tot("flops_precond"))}
-        if qr:
-            kernels["precond"] = dict(kernel="k_house_vec + k_house_apply + k_qr_ytx + k_gemm64 "
-                                             "(Householder QR and U = Q W, FP64)",
-                                      ms=tot("ms_precond"), launches=None, flops=tot("flops_precond"))
-        for c in kernels.values():
-            c.update(bound="alu", peak=FP64_PEAK_TFLOPS, peak_basis=FP64_BASIS, unit="TFLOP/s")
-        if emu:
-            # FP64-accurate products from bf16 slices: the tensor pipe on the
-            # issued slice products, the FP64-equivalent rate beside it
-            u = kernels["update"]
-            u.update(kernel="k_emu_gram + k_emu_cols (tcgen05, FP64-accurate)", flops=36 * tot("flops_update"),
-                     bound="tensor", peak=peaks.get("bf16_tflops_sustained"),
-                     peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
-                                "flops = the 36 bf16 slice products issued",
-                     fp64_equiv_tflops=(tot("flops_update") / (u["ms"] / 1e3) / 1e12 if u["ms"] > 0 else None))
-        for c in kernels.values():
-            c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
-            c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None
+        kernels = svd_kernel_classes(stats, wl, peaks)
         dom = max(kernels, key=lambda c: kernels[c]["ms"])
         kc = kernels[dom]
         k = 2 * b

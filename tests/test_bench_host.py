@@ -136,3 +136,42 @@ def test_new_workloads_carry_their_options():
     assert bench.WORKLOADS["svd16384x2048qr"]["svd_qr"] == 1
     assert bench.WORKLOADS["svd16384x2048qremu"]["precision"] == 5
     assert bench.WORKLOADS["mixed8192emu"]["fp64_products"] == 1
+
+
+def _stats(**kw):
+    base = dict(ms_update=0.0, update_launches=0, flops_update=0.0, ms_pivot=0.0, pivot_launches=0,
+                flops_fp64=0.0, flops_precond=0.0, ms_precond=0.0, flops_lowp=0.0, ms_update_lowp=0.0,
+                sweeps_lowp=0, ms_refine=0.0, flops_refine=0.0)
+    base.update(kw)
+    return SimpleNamespace(**base)
+
+
+def test_svd_kernel_classes_direct_qr_and_emulated():
+    peaks = {"bf16_tflops_sustained": 1688.5}
+    st = _stats(ms_update=1000.0, update_launches=620, flops_update=1e12, ms_pivot=500.0, pivot_launches=310,
+                flops_fp64=1.2e12 + 5e11, flops_precond=5e11, ms_precond=400.0)
+    # direct FP64: update flops are FP64 flops, pivot = the rest of flops_fp64
+    k = bench.svd_kernel_classes([st], dict(m=16384, n=2048, b=64), peaks)
+    assert set(k) == {"update", "pivot"} and k["update"]["bound"] == "alu"
+    assert abs(k["update"]["achieved"] - 1.0) < 1e-12          # 1e12 flops in 1 s
+    assert abs(k["pivot"]["flops"] - (1.7e12 - 1e12 - 5e11)) < 1.0
+    # QR form: the preconditioning is its own class
+    k = bench.svd_kernel_classes([st], dict(m=16384, n=2048, b=64, svd_qr=1), peaks)
+    assert set(k) == {"update", "pivot", "precond"} and k["precond"]["ms"] == 400.0
+    # emulated products: the update class counts the 36 slice products against bf16
+    k = bench.svd_kernel_classes([st], dict(m=16384, n=2048, b=64, svd_qr=1, precision=5), peaks)
+    assert k["update"]["bound"] == "tensor" and k["update"]["flops"] == 36e12
+    assert abs(k["update"]["fp64_equiv_tflops"] - 1.0) < 1e-12
+    assert abs(k["pivot"]["flops"] - (1.7e12 - 5e11)) < 1.0     # emulated updates add no FP64 flops
+
+
+def test_evd_kernel_classes_emulated_and_mixed():
+    peaks = {"bf16_tflops_sustained": 1688.5}
+    st = _stats(ms_update=2000.0, update_launches=1764, flops_update=2e12, ms_pivot=900.0,
+                pivot_launches=882, flops_fp64=4e11, flops_lowp=72e12)
+    k = bench.evd_kernel_classes([st], dict(n=4096, b=64, precision=5), peaks)
+    assert "update_emu" in k and k["update_emu"]["flops"] == 36 * 2e12
+    assert abs(k["update_emu"]["fp64_equiv_tflops"] - 1.0) < 1e-12
+    assert abs(k["pivot"]["flops"] - 4e11) < 1.0
+    k = bench.evd_kernel_classes([st], dict(n=4096, b=64), peaks)
+    assert "update_fp64" in k and k["update_fp64"]["bound"] == "alu"
