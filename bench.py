@@ -486,6 +486,21 @@ def evd_kernel_classes(stats, wl, peaks):
     return cls
 
 
+def qr_precond_flops(m, n, nb=32):
+    """FP64-equivalent flops of the QR preconditioning as the library counts
+    them, split into the panel work (reflectors, T, Y T: always FP64) and the
+    blocked products (W = Y^T X and X -= (Y T) W for the trailing matrix
+    and for U = Q W), which run on the emulated tensor-core products when
+    those are on.  Leading terms: products 6 m n^2 - 8 n^3 / 3."""
+    panel = prod = 0.0
+    for j0 in range(0, n, nb):
+        nbp, rows = min(nb, n - j0), m - j0
+        nc = n - j0 - nbp
+        panel += 5.0 * rows * nbp * nbp + 2.0 * rows * nbp * nbp
+        prod += 4.0 * rows * nbp * nc + 4.0 * rows * nbp * n
+    return panel, prod
+
+
 def svd_kernel_classes(stats, wl, peaks):
     """Device time, issued flops and roofline of the one-sided solve's kernel
     classes (summed over the timed steps): Gram + column update, the Gram
@@ -514,6 +529,19 @@ def svd_kernel_classes(stats, wl, peaks):
                  peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); "
                             "flops = the 36 bf16 slice products issued",
                  fp64_equiv_tflops=(tot("flops_update") / (u["ms"] / 1e3) / 1e12 if u["ms"] > 0 else None))
+        if qr:
+            # the blocked products of the QR and of U = Q W are emulated, the
+            # panels stay FP64: the tensor pipe on the issued slice products
+            # over the whole class time (panel kernels included: a lower bound)
+            c = kernels["precond"]
+            panel, prod = qr_precond_flops(wl["m"], wl["n"])
+            c.update(kernel="k_house_vec + k_house_apply + k_gemm64 (FP64 panels) + k_emu_line_exps + k_emu_gemm_big + "
+                            "k_emu_sum_t (trailing, Q and Q W products, tcgen05, FP64-accurate)",
+                     flops=36 * prod * len(stats), flops_fp64_panels=panel * len(stats),
+                     bound="tensor", peak=peaks.get("bf16_tflops_sustained"),
+                     peak_basis="measured bf16 dense, sustained (MEASURED_PEAKS.json); flops = the 36 bf16 "
+                                "slice products issued, time = the whole class (FP64 panels included)",
+                     fp64_equiv_tflops=(tot("flops_precond") / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None))
     for c in kernels.values():
         c["achieved"] = c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None
         c["frac"] = c["achieved"] / c["peak"] if c["achieved"] and c["peak"] else None

@@ -163,6 +163,30 @@ def test_svd_kernel_classes_direct_qr_and_emulated():
     assert k["update"]["bound"] == "tensor" and k["update"]["flops"] == 36e12
     assert abs(k["update"]["fp64_equiv_tflops"] - 1.0) < 1e-12
     assert abs(k["pivot"]["flops"] - (1.7e12 - 5e11)) < 1.0     # emulated updates add no FP64 flops
+    # ... and the QR's blocked products: tensor-bound on their issued slice products
+    panel, prod = bench.qr_precond_flops(16384, 2048)
+    assert k["precond"]["bound"] == "tensor" and k["precond"]["flops"] == 36 * prod
+    assert k["precond"]["flops_fp64_panels"] == panel
+    assert abs(k["precond"]["fp64_equiv_tflops"] - 5e11 / 0.4 / 1e12) < 1e-12
+    k = bench.svd_kernel_classes([st], dict(m=16384, n=2048, b=64, svd_qr=1), peaks)
+    assert k["precond"]["bound"] == "alu" and k["precond"]["flops"] == 5e11
+
+
+@pytest.mark.parametrize("m,n", [(16384, 2048), (4096, 4096), (3000, 1000), (100, 37)])
+def test_qr_precond_flops_leading_terms(m, n):
+    """Householder QR with a blocked (compact WY) update plus U = Q W:
+    products 2 m n^2 - 2 n^3/3 (the factorisation) + 4 m n^2 - 2 n^3 (the
+    back-application), up to the panels' lower-order terms; panels
+    7 nb (m n - n^2 / 2) to leading order."""
+    nb = 32
+    panel, prod = bench.qr_precond_flops(m, n, nb)
+    lead = 6.0 * m * n * n - 8.0 * n ** 3 / 3.0
+    assert abs(prod - lead) <= 4.0 * nb * m * n + 4.0 * nb * n * n     # O(nb m n) correction
+    assert abs(panel - 7.0 * nb * (m * n - n * n / 2.0)) <= 7.0 * nb * nb * m
+    # exact count for one panel (n <= nb): no trailing matrix, back-application only
+    p1, q1 = bench.qr_precond_flops(m, min(n, nb), nb)
+    k = min(n, nb)
+    assert p1 == 7.0 * m * k * k and q1 == 4.0 * m * k * k
 
 
 def test_evd_kernel_classes_emulated_and_mixed():
