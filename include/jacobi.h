@@ -204,6 +204,21 @@ int jacobi_syev_h(int n, double* h_A, int lda, double* h_w, double* h_Q, int ldq
                   const jacobi_params* p, jacobi_stats* st, void* stream);
 
 /*
+ * jacobi_syev_f32 -- jacobi_syev for a matrix stored in FP32: A (n x n, lda
+ * >= n, lower triangle read), w (n floats) and Q (n x n, ldq >= n, or NULL
+ * when p->want_vectors == 0) are device FP32 buffers with the meaning, the
+ * ownership and the return codes of jacobi_syev.  The input is widened
+ * exactly to FP64 in library workspace, solved by jacobi_syev with the same
+ * parameters (p->precision FP64, a mixed form or FP64_EMU), and D, w and Q
+ * are rounded to FP32 once at the end (also when the sweep cap ends the
+ * call); on a negative return the caller's buffers are left as they were.
+ * With p->warm_start the FP32 Q is the (widened) start.  p->tol keeps its
+ * FP64 meaning: a value near 2^-24 stops at FP32 accuracy sooner.
+ */
+int jacobi_syev_f32(int n, float* A, int lda, float* w, float* Q, int ldq,
+                    const jacobi_params* p, jacobi_stats* st, void* stream);
+
+/*
  * jacobi_gesvd -- one-sided blocked Jacobi SVD of an m x n matrix, m >= n
  * (Algorithm 6 in the parallel order): the pivot of block-column pair (I,J)
  * is the Gram block G(:,[I,J])^T G(:,[I,J]) (Sec. 6, eq. (SVD_subproblem)),

@@ -112,6 +112,7 @@ SIGNATURES = {
     "jacobi_status_string": (C.c_char_p, [_I]),
     "jacobi_syev": (_I, [_I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
     "jacobi_syev_h": (_I, [_I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
+    "jacobi_syev_f32": (_I, [_I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
     "jacobi_gesvd": (_I, [_I, _I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
     "jacobi_gesvd_h": (_I, [_I, _I, _P, _I, _P, _P, _I, _PP, _SP, _P]),
     "jacobi_ordering_table": (_I, [_I, _I, _P, _P]),
@@ -224,6 +225,22 @@ def jacobi_syev_h(A, w, Q, p: jacobi_params | None = None, stream=None):
                              _colmajor_ld(Q) if Q is not None else n,
                              C.byref(p) if p is not None else None, C.byref(st),
                              _stream_ptr(stream))
+    return rc, _stats(st)
+
+
+def jacobi_syev_f32(A, w, Q, p: jacobi_params | None = None, stream=None):
+    """C ``jacobi_syev_f32`` on CUDA float32 tensors: same layout as
+    jacobi_syev (A column-major n x n, overwritten by D; w (n); Q or None)."""
+    import torch
+    for t in (A, w, Q):
+        if t is not None and t.dtype != torch.float32:
+            raise TypeError("jacobi_syev_f32 takes float32 tensors")
+    n = A.shape[0]
+    st = jacobi_stats()
+    rc = lib().jacobi_syev_f32(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
+                               _colmajor_ld(Q) if Q is not None else n,
+                               C.byref(p) if p is not None else None, C.byref(st),
+                               _stream_ptr(stream))
     return rc, _stats(st)
 
 

@@ -108,3 +108,28 @@ def test_binding_structs_mirror_the_header(jg, name):
     for (nm, ct, ln), (gnm, gty) in zip(want, got):
         base = ctmap[ct]
         assert gty == (base * ln if ln > 1 else base), nm
+
+
+@pytest.mark.parametrize("fn", ["jacobi_syev", "jacobi_syev_f32", "jacobi_syev_h"])
+def test_syev_argument_errors_come_before_any_device_work(jg, fn):
+    """The argument checks of the EVD entry points return -k (k the argument's
+    position) or JACOBI_ERR_UNSUPPORTED before touching the device, so they
+    run here without a GPU; the buffers are never dereferenced."""
+    f = getattr(jg.lib(), fn)
+    fake = C.c_void_p(0x1000)   # never dereferenced on these paths
+    null = C.c_void_p(0)
+    p = jg.params(b=16)
+
+    def call(n, A, lda, w, Q, ldq, prm):
+        return f(n, A, lda, w, Q, ldq, C.byref(prm), None, null)
+
+    assert call(0, fake, 4, fake, fake, 4, p) == -1
+    assert call(4, null, 4, fake, fake, 4, p) == -2
+    assert call(4, fake, 3, fake, fake, 4, p) == -3
+    assert call(4, fake, 4, null, fake, 4, p) == -4
+    assert call(4, fake, 4, fake, null, 4, p) == -5
+    assert call(4, fake, 4, fake, fake, 3, p) == -6
+    if fn != "jacobi_syev_h":   # the host-buffer form validates its parameters on the device path
+        for bad in (dict(b=0), dict(precision=9), dict(pivot_order=3), dict(tol=-1.0), dict(conv=4)):
+            assert call(4, fake, 4, fake, fake, 4, jg.params(**{"b": 16, **bad})) == -7, bad
+        assert call(4, fake, 4, fake, fake, 4, jg.params(b=129)) == jg.ERR_UNSUPPORTED

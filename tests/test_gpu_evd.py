@@ -300,6 +300,49 @@ def test_host_buffers_match_device(jg):
     assert np.array_equal(wh.numpy(), _np(w)) and np.array_equal(Qh.numpy(), _np(Q))
 
 
+def test_fp32_storage_is_the_fp64_solve_rounded_once(jg):
+    """jacobi_syev_f32: the FP32 matrix widened exactly, solved by the FP64
+    path, D, w and Q rounded once, i.e. bitwise the FP64 call on the widened
+    matrix rounded to FP32 (the FP64 path is deterministic).  Padding rows
+    of the leading dimensions hold NaN: they are neither read nor written."""
+    import torch
+    n = 150
+    A, lam = gen.sym_known(n, "uniform", seed=3700)
+    A32 = A.astype(np.float32)
+    Ad = _dev(A32.astype(np.float64))
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    Q = jg.colmajor_empty(n, n, torch.float64, "cuda")
+    rc, st = jg.jacobi_syev(Ad, w, Q, jg.params(b=16))
+    assert rc == 0
+    Ap = jg.colmajor_empty(n + 5, n, torch.float32, "cuda").fill_(float("nan"))
+    Qp = jg.colmajor_empty(n + 3, n, torch.float32, "cuda").fill_(float("nan"))
+    A32d, Q32 = Ap[:n], Qp[:n]
+    A32d.copy_(torch.from_numpy(A32))
+    w32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    rc32, st32 = jg.jacobi_syev_f32(A32d, w32, Q32, jg.params(b=16))
+    assert rc32 == 0 and st32.status == 0 and st32.sweeps == st.sweeps
+    assert torch.equal(w32, w.float()) and torch.equal(Q32, Q.float()) and torch.equal(A32d, Ad.float())
+    assert torch.isnan(Ap[n:]).all() and torch.isnan(Qp[n:]).all()
+    check(A32.astype(np.float64), _np(w32).astype(np.float64), _np(Q32).astype(np.float64),
+          np.sort(lam), eig=1e-6, res=1e-5, orth=1e-6)
+    # eigenvalues only
+    w32b = torch.empty(n, dtype=torch.float32, device="cuda")
+    B = jg.colmajor(A32, device="cuda", dtype=torch.float32)
+    rc, _ = jg.jacobi_syev_f32(B, w32b, None, jg.params(b=16, want_vectors=0))
+    assert rc == 0 and torch.allclose(w32b, w32, rtol=0, atol=1e-6)
+    # a non-finite entry: the error code, the caller's buffers untouched
+    A32[7, 3] = np.inf
+    C32 = jg.colmajor(A32, device="cuda", dtype=torch.float32)
+    C0 = C32.clone()
+    w0 = torch.full((n,), 5.0, dtype=torch.float32, device="cuda")
+    rc, st = jg.jacobi_syev_f32(C32, w0, Q32, jg.params(b=16))
+    assert rc == jg.ERR_NONFINITE and st.status == rc
+    assert torch.equal(C32.isinf(), C0.isinf()) and torch.equal(C32.nan_to_num(), C0.nan_to_num())
+    assert (w0 == 5.0).all()
+    with pytest.raises(TypeError):
+        jg.jacobi_syev_f32(Ad, w, Q, jg.params(b=16))
+
+
 # ------------------------------------------------------------------ full size (n = 4096, b = 64)
 def test_full_size_n4096_b64(jg):
     """The benchmark workload: first step element-wise against the oracle at
