@@ -518,21 +518,20 @@ extern "C" int jacobi_plan_execute(jacobi_plan* pl, void* const* A_or_G, void* c
         }
         pl->graph_info = info;
     }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    if (cudaMemsetAsync(pl->d_cnt, 0, sizeof(DevCounters), s) != cudaSuccess) return JACOBI_ERR_CUDA;
-    cudaEventRecord(e0, s);
-    if (cudaGraphLaunch(pl->exec, s) != cudaSuccess) return JACOBI_ERR_CUDA;
-    cudaEventRecord(e1, s);
     DevCounters hc;
-    if (cudaMemcpyAsync(&hc, pl->d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return JACOBI_ERR_CUDA;
+    const bool ok = cudaMemsetAsync(pl->d_cnt, 0, sizeof(DevCounters), s) == cudaSuccess &&
+                    cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(pl->exec, s) == cudaSuccess &&
+                    cudaEventRecord(e1, s) == cudaSuccess &&
+                    cudaMemcpyAsync(&hc, pl->d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                    cudaStreamSynchronize(s) == cudaSuccess;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (ok) cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!ok) return JACOBI_ERR_CUDA;
     pl->last_ms = ms;
     if (st) {
         memset(st, 0, sizeof(*st));
