@@ -52,7 +52,7 @@ U64 = 2.0 ** -53
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_BASIS = ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; "
-              "measured DFMA loop 1.197 TFLOP/s on this pool)")
+              "measured DFMA loop 1.197 TFLOP/s on a GB300)")
 FP32_BASIS = "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz (FP32 pipe)"
 
 

@@ -223,7 +223,7 @@ int jacobi_syev_f32(int n, float* A, int lda, float* w, float* Q, int ldq,
  * (Algorithm 6 in the parallel order): the pivot of block-column pair (I,J)
  * is the Gram block G(:,[I,J])^T G(:,[I,J]) (Sec. 6, eq. (SVD_subproblem)),
  * its eigenvectors rotate the column pair of G and of V; at exit
- * sigma_i = ||G(:,i)||_2 and U = G Sigma^+ (Algorithm 6, last two lines),
+ * sigma_i = ||G(:,i)||_2 and U = G Sigma^+ (the output step of Algorithm 6),
  * sorted descending.
  *
  *   G      device, m x n, ldg >= m; in: G, out: U (zero column for sigma = 0)

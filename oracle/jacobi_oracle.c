@@ -936,7 +936,7 @@ static double svd_step(int m, int np, int n_real, int b, double *G, int ldg, dou
     return mx;
 }
 
-/* SVD finalisation (Algorithm 6, last two lines): sigma_i = ||g_i||_2,
+/* SVD finalisation (the output step of Algorithm 6): sigma_i = ||g_i||_2,
  * u_i = g_i / sigma_i (0 when sigma_i == 0), sorted descending (stable). */
 static void finalize_svd(int m, int n, double *Gw, int ldgw, double *G, int ldg,
                          double *sigma, double *Vw, int ldvw, double *V, int ldv)
