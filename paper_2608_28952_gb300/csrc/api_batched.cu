@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batched.h"
+#include "batched_svd.h"
 
 using namespace jac;
 
@@ -139,6 +140,7 @@ struct jacobi_plan {
     cudaGraphExec_t exec = nullptr;
     int* graph_info = nullptr;        // info pointer baked into the graph
     int large_mode = 2;               // EVD orders above the smem size: 0 L2 slots, 1 clusters, 2 blocked
+    bool svd_tiled = false;           // one-sided: the row-tiled kernel (JACOBI_BATCHED_SVD=tiled)
     void* d_blk = nullptr;            // blocked-form slots
     size_t blk_slot = 0;
     int blk_grid = 0;
@@ -266,6 +268,7 @@ cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape&
     a.max_sweeps = pl->p.max_sweeps;
     a.inner_max_sweeps = pl->p.inner_max_sweeps;
     a.cnt = pl->d_cnt;
+    if (pl->svd_tiled) return launch_batched_svd_tiled<T>(a, pl->kmax, grid, sh.threads, s);
     return launch_batched_svd<T>(a, pl->kmax, grid, sh.threads, s);
 }
 
@@ -280,7 +283,8 @@ template <typename T>
 int occupancy_grid(jacobi_plan* pl, const Shape& sh)
 {
     const int per_sm = pl->kind == 0 ? batched_evd_occupancy<T>(sh.threads, sh.smem_kmax, pl->vec)
-                                     : batched_svd_occupancy<T>(sh.threads, pl->kmax);
+                       : pl->svd_tiled ? batched_svd_tiled_occupancy<T>(sh.threads, pl->kmax)
+                                       : batched_svd_occupancy<T>(sh.threads, pl->kmax);
     return device_sms() * std::max(1, std::min(per_sm, 4));
 }
 
@@ -322,6 +326,7 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
         if (!strcmp(env, "l2")) pl->large_mode = 0;
         else if (!strcmp(env, "cluster")) pl->large_mode = 1;
     }
+    if (const char* env = getenv("JACOBI_BATCHED_SVD")) pl->svd_tiled = kind == 1 && !strcmp(env, "tiled");
     if (precision == JACOBI_PREC_FP32 && p.inner_tol == 4.0 * U64) pl->p.inner_tol = 4.0 * U32;
     pl->h_n.assign(h_n, h_n + batch);
     pl->h_m = kind == 1 ? std::vector<int>(h_m, h_m + batch) : pl->h_n;

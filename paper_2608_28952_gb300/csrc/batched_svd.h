@@ -1,0 +1,27 @@
+// batched_svd.h -- the row-tiled variant of the batched one-sided SVD kernel.
+//
+// Same method, arguments, outputs and per-entry summation order as
+// k_batched_svd (so the two agree bit for bit); the Gram blocks, the column
+// rotations of G and V and the final column norms are formed from row tiles
+// of G staged in shared memory (each element of G read once per pass
+// instead of once per Gram entry, coalesced) with register-blocked
+// products.  Selected by the plan when JACOBI_BATCHED_SVD=tiled.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "batched.h"
+
+namespace jac {
+
+constexpr int kSvdTileRows = 64;                  // rows of G per staged tile
+constexpr int kSvdTileLd = kSvdTileRows + 1;      // odd: conflict-free column reads
+
+template <typename T>
+size_t batched_svd_tiled_smem(int kmax);
+template <typename T>
+int batched_svd_tiled_occupancy(int threads, int kmax);
+template <typename T>
+cudaError_t launch_batched_svd_tiled(const BatchedSvdArgs<T>& a, int kmax, int grid, int threads,
+                                     cudaStream_t s);
+
+}  // namespace jac

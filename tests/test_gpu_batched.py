@@ -10,6 +10,8 @@ against the FP64 oracle with the FP64 bounds scaled by u32/u64 = 2^29
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -140,6 +142,33 @@ def test_batched_tall_svd_f32(jg):
         assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * SCALE32 * n
         assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-13 * SCALE32 * n
         assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-12 * SCALE32 * np.linalg.norm(G)
+
+
+@pytest.mark.skipif(os.environ.get("JACOBI_TEST_TILED_SVD") != "1",
+                    reason="row-tiled batched SVD kernel: opt-in (JACOBI_TEST_TILED_SVD=1)")
+def test_batched_tall_svd_tiled_is_bitwise_the_default(jg, monkeypatch):
+    """The row-tiled kernel (JACOBI_BATCHED_SVD=tiled) keeps every output's
+    FMA chain in the default kernel's order: sigma, U, V and info agree bit
+    for bit over a batch of tall, square, ragged and odd shapes."""
+    import torch
+    shapes = [(1024, 64)] * 6 + [(300, 40), (100, 100), (64, 1), (77, 33), (2, 2), (129, 65), (1000, 7)]
+    mats = [gen.tall_gaussian(m, n, 78, i, dtype=np.float64) for i, (m, n) in enumerate(shapes)]
+    outs = []
+    for variant in ("default", "tiled"):
+        if variant == "tiled":
+            monkeypatch.setenv("JACOBI_BATCHED_SVD", "tiled")
+        else:
+            monkeypatch.delenv("JACOBI_BATCHED_SVD", raising=False)
+        Gs = [jg.colmajor(g, device="cuda", dtype=torch.float32) for g in mats]
+        ss = [torch.empty(g.shape[1], dtype=torch.float32, device="cuda") for g in mats]
+        Vs = [jg.colmajor_empty(g.shape[1], g.shape[1], torch.float32, "cuda") for g in mats]
+        info = torch.full((len(mats),), -7, dtype=torch.int32, device="cuda")
+        rc, st = jg.jacobi_gesvd_batched_f32(Gs, ss, Vs, info, jg.params())
+        assert rc == 0 and torch.all(info == 0), (variant, info)
+        outs.append((Gs, ss, Vs))
+    for a, b in zip(outs[0], outs[1]):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
 
 
 @pytest.mark.parametrize("f32", [False, True])
