@@ -209,6 +209,24 @@ def test_graded_dhd_relative_criterion(jg):
 
 
 # ------------------------------------------------------------------ edge cases
+def test_clustered_eigenvalues_invariant_subspace(jg):
+    """Five eigenvalues within 1e-12 of each other (gap 0.5 to the rest): the
+    eigenvalues and the cluster's invariant subspace (its projector, which
+    is unique where the vectors are not) against the constructed ones."""
+    n, m = 200, 5
+    r = gen.rng(3800)
+    Qt = gen.haar_q(n, n, r)
+    lam = np.concatenate([1.0 + 1e-12 * np.arange(m), r.uniform(-1.0, 0.5, n - m)])
+    A = (Qt * lam[None, :]) @ Qt.T
+    A = np.asfortranarray(0.5 * (A + A.T))
+    w, Q, _, st = jg.syev(A, b=16)
+    w, Q = _np(w), _np(Q)
+    assert st.status == 0
+    check(A, w, Q, np.sort(lam))
+    P = Q[:, -m:] @ Q[:, -m:].T
+    assert np.linalg.norm(P - Qt[:, :m] @ Qt[:, :m].T, 2) <= 1e-12
+
+
 def test_diagonal_input_no_rotation(jg):
     d = np.linspace(-2, 3, 40)
     w, Q, D, st = jg.syev(np.diag(d), b=8)

@@ -122,6 +122,32 @@ def test_known_spectrum_blocked(b, ordering, kind):
     assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * n
 
 
+def _clustered(n, seed, width=1e-12, m=5):
+    """A = Q diag(lam) Q^T with m eigenvalues within `width` of 1 and the rest
+    in [-1, 0.5] (gap 0.5 to the cluster); returns A, lam, the cluster's basis."""
+    r = gen.rng(seed)
+    Q = gen.haar_q(n, n, r)
+    lam = np.concatenate([1.0 + width * np.arange(m), r.uniform(-1.0, 0.5, n - m)])
+    A = (Q * lam[None, :]) @ Q.T
+    return np.asfortranarray(0.5 * (A + A.T)), lam, Q[:, :m]
+
+
+@pytest.mark.parametrize("scalar,b", [(False, 4), (True, 1)])
+def test_clustered_eigenvalues_invariant_subspace(scalar, b):
+    """Within a tight cluster the eigenvectors are not unique but the
+    invariant subspace is: its projector matches the constructed one within
+    the perturbation bound u ||A|| / gap (Davis-Kahan sin-theta), and every
+    eigenvalue matches within 1e-13 ||A||_2."""
+    n, m = 40, 5
+    A, lam, Qc = _clustered(n, 31, m=m)
+    w, Q, Af, st, status = oracle.syev(A, b=b, scalar=scalar)
+    assert status == 0
+    assert np.abs(w - np.sort(lam)).max() <= 1e-13
+    P = Q[:, -m:] @ Q[:, -m:].T
+    assert np.linalg.norm(P - Qc @ Qc.T, 2) <= 1e-12
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * n
+
+
 def test_known_spectrum_scalar():
     n = 48
     A, lam = gen.sym_known(n, "uniform", seed=22)
