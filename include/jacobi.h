@@ -295,6 +295,8 @@ int jacobi_gesvd_step(int m, int np, double* G, int ldg, double* V, int ldv,
  * = tight).  info: DEVICE array of batch ints: 0 converged, >0 sweeps run
  * without converging, -100 non-finite input.  A is read only (lower
  * triangle); w ascending; Q (or NULL when p->want_vectors == 0) eigenvectors.
+ * Argument errors carry jacobi_plan_create_batched's codes: -4 batch < 1,
+ * -6 h_n (NULL, or some n outside 1..512), -7 a leading dimension too small.
  */
 int jacobi_syev_batched(int batch, const int* h_n, double* const* A, const int* h_lda,
                         double* const* w, double* const* Q, const int* h_ldq,
@@ -304,11 +306,15 @@ int jacobi_syev_batched_f32(int batch, const int* h_n, float* const* A, const in
                             const jacobi_params* p, int* info, jacobi_stats* st, void* stream);
 
 /* Batched one-sided SVD (Algorithm 6 with a single column-block pair): each
- * sweep forms the n x n Gram block of G (m x n, m >= n, n <= 64 for the
- * shared-memory path on GB300), solves it with the FP32 Jacobi core, sorts its
- * eigenpairs descending and rotates G's columns and V.  Stop: the Gram's
- * largest normalised off-diagonal <= max(p->tol, sqrt(m) 2^-24), or a sweep
- * without rotation.  G is overwritten by U; sigma descending. */
+ * sweep forms the n x n Gram block of G (m x n, m >= n, m n < 2^31; the
+ * Gram, V-hat and the accumulated V live in shared memory, which bounds n at
+ * 124 on GB300: larger n returns JACOBI_ERR_UNSUPPORTED), solves it with the
+ * FP32 Jacobi core, sorts its eigenpairs descending and rotates G's columns
+ * and V.  Stop: the Gram's largest normalised off-diagonal <= max(p->tol,
+ * sqrt(m) 2^-24), or a sweep without rotation.  G is overwritten by U; sigma
+ * descending.  Argument errors carry jacobi_plan_create_batched's codes:
+ * -4 batch < 1, -5 h_m (NULL, or some m n >= 2^31), -6 h_n (some n < 1,
+ * n > 512 or n > m), -7 a leading dimension too small. */
 int jacobi_gesvd_batched_f32(int batch, const int* h_m, const int* h_n, float* const* G,
                              const int* h_ldg, float* const* sigma, float* const* V,
                              const int* h_ldv, const jacobi_params* p, int* info,

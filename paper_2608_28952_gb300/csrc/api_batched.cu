@@ -335,6 +335,7 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
     for (int i = 0; i < batch; ++i) {
         const int n = pl->h_n[i], m = pl->h_m[i];
         if (n < 1 || n > kBatchedMaxK || m < n) { delete pl; return -6; }
+        if ((long long)m * n > 0x7fffffffLL) { delete pl; return -5; }   // kernels index m x n in int
         pl->h_lda[i] = h_lda ? h_lda[i] : m;
         pl->h_ldq[i] = h_ldq ? h_ldq[i] : n;
         if (pl->h_lda[i] < m || (pl->vec && pl->h_ldq[i] < n)) { delete pl; return -7; }

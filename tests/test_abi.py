@@ -133,3 +133,37 @@ def test_syev_argument_errors_come_before_any_device_work(jg, fn):
         for bad in (dict(b=0), dict(precision=9), dict(pivot_order=3), dict(tol=-1.0), dict(conv=4)):
             assert call(4, fake, 4, fake, fake, 4, jg.params(**{"b": 16, **bad})) == -7, bad
         assert call(4, fake, 4, fake, fake, 4, jg.params(b=129)) == jg.ERR_UNSUPPORTED
+
+
+def test_batched_argument_errors_come_before_any_device_work(jg):
+    """The batched calls validate sizes on the host before any CUDA call,
+    with jacobi_plan_create_batched's codes: -4 batch, -5 h_m (one-sided:
+    NULL or m n >= 2^31, the kernels' int index range), -6 h_n, -7 a
+    leading dimension."""
+    L = jg.lib()
+    null = C.c_void_p(0)
+    fake = C.c_void_p(0x1000)       # pointer arrays: never read on these paths
+    p = jg.params()
+
+    def ints(*v):
+        return (C.c_int * len(v))(*v)
+
+    def svd(batch, hm, hn, hld=None):
+        return L.jacobi_gesvd_batched_f32(batch, hm, hn, fake, hld, fake, fake, None, C.byref(p),
+                                          fake, None, null)
+
+    def evd(batch, hn, hld=None):
+        return L.jacobi_syev_batched(batch, hn, fake, hld, fake, fake, None, C.byref(p), fake, None, null)
+
+    assert svd(0, ints(8), ints(4)) == -4
+    assert svd(1, None, ints(4)) == -5
+    assert svd(1, ints(1 << 26), ints(64)) == -5           # m n = 2^32
+    assert svd(2, ints(100, 40000000), ints(10, 60)) == -5  # one matrix past the int range
+    assert svd(1, ints(8), None) == -6
+    assert svd(1, ints(8), ints(9)) == -6                   # n > m
+    assert svd(1, ints(8), ints(0)) == -6
+    assert svd(1, ints(8), ints(4), ints(7)) == -7          # ldg < m
+    assert evd(0, ints(4)) == -4
+    assert evd(1, None) == -6
+    assert evd(1, ints(513)) == -6
+    assert evd(1, ints(5), ints(4)) == -7
