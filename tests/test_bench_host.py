@@ -80,9 +80,10 @@ def test_padding_and_update_flops():
 
 
 def _stats(**kw):
-    base = dict(sweeps_lowp=0, ms_pivot=0.0, pivot_launches=0, flops_fp64=0.0, flops_update=0.0,
-                flops_refine=0.0, ms_update=0.0, ms_update_lowp=0.0, update_launches=0,
-                flops_lowp=0.0, ms_refine=0.0)
+    """A stand-in for the library's Stats with every field the accounting reads."""
+    base = dict(ms_update=0.0, update_launches=0, flops_update=0.0, ms_pivot=0.0, pivot_launches=0,
+                flops_fp64=0.0, flops_precond=0.0, ms_precond=0.0, flops_lowp=0.0, ms_update_lowp=0.0,
+                sweeps_lowp=0, ms_refine=0.0, flops_refine=0.0)
     base.update(kw)
     return SimpleNamespace(**base)
 
@@ -138,14 +139,6 @@ def test_new_workloads_carry_their_options():
     assert bench.WORKLOADS["mixed8192emu"]["fp64_products"] == 1
 
 
-def _stats(**kw):
-    base = dict(ms_update=0.0, update_launches=0, flops_update=0.0, ms_pivot=0.0, pivot_launches=0,
-                flops_fp64=0.0, flops_precond=0.0, ms_precond=0.0, flops_lowp=0.0, ms_update_lowp=0.0,
-                sweeps_lowp=0, ms_refine=0.0, flops_refine=0.0)
-    base.update(kw)
-    return SimpleNamespace(**base)
-
-
 def test_svd_kernel_classes_direct_qr_and_emulated():
     peaks = {"bf16_tflops_sustained": 1688.5}
     st = _stats(ms_update=1000.0, update_launches=620, flops_update=1e12, ms_pivot=500.0, pivot_launches=310,
@@ -199,3 +192,26 @@ def test_evd_kernel_classes_emulated_and_mixed():
     assert abs(k["pivot"]["flops"] - 4e11) < 1.0
     k = bench.evd_kernel_classes([st], dict(n=4096, b=64), peaks)
     assert "update_fp64" in k and k["update_fp64"]["bound"] == "alu"
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` runs the oracle on the host (no GPU) and
+    prints one JSON line with the contract's keys, the oracle described in
+    cpu_baseline and an e2e entry without copies."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "evd256", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("plain FP64") and "n=256" in d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
