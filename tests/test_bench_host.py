@@ -68,6 +68,10 @@ def test_workloads_are_complete():
     assert bench.WORKLOADS["mixed8192"]["n"] == 8192 and bench.WORKLOADS["mixed8192"]["b"] == 128
     assert bench.WORKLOADS["batched_f64"]["count"] == 20000
     assert bench.WORKLOADS["batched_svd_f32"]["count"] == 4096
+    # the reference arm extrapolates by the oracle's own sweep count on each input
+    for name, wl in bench.WORKLOADS.items():
+        if wl["kind"] in ("evd", "svd"):
+            assert isinstance(wl.get("ref_sweeps"), int) and wl["ref_sweeps"] >= 1, name
 
 
 def test_padding_and_update_flops():
