@@ -16,7 +16,9 @@ transposed V, a wrong index in the ordering -- fails at least one of them:
 * the paper's printed ordering list, label matrix and transformation
   patterns (Sec. 3, eqs. (disjoint), (group_one_transformation),
   (alt_transformations), (parallel_list); Algorithm 3);
-* Gram block as a sum over row tiles (Sec. 6, eq. after (SVD_subproblem)).
+* Gram block as a sum over row tiles (Sec. 6, eq. after (SVD_subproblem));
+* tight clusters: the invariant (singular) subspaces' projectors against the
+  constructed ones within the Davis-Kahan / Wedin perturbation bound.
 """
 from __future__ import annotations
 
@@ -551,6 +553,27 @@ def test_known_singular_values(scalar, b):
     assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
     assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
     assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-13 * np.linalg.norm(G)
+
+
+@pytest.mark.parametrize("qr", [False, True])
+def test_clustered_singular_values_subspaces(qr):
+    """Four singular values within 1e-12 of each other (gap 0.5 to the
+    rest): the right and left singular subspaces of the cluster (their
+    projectors) match the constructed ones within u ||G|| / gap, direct and
+    QR-preconditioned."""
+    m, n, c = 160, 30, 4
+    r = gen.rng(83)
+    Uc = gen.haar_q(m, n, r)
+    Vc = gen.haar_q(n, n, r)
+    sig = np.concatenate([1.0 + 1e-12 * np.arange(c)[::-1], r.uniform(0.01, 0.5, n - c)])
+    G = np.asfortranarray((Uc * sig[None, :]) @ Vc.T)
+    U, s, V, st, status = (oracle.gesvd_qr if qr else oracle.gesvd)(G, b=5)
+    assert status == 0
+    assert np.abs(s - np.sort(sig)[::-1]).max() <= 1e-13
+    PV = V[:, :c] @ V[:, :c].T
+    PU = U[:, :c] @ U[:, :c].T
+    assert np.linalg.norm(PV - Vc[:, :c] @ Vc[:, :c].T, 2) <= 1e-12
+    assert np.linalg.norm(PU - Uc[:, :c] @ Uc[:, :c].T, 2) <= 1e-12
 
 
 @pytest.mark.parametrize("transpose,m,n,b", [(True, 200, 40, 4), (False, 200, 40, 4), (True, 60, 60, 6),
