@@ -81,7 +81,8 @@ extern "C" {
 
 typedef struct {
     int b;                /* block size, 1 <= b <= 128; n need not be a multiple
-                             (zero padding, exact: see the design notes)       */
+                             (zero padding, exact: a zero row and column is
+                             never rotated)                                    */
     int ordering;         /* JACOBI_ORDER_*                                     */
     int max_sweeps;       /* outer sweep cap (default 30)                       */
     int inner_max_sweeps; /* cap on the sweeps of one pivot solve; a small cap

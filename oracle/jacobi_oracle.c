@@ -7,6 +7,12 @@
  * (the CUDA library) never calls it, and it shares no code, header, table or
  * constant generator with the product.
  *
+ * Every public function is pinned against facts from outside this file
+ * (closed forms, printed tables, constructed spectra, exact roots, LAPACK,
+ * mpmath) in tests/test_oracle_pins.py, and tests/test_oracle_mutants.py
+ * plants plausible mistakes in copies of this file to show the pins catch
+ * them; no function is parity-unpinned.
+ *
  * What is computed, and where the paper defines it
  * (Demmel, Luo, Schneider, Wang, "Minimizing the Arithmetic and Communication
  *  Complexity of Jacobi's Method ... Part Two -- Parallel Algorithms"):
@@ -34,7 +40,7 @@
  *     G(:,[I,J]) <- G(:,[I,J]) Vhat, V likewise; Sigma = column norms,
  *     U = G Sigma^+                                                    Algorithm 6, Sec. 6
  *
- * Readings where the paper is silent (stated in full in the design notes):
+ * Readings where the paper is silent:
  *   - round-robin: block 0 fixed, positions 1..N-1 rotate by one per step;
  *     step s pairs position k with position N-1-k;
  *   - anti-diagonal groups are emitted in the order K = 0..N-1;
