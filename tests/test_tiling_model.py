@@ -1,6 +1,7 @@
 """CPU model of the index arithmetic of the row-tiled batched one-sided SVD
 kernel (k_batched_svd_tiled: the Gram from 4 x 4 blocks of staged 64-row
-tiles, svd_rotate_rows, the column permutation), with the threads of a CTA
+tiles, svd_rotate_rows with its column permutation, and the finalisation:
+column norms, their descending rank, U = G Sigma^+), with the threads of a CTA
 run one after another between its barriers.  Every access goes to a flat
 buffer of exactly the size the kernel allocates (the caller's minimal G
 buffer ld * (n - 1) + m, the tile kSvdTileLd x kq, V-hat and the accumulated
@@ -122,6 +123,38 @@ def rotate(X, ldx, rows, n, k, Vh, dest, kq, nt):
             X[i] = v
 
 
+def finalize(G, ldg, m, n, kq, nt):
+    """The kernel's finalisation: column norms over staged tiles (one FMA
+    chain per column in row order), the descending stable rank, and
+    G(:, dest[j]) <- G(:, j) / norm_j over staged tiles."""
+    tile = Buf(TRS * kq, "tile")
+    nrm = Buf(tri_pad(kq), "nrm")          # the packed-Gram area, reused
+    for j in range(n):
+        nrm[j] = 0.0
+    for r0 in range(0, m, TR):
+        tr = min(TR, m - r0)
+        for idx in range(tr * n):
+            rr, c = idx % tr, idx // tr
+            tile[c * TRS + rr] = G[(r0 + rr) + ldg * c]
+        for j in range(n):
+            acc = nrm[j]
+            for rr in range(tr):
+                acc += tile[j * TRS + rr] * tile[j * TRS + rr]
+            nrm[j] = acc
+    norms = [math.sqrt(nrm[j]) for j in range(n)]
+    dest = [sum(1 for y in range(n) if norms[y] > norms[x] or (norms[y] == norms[x] and y < x))
+            for x in range(n)]
+    for r0 in range(0, m, TR):
+        tr = min(TR, m - r0)
+        for idx in range(tr * n):
+            rr, c = idx % tr, idx // tr
+            tile[c * TRS + rr] = G[(r0 + rr) + ldg * c]
+        for idx in range(tr * n):
+            rr, j = idx % tr, idx // tr
+            G[(r0 + rr) + ldg * dest[j]] = tile[j * TRS + rr] / norms[j] if norms[j] > 0 else 0.0
+    return norms, dest
+
+
 def _check(m, n, ldg_pad, nt, seed):
     rng = np.random.default_rng(seed)
     k = n + (n & 1)
@@ -162,6 +195,17 @@ def _check(m, n, ldg_pad, nt, seed):
     for j in range(n):
         for i in range(n):
             assert abs(Vacc[i + k * dest[j]] - V[i, j]) <= 1e-12
+    # finalisation of the rotated G: sigma = column norms, U = G Sigma^+ sorted
+    R = np.array([[G[r + ldg * c] for c in range(n)] for r in range(m)])
+    norms, dest2 = finalize(G, ldg, m, n, kq, nt)
+    want = np.linalg.norm(R, axis=0)
+    assert np.allclose(norms, want, rtol=1e-12, atol=0)
+    assert sorted(dest2) == list(range(n))
+    order = np.argsort(-want, kind="stable")
+    for pos, j in enumerate(order):
+        assert dest2[j] == pos
+        for r in range(m):
+            assert abs(G[r + ldg * pos] - R[r, j] / want[j]) <= 1e-12
 
 
 @pytest.mark.parametrize("m,n,ldg_pad,nt,seed", [
