@@ -15,22 +15,36 @@ namespace jac {
 
 constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 
-// Stream-ordered workspace that is released when the call returns.
+// Stream-ordered workspace that is released when the call returns.  The
+// environment variable JACOBI_WORKSPACE_LIMIT=<bytes> caps what one
+// Workspace may hold (host-side fault injection: the call then returns
+// JACOBI_ERR_ALLOC before it launches anything, as on a real allocation
+// failure).
 struct Workspace {
     cudaStream_t s;
     std::vector<void*> ptrs;
     bool failed = false;
-    explicit Workspace(cudaStream_t st) : s(st) {}
+    size_t used = 0, limit = (size_t)-1;
+    explicit Workspace(cudaStream_t st) : s(st)
+    {
+        if (const char* e = getenv("JACOBI_WORKSPACE_LIMIT")) limit = (size_t)strtoull(e, nullptr, 10);
+    }
     template <class T>
     T* get(size_t count)
     {
         if (count == 0) count = 1;
+        const size_t bytes = count * sizeof(T);
+        if (failed || bytes > limit - used) {
+            failed = true;
+            return nullptr;
+        }
         void* p = nullptr;
-        if (cudaMallocAsync(&p, count * sizeof(T), s) != cudaSuccess) {
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
             failed = true;
             cudaGetLastError();
             return nullptr;
         }
+        used += bytes;
         ptrs.push_back(p);
         return (T*)p;
     }

@@ -167,3 +167,21 @@ def test_batched_argument_errors_come_before_any_device_work(jg):
     assert evd(1, None) == -6
     assert evd(1, ints(513)) == -6
     assert evd(1, ints(5), ints(4)) == -7
+
+
+@pytest.mark.parametrize("fn", ["jacobi_syev", "jacobi_syev_f32", "jacobi_gesvd"])
+def test_workspace_fault_injection_returns_alloc_before_any_launch(jg, fn, monkeypatch):
+    """JACOBI_WORKSPACE_LIMIT caps one call's workspace: the drivers check the
+    allocation before their first launch and return JACOBI_ERR_ALLOC, so this
+    runs here without a GPU (the device pointers are never dereferenced)."""
+    monkeypatch.setenv("JACOBI_WORKSPACE_LIMIT", "16")
+    f = getattr(jg.lib(), fn)
+    fake = C.c_void_p(0x1000)
+    p = jg.params(b=16)
+    st = jg.jacobi_stats()
+    if fn == "jacobi_gesvd":
+        rc = f(200, 64, fake, 200, fake, fake, 64, C.byref(p), C.byref(st), C.c_void_p(0))
+    else:
+        rc = f(64, fake, 64, fake, fake, 64, C.byref(p), C.byref(st), C.c_void_p(0))
+    assert rc == jg.ERR_ALLOC
+    assert st.status == jg.ERR_ALLOC

@@ -268,6 +268,26 @@ def test_nonfinite_and_bad_arguments(jg):
     assert jg.jacobi_syev(_dev(A), w, Q, jg.params(ordering=5))[0] == -7
 
 
+def test_workspace_fault_injection_leaves_the_context_usable(jg, monkeypatch):
+    """A workspace cap (JACOBI_WORKSPACE_LIMIT, host-side fault injection)
+    makes the call return JACOBI_ERR_ALLOC before any launch, with the
+    caller's buffers untouched; the next call without the cap succeeds."""
+    import torch
+    A, lam = gen.sym_known(64, "uniform", seed=3900)
+    Ad = _dev(A)
+    A0 = Ad.clone()
+    w = torch.full((64,), 7.0, dtype=torch.float64, device="cuda")
+    Q = jg.colmajor_empty(64, 64, torch.float64, "cuda")
+    monkeypatch.setenv("JACOBI_WORKSPACE_LIMIT", "4096")
+    rc, st = jg.jacobi_syev(Ad, w, Q, jg.params(b=16))
+    assert rc == jg.ERR_ALLOC and st.status == rc
+    assert torch.equal(Ad, A0) and bool((w == 7.0).all())
+    monkeypatch.delenv("JACOBI_WORKSPACE_LIMIT")
+    rc, st = jg.jacobi_syev(Ad, w, Q, jg.params(b=16))
+    assert rc == 0
+    check(A, _np(w), _np(Q), np.sort(lam))
+
+
 def test_leading_dimension_and_no_vectors(jg):
     import torch
     n, ld = 50, 64
