@@ -26,6 +26,18 @@
  *     cluster of up to 8 CTAs per pair (chosen automatically); the
  *     environment variable JACOBI_PIVOT_CLUSTER=1 forces one CTA per pair,
  *     =2/4/8 that cluster size where it fits.
+ *
+ * Environment switches (read at each call; none is needed):
+ *   JACOBI_PIVOT_CLUSTER=1|2|4|8   pivot cluster size (above);
+ *   JACOBI_BATCHED_LARGE=blocked|cluster|l2   route of the batched EVD
+ *                                  orders above the shared-memory size
+ *                                  (default blocked);
+ *   JACOBI_BATCHED_SVD=tiled       the row-tiled batched one-sided SVD
+ *                                  kernel (same results bit for bit);
+ *   JACOBI_TUNE_CACHE=<path>       file of the batched autotuner's cache;
+ *   JACOBI_WORKSPACE_LIMIT=<bytes> cap on one call's workspace (fault
+ *                                  injection: JACOBI_ERR_ALLOC before any
+ *                                  launch).
  */
 #ifndef JACOBI_GB300_H
 #define JACOBI_GB300_H
