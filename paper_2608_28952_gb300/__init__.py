@@ -203,11 +203,27 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def _need(dtype: str, device: str, *tensors):
+    """Raise before the C call when a tensor's element type or memory space is
+    not the one the entry point reads: the C side receives bare pointers and
+    cannot tell (a float32 buffer read as float64 runs past its end)."""
+    import torch
+    want = getattr(torch, dtype)
+    for t in tensors:
+        if t is None:
+            continue
+        if t.dtype != want:
+            raise TypeError(f"expected {dtype} tensors, got {t.dtype}")
+        if t.device.type != device:
+            raise ValueError(f"expected tensors on {device}, got {t.device}")
+
+
 # ------------------------------------------------------------------ C-ABI names
 def jacobi_syev(A, w, Q, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_syev`` on CUDA tensors: A (n x n, column-major, float64,
     overwritten by D), w (n), Q (n x n column-major or None).
     Returns (status, Stats)."""
+    _need("float64", "cuda", A, w, Q)
     n = A.shape[0]
     st = jacobi_stats()
     rc = lib().jacobi_syev(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
@@ -219,6 +235,7 @@ def jacobi_syev(A, w, Q, p: jacobi_params | None = None, stream=None):
 def jacobi_syev_h(A, w, Q, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_syev_h`` on HOST buffers (torch CPU tensors, ideally
     pinned): same layout as jacobi_syev."""
+    _need("float64", "cpu", A, w, Q)
     n = A.shape[0]
     st = jacobi_stats()
     rc = lib().jacobi_syev_h(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
@@ -231,10 +248,7 @@ def jacobi_syev_h(A, w, Q, p: jacobi_params | None = None, stream=None):
 def jacobi_syev_f32(A, w, Q, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_syev_f32`` on CUDA float32 tensors: same layout as
     jacobi_syev (A column-major n x n, overwritten by D; w (n); Q or None)."""
-    import torch
-    for t in (A, w, Q):
-        if t is not None and t.dtype != torch.float32:
-            raise TypeError("jacobi_syev_f32 takes float32 tensors")
+    _need("float32", "cuda", A, w, Q)
     n = A.shape[0]
     st = jacobi_stats()
     rc = lib().jacobi_syev_f32(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
@@ -247,6 +261,7 @@ def jacobi_syev_f32(A, w, Q, p: jacobi_params | None = None, stream=None):
 def jacobi_gesvd(G, sigma, V, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_gesvd`` on CUDA tensors: G (m x n column-major float64, out:
     U), sigma (n), V (n x n or None).  Returns (status, Stats)."""
+    _need("float64", "cuda", G, sigma, V)
     m, n = G.shape
     st = jacobi_stats()
     rc = lib().jacobi_gesvd(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
@@ -256,6 +271,7 @@ def jacobi_gesvd(G, sigma, V, p: jacobi_params | None = None, stream=None):
 
 
 def jacobi_gesvd_h(G, sigma, V, p: jacobi_params | None = None, stream=None):
+    _need("float64", "cpu", G, sigma, V)
     m, n = G.shape
     st = jacobi_stats()
     rc = lib().jacobi_gesvd_h(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
@@ -268,6 +284,7 @@ def jacobi_gesvd_h(G, sigma, V, p: jacobi_params | None = None, stream=None):
 def jacobi_syev_step(A, Q, step: int, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_syev_step``: one parallel step in place on the full
     symmetric np x np column-major CUDA tensor A (and Q or None)."""
+    _need("float64", "cuda", A, Q)
     np_ = A.shape[0]
     return lib().jacobi_syev_step(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                   _colmajor_ld(Q) if Q is not None else np_,
@@ -279,6 +296,7 @@ def jacobi_syev_step_noalloc(A, Q, step: int, p: jacobi_params | None = None, st
     """C ``jacobi_syev_step_noalloc``: ``jacobi_syev_step`` for callers that
     cannot allocate device memory (np <= 768, b <= 128); the library keeps its
     working buffers in one fixed device array instead."""
+    _need("float64", "cuda", A, Q)
     np_ = A.shape[0]
     return lib().jacobi_syev_step_noalloc(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                           _colmajor_ld(Q) if Q is not None else np_,
@@ -289,6 +307,7 @@ def jacobi_syev_step_noalloc(A, Q, step: int, p: jacobi_params | None = None, st
 def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=None):
     """C ``jacobi_gesvd_step``: one one-sided step in place on G (m x np) and
     V (np x np or None).  Returns (status, relmax)."""
+    _need("float64", "cuda", G, V)
     m, np_ = G.shape
     r = C.c_double(0.0)
     rc = lib().jacobi_gesvd_step(m, np_, _ptr(G), _colmajor_ld(G), _ptr(V),
@@ -301,6 +320,7 @@ def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=No
 def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
     """C ``jacobi_lowp_gemm``: C = op(A) B (FP32, column-major CUDA tensors)
     on the tensor cores with bf16 hi/lo operand splits."""
+    _need("float32", "cuda", A, B, C)
     K, N = B.shape
     M = C.shape[0]
     return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
@@ -311,6 +331,7 @@ def jacobi_rotation_params(app, aqq, apq, tol: float, out, stream=None):
     """C ``jacobi_rotation_params``: for each triple, out[i] = (t, s, tau,
     rotate) as the FP64 pivot solves compute them, then the same four by the
     textbook formulas (contiguous FP64 CUDA tensors; out is count x 8)."""
+    _need("float64", "cuda", app, aqq, apq, out)
     return lib().jacobi_rotation_params(app.numel(), _ptr(app), _ptr(aqq), _ptr(apq), float(tol), _ptr(out),
                                         _stream_ptr(stream))
 
@@ -318,6 +339,7 @@ def jacobi_rotation_params(app, aqq, apq, tol: float, out, stream=None):
 def jacobi_f64emu_gemm(A, B, C, transA: bool = False, stream=None):
     """C ``jacobi_f64emu_gemm``: C = op(A) B (FP64, column-major CUDA tensors,
     K <= 256) on the tensor cores from eight bf16 slices per operand."""
+    _need("float64", "cuda", A, B, C)
     K, N = B.shape
     M = C.shape[0]
     return lib().jacobi_f64emu_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
@@ -328,6 +350,7 @@ def jacobi_syev_step_lowp(A, Q, step: int, p: jacobi_params | None = None, strea
     """C ``jacobi_syev_step_lowp``: one low-precision step of the mixed form
     in place on FP32 column-major CUDA tensors A (np x np, symmetric) and Q
     (or None); p.precision must be JACOBI_PREC_MIXED_BF16X3."""
+    _need("float32", "cuda", A, Q)
     np_ = A.shape[0]
     return lib().jacobi_syev_step_lowp(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                        _colmajor_ld(Q) if Q is not None else np_,
@@ -441,6 +464,8 @@ class Plan:
 
 def jacobi_syev_batched(As, ws, Qs, info, p=None, stream=None, f32=False):
     """C ``jacobi_syev_batched`` / ``_f32`` on lists of column-major CUDA tensors."""
+    _need("float32" if f32 else "float64", "cuda", *As, *ws, *(Qs or []))
+    _need("int32", "cuda", info)
     n = [a.shape[0] for a in As]
     st = jacobi_stats()
     f = lib().jacobi_syev_batched_f32 if f32 else lib().jacobi_syev_batched
@@ -454,6 +479,8 @@ def jacobi_syev_batched(As, ws, Qs, info, p=None, stream=None, f32=False):
 
 def jacobi_gesvd_batched_f32(Gs, sigmas, Vs, info, p=None, stream=None):
     """C ``jacobi_gesvd_batched_f32`` on lists of column-major CUDA tensors."""
+    _need("float32", "cuda", *Gs, *sigmas, *(Vs or []))
+    _need("int32", "cuda", info)
     m = [g.shape[0] for g in Gs]
     n = [g.shape[1] for g in Gs]
     st = jacobi_stats()

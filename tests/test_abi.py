@@ -185,3 +185,22 @@ def test_workspace_fault_injection_returns_alloc_before_any_launch(jg, fn, monke
         rc = f(64, fake, 64, fake, fake, 64, C.byref(p), C.byref(st), C.c_void_p(0))
     assert rc == jg.ERR_ALLOC
     assert st.status == jg.ERR_ALLOC
+
+
+def test_binding_rejects_wrong_element_type_or_memory_space(jg):
+    """The C entry points receive bare pointers: the binding refuses tensors
+    of another element type or memory space before the call (here without a
+    GPU: the check comes first)."""
+    import torch
+    A = torch.zeros(8, 8, dtype=torch.float64)
+    w = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        jg.jacobi_syev(A, w, None)                       # host tensors to a device entry point
+    with pytest.raises(TypeError):
+        jg.jacobi_syev_h(A.float(), w, None)             # float32 to an FP64 entry point
+    with pytest.raises(TypeError):
+        jg.jacobi_syev_f32(A, w, None)                   # float64 to the FP32-storage entry point
+    with pytest.raises(ValueError):
+        jg.jacobi_syev_batched([A], [w], None, torch.zeros(1, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        jg.jacobi_lowp_gemm(A, A, A)                     # the FP32 product given FP64 operands
