@@ -203,6 +203,22 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
 
 
+def _fits(rows: int, cols: int, *mats):
+    """Raise when a matrix argument holds fewer than rows x cols elements in
+    its column-major layout (the library would read or write past it)."""
+    for t in mats:
+        if t is None:
+            continue
+        if t.dim() != 2 or t.shape[0] < rows or t.shape[1] < cols:
+            raise ValueError(f"expected at least a {rows} x {cols} matrix, got {tuple(t.shape)}")
+
+
+def _holds(count: int, *vecs):
+    for t in vecs:
+        if t is not None and t.numel() < count:
+            raise ValueError(f"expected at least {count} elements, got {t.numel()}")
+
+
 def _need(dtype: str, device: str, *tensors):
     """Raise before the C call when a tensor's element type or memory space is
     not the one the entry point reads: the C side receives bare pointers and
@@ -225,6 +241,8 @@ def jacobi_syev(A, w, Q, p: jacobi_params | None = None, stream=None):
     Returns (status, Stats)."""
     _need("float64", "cuda", A, w, Q)
     n = A.shape[0]
+    _fits(n, n, A, Q)
+    _holds(n, w)
     st = jacobi_stats()
     rc = lib().jacobi_syev(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
                            _colmajor_ld(Q) if Q is not None else n,
@@ -237,6 +255,8 @@ def jacobi_syev_h(A, w, Q, p: jacobi_params | None = None, stream=None):
     pinned): same layout as jacobi_syev."""
     _need("float64", "cpu", A, w, Q)
     n = A.shape[0]
+    _fits(n, n, A, Q)
+    _holds(n, w)
     st = jacobi_stats()
     rc = lib().jacobi_syev_h(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
                              _colmajor_ld(Q) if Q is not None else n,
@@ -250,6 +270,8 @@ def jacobi_syev_f32(A, w, Q, p: jacobi_params | None = None, stream=None):
     jacobi_syev (A column-major n x n, overwritten by D; w (n); Q or None)."""
     _need("float32", "cuda", A, w, Q)
     n = A.shape[0]
+    _fits(n, n, A, Q)
+    _holds(n, w)
     st = jacobi_stats()
     rc = lib().jacobi_syev_f32(n, _ptr(A), _colmajor_ld(A), _ptr(w), _ptr(Q),
                                _colmajor_ld(Q) if Q is not None else n,
@@ -263,6 +285,8 @@ def jacobi_gesvd(G, sigma, V, p: jacobi_params | None = None, stream=None):
     U), sigma (n), V (n x n or None).  Returns (status, Stats)."""
     _need("float64", "cuda", G, sigma, V)
     m, n = G.shape
+    _fits(n, n, V)
+    _holds(n, sigma)
     st = jacobi_stats()
     rc = lib().jacobi_gesvd(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
                             _colmajor_ld(V) if V is not None else n,
@@ -273,6 +297,8 @@ def jacobi_gesvd(G, sigma, V, p: jacobi_params | None = None, stream=None):
 def jacobi_gesvd_h(G, sigma, V, p: jacobi_params | None = None, stream=None):
     _need("float64", "cpu", G, sigma, V)
     m, n = G.shape
+    _fits(n, n, V)
+    _holds(n, sigma)
     st = jacobi_stats()
     rc = lib().jacobi_gesvd_h(m, n, _ptr(G), _colmajor_ld(G), _ptr(sigma), _ptr(V),
                               _colmajor_ld(V) if V is not None else n,

@@ -204,3 +204,22 @@ def test_binding_rejects_wrong_element_type_or_memory_space(jg):
         jg.jacobi_syev_batched([A], [w], None, torch.zeros(1, dtype=torch.int32))
     with pytest.raises(TypeError):
         jg.jacobi_lowp_gemm(A, A, A)                     # the FP32 product given FP64 operands
+
+
+def test_binding_rejects_buffers_too_small_for_the_call(jg):
+    """A w shorter than n or a Q smaller than n x n would be written past its
+    end by the library: the binding refuses it first (host tensors through
+    the host-buffer entry points, so no GPU is involved)."""
+    import torch
+    A = torch.zeros(8, 8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        jg.jacobi_syev_h(A, torch.zeros(7, dtype=torch.float64), None)
+    with pytest.raises(ValueError):
+        jg.jacobi_syev_h(A, torch.zeros(8, dtype=torch.float64), torch.zeros(8, 7, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        jg.jacobi_syev_h(A[:, :7], torch.zeros(8, dtype=torch.float64), None)
+    G = torch.zeros(20, 6, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        jg.jacobi_gesvd_h(G, torch.zeros(5, dtype=torch.float64), None)
+    with pytest.raises(ValueError):
+        jg.jacobi_gesvd_h(G, torch.zeros(6, dtype=torch.float64), torch.zeros(6, 5, dtype=torch.float64))
