@@ -312,6 +312,7 @@ def jacobi_syev_step(A, Q, step: int, p: jacobi_params | None = None, stream=Non
     symmetric np x np column-major CUDA tensor A (and Q or None)."""
     _need("float64", "cuda", A, Q)
     np_ = A.shape[0]
+    _fits(np_, np_, A, Q)
     return lib().jacobi_syev_step(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                   _colmajor_ld(Q) if Q is not None else np_,
                                   C.byref(p) if p is not None else None, step,
@@ -324,6 +325,7 @@ def jacobi_syev_step_noalloc(A, Q, step: int, p: jacobi_params | None = None, st
     working buffers in one fixed device array instead."""
     _need("float64", "cuda", A, Q)
     np_ = A.shape[0]
+    _fits(np_, np_, A, Q)
     return lib().jacobi_syev_step_noalloc(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                           _colmajor_ld(Q) if Q is not None else np_,
                                           C.byref(p) if p is not None else None, step,
@@ -335,6 +337,7 @@ def jacobi_gesvd_step(G, V, step: int, p: jacobi_params | None = None, stream=No
     V (np x np or None).  Returns (status, relmax)."""
     _need("float64", "cuda", G, V)
     m, np_ = G.shape
+    _fits(np_, np_, V)
     r = C.c_double(0.0)
     rc = lib().jacobi_gesvd_step(m, np_, _ptr(G), _colmajor_ld(G), _ptr(V),
                                  _colmajor_ld(V) if V is not None else np_,
@@ -349,6 +352,9 @@ def jacobi_lowp_gemm(A, B, C, transA: bool = False, stream=None):
     _need("float32", "cuda", A, B, C)
     K, N = B.shape
     M = C.shape[0]
+    _fits(K, M, A if transA else None)
+    _fits(M, K, None if transA else A)
+    _fits(M, N, C)
     return lib().jacobi_lowp_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
                                   _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
 
@@ -358,6 +364,8 @@ def jacobi_rotation_params(app, aqq, apq, tol: float, out, stream=None):
     rotate) as the FP64 pivot solves compute them, then the same four by the
     textbook formulas (contiguous FP64 CUDA tensors; out is count x 8)."""
     _need("float64", "cuda", app, aqq, apq, out)
+    _holds(app.numel(), aqq, apq)
+    _holds(8 * app.numel(), out)
     return lib().jacobi_rotation_params(app.numel(), _ptr(app), _ptr(aqq), _ptr(apq), float(tol), _ptr(out),
                                         _stream_ptr(stream))
 
@@ -368,6 +376,9 @@ def jacobi_f64emu_gemm(A, B, C, transA: bool = False, stream=None):
     _need("float64", "cuda", A, B, C)
     K, N = B.shape
     M = C.shape[0]
+    _fits(K, M, A if transA else None)
+    _fits(M, K, None if transA else A)
+    _fits(M, N, C)
     return lib().jacobi_f64emu_gemm(M, N, K, _ptr(A), _colmajor_ld(A), int(transA), _ptr(B),
                                     _colmajor_ld(B), _ptr(C), _colmajor_ld(C), _stream_ptr(stream))
 
@@ -378,6 +389,7 @@ def jacobi_syev_step_lowp(A, Q, step: int, p: jacobi_params | None = None, strea
     (or None); p.precision must be JACOBI_PREC_MIXED_BF16X3."""
     _need("float32", "cuda", A, Q)
     np_ = A.shape[0]
+    _fits(np_, np_, A, Q)
     return lib().jacobi_syev_step_lowp(np_, _ptr(A), _colmajor_ld(A), _ptr(Q),
                                        _colmajor_ld(Q) if Q is not None else np_,
                                        C.byref(p) if p is not None else None, step,
