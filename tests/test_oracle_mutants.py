@@ -6,9 +6,11 @@ them.  The mistakes are the kinds a restatement of the paper could make: a
 wrong sign in the 2x2 rotation or in the rotation's application, a
 transposed V-hat in the block-row update (Algorithm 2), a dropped term in
 the block-column update, a wrong index in the round-robin table, a dropped
-row in the Gram block (Sec. 6), and a diagonal that stops carrying its low
+row in the Gram block (Sec. 6), a diagonal that stops carrying its low
 word between rotations (the single-word diagonal that loses the energy of
-late rotations)."""
+late rotations), singular values sorted the wrong way, an off-norm that
+counts the diagonal (Sec. 2.1, eq. (Omega_A)), and Algorithm 3's groups
+shifted by one label."""
 from __future__ import annotations
 
 import os
@@ -40,6 +42,15 @@ MUTANTS = {
     "gram_row_dropped": (
         "for (int r = 0; r < m; r++) s += AT(G, ldg, r, gi) * AT(G, ldg, r, gj);",
         "for (int r = 1; r < m; r++) s += AT(G, ldg, r, gi) * AT(G, ldg, r, gj);"),
+    "svd_sorted_ascending": (
+        "    stable_argsort(n, sg, idx, 0);",
+        "    stable_argsort(n, sg, idx, 1);"),
+    "off_norm_counts_the_diagonal": (
+        "            if (i != j) s += AT(A, lda, i, j) * AT(A, lda, i, j);",
+        "            s += AT(A, lda, i, j) * AT(A, lda, i, j);"),
+    "anti_diagonal_group_shifted": (
+        "                if ((I + J) % N == K) {",
+        "                if ((I + J + 1) % N == K) {"),
     "diagonal_low_word_not_carried": (
         "err += *lo + dl;",
         "err += dl;"),
@@ -56,6 +67,7 @@ PINS = [
     (pins.test_known_singular_values, (False, 4)),
     (pins.test_pivot_solve_preserves_energy_without_bias, ()),
     (pins.test_pivot_eigenvectors_keep_unit_length, ()),
+    (pins.test_algorithm3_matches_printed_label_matrix, ()),
 ]
 
 
