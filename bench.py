@@ -913,7 +913,8 @@ def run_batched(args, wl):
     f_issued = (st.flops_fp32 if wl["f32"] else st.flops_fp64)
     peak = FP32_PEAK_TFLOPS if wl["f32"] else FP64_PEAK_TFLOPS
     achieved = f_issued / (st.ms_total / 1e3) / 1e12
-    kname = "k_batched_evd" if evd else "k_batched_svd"
+    kname = "k_batched_evd" if evd else (
+        "k_batched_svd" if os.environ.get("JACOBI_BATCHED_SVD") == "rowwise" else "k_batched_svd_tiled")
     traffic, prof = profile_traffic(f"{kname}_{'f32' if wl['f32'] else 'f64'}_{B}")
     roofline = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,

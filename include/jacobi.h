@@ -32,8 +32,9 @@
  *   JACOBI_BATCHED_LARGE=blocked|cluster|l2   route of the batched EVD
  *                                  orders above the shared-memory size
  *                                  (default blocked);
- *   JACOBI_BATCHED_SVD=tiled       the row-tiled batched one-sided SVD
- *                                  kernel (same results bit for bit);
+ *   JACOBI_BATCHED_SVD=rowwise     the batched one-sided SVD with one Gram
+ *                                  entry per thread instead of staged row
+ *                                  tiles (same results bit for bit);
  *   JACOBI_TUNE_CACHE=<path>       file of the batched autotuner's cache;
  *   JACOBI_WORKSPACE_LIMIT=<bytes> cap on one call's workspace (fault
  *                                  injection: JACOBI_ERR_ALLOC before any

@@ -140,7 +140,7 @@ struct jacobi_plan {
     cudaGraphExec_t exec = nullptr;
     int* graph_info = nullptr;        // info pointer baked into the graph
     int large_mode = 2;               // EVD orders above the smem size: 0 L2 slots, 1 clusters, 2 blocked
-    bool svd_tiled = false;           // one-sided: the row-tiled kernel (JACOBI_BATCHED_SVD=tiled)
+    bool svd_tiled = false;           // one-sided: the row-tiled kernel (default; JACOBI_BATCHED_SVD=rowwise: the other)
     void* d_blk = nullptr;            // blocked-form slots
     size_t blk_slot = 0;
     int blk_grid = 0;
@@ -326,7 +326,8 @@ extern "C" int jacobi_plan_create_batched(jacobi_plan** out, int kind, int preci
         if (!strcmp(env, "l2")) pl->large_mode = 0;
         else if (!strcmp(env, "cluster")) pl->large_mode = 1;
     }
-    if (const char* env = getenv("JACOBI_BATCHED_SVD")) pl->svd_tiled = kind == 1 && !strcmp(env, "tiled");
+    pl->svd_tiled = kind == 1;
+    if (const char* env = getenv("JACOBI_BATCHED_SVD")) pl->svd_tiled = kind == 1 && strcmp(env, "rowwise") != 0;
     if (precision == JACOBI_PREC_FP32 && p.inner_tol == 4.0 * U64) pl->p.inner_tol = 4.0 * U32;
     pl->h_n.assign(h_n, h_n + batch);
     pl->h_m = kind == 1 ? std::vector<int>(h_m, h_m + batch) : pl->h_n;

@@ -10,8 +10,6 @@ against the FP64 oracle with the FP64 bounds scaled by u32/u64 = 2^29
 """
 from __future__ import annotations
 
-import os
-
 import numpy as np
 import pytest
 
@@ -144,19 +142,18 @@ def test_batched_tall_svd_f32(jg):
         assert np.linalg.norm(G @ V - U * s[None, :]) <= 1e-12 * SCALE32 * np.linalg.norm(G)
 
 
-@pytest.mark.skipif(os.environ.get("JACOBI_TEST_TILED_SVD") != "1",
-                    reason="row-tiled batched SVD kernel: opt-in (JACOBI_TEST_TILED_SVD=1)")
-def test_batched_tall_svd_tiled_is_bitwise_the_default(jg, monkeypatch):
-    """The row-tiled kernel (JACOBI_BATCHED_SVD=tiled) keeps every output's
-    FMA chain in the default kernel's order: sigma, U, V and info agree bit
-    for bit over a batch of tall, square, ragged and odd shapes."""
+def test_batched_tall_svd_tiled_is_bitwise_the_rowwise_kernel(jg, monkeypatch):
+    """The row-tiled kernel (the default) keeps every output's FMA chain in
+    the order of the one-entry-per-thread kernel (JACOBI_BATCHED_SVD=rowwise):
+    sigma, U, V and info agree bit for bit over a batch of tall, square,
+    ragged and odd shapes."""
     import torch
     shapes = [(1024, 64)] * 6 + [(300, 40), (100, 100), (64, 1), (77, 33), (2, 2), (129, 65), (1000, 7)]
     mats = [gen.tall_gaussian(m, n, 78, i, dtype=np.float64) for i, (m, n) in enumerate(shapes)]
     outs = []
-    for variant in ("default", "tiled"):
-        if variant == "tiled":
-            monkeypatch.setenv("JACOBI_BATCHED_SVD", "tiled")
+    for variant in ("rowwise", "tiled"):
+        if variant == "rowwise":
+            monkeypatch.setenv("JACOBI_BATCHED_SVD", "rowwise")
         else:
             monkeypatch.delenv("JACOBI_BATCHED_SVD", raising=False)
         Gs = [jg.colmajor(g, device="cuda", dtype=torch.float32) for g in mats]

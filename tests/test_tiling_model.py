@@ -216,6 +216,7 @@ def _check(m, n, ldg_pad, nt, seed):
     (200, 37, 2, 64, 5),     # several column chunks per warp
     (33, 1, 0, 128, 6),      # a single column
     (65, 66, 0, 64, 7),      # n > tile rows: the accumulated V spans two row tiles
+    (100, 64, 0, 512, 8),    # the autotuner's largest CTA: 16 warps, one column chunk
 ])
 def test_tiled_svd_indexing(m, n, ldg_pad, nt, seed):
     _check(m, n, ldg_pad, nt, seed)
