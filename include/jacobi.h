@@ -362,17 +362,27 @@ void jacobi_plan_destroy(jacobi_plan* plan);
  * as code inside a framework that owns all device memory through its own pool
  * (a cudaMalloc from outside the pool fails or fragments it) and
  * latency-critical loops that cannot take an allocation's implicit
- * synchronisation.  Same arguments, semantics and results as
- * jacobi_syev_step; every buffer besides A and Q lives in a fixed array in
- * device global memory, so the call makes no cudaMalloc / cudaFree and no host
- * heap allocation.
- *   Limits: np <= 768 and 1 <= p->b <= 128, else JACOBI_ERR_UNSUPPORTED.  The
- *   array (about 24 MB) stays resident on every GPU the process uses until
- *   the process exits.
+ * synchronisation.  Same arguments and the same step as jacobi_syev_step;
+ * every buffer besides A and Q lives in a fixed array in device global
+ * memory, so the call makes no cudaMalloc / cudaFree and no host heap
+ * allocation.
+ *   Limits: np <= 768 and 1 <= p->b <= 128, else JACOBI_ERR_UNSUPPORTED.
+ *   Plain FP64 products only: p->precision other than JACOBI_PREC_FP64,
+ *   p->fp64_products = 1, or p->pivot_order = 2 (the QRCP pivoting step)
+ *   return JACOBI_ERR_UNSUPPORTED; the other parameters are checked as in
+ *   jacobi_syev_step (-6 when invalid).  The array (about 24 MB) stays
+ *   resident on every GPU the process uses until the process exits.
+ *   Results: the pivot solves always run one CTA per pair, so A and Q agree
+ *   with jacobi_syev_step to rounding, and bit for bit when that call also
+ *   runs one CTA per pair (JACOBI_PIVOT_CLUSTER=1).
  *   The first call on a device looks up the array's address on that device;
- *   make that first call before any stream capture.
+ *   make that first call before any stream capture.  The address is kept for
+ *   the life of the process: after cudaDeviceReset on a device, do not call
+ *   this entry point on that device again.
  *   All calls share the array: calls whose work overlaps on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller.
+ *   Returns 0, -k for an invalid argument k, -7 for a step outside the
+ *   schedule, JACOBI_ERR_UNSUPPORTED, JACOBI_ERR_CUDA.
  */
 int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, int ldq,
                              const jacobi_params* p, int step, void* stream);

@@ -149,7 +149,10 @@ __global__ void k_batched_svd(BatchedSvdArgs<T> a)
     const int tid = threadIdx.x, nt = blockDim.x;
 
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        if (tid == 0) {  // the flag is cleared before the barrier that publishes the item
+            s_item = (int)atomicAdd(a.queue, 1u);
+            s_bad = 0;
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= a.batch) break;
@@ -162,7 +165,6 @@ __global__ void k_batched_svd(BatchedSvdArgs<T> a)
         T* rowbuf = Vacc + (size_t)k * k;                         // nt x (k+1) staging
         T* G = a.G[mat];
         const int ldg = a.ldg[mat];
-        if (tid == 0) s_bad = 0;
         for (int idx = tid; idx < k * k; idx += nt) Vacc[idx] = (idx % k == idx / k) ? T(1) : T(0);
         int bad = 0;
         for (int idx = tid; idx < m * n; idx += nt) {
@@ -469,7 +471,10 @@ __global__ void k_batched_svd_tiled(BatchedSvdArgs<T> a, int kq)
     T* tile = Vacc + (size_t)kq * kq;                               // kSvdTileLd x kq
 
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        if (tid == 0) {  // the flag is cleared before the barrier that publishes the item
+            s_item = (int)atomicAdd(a.queue, 1u);
+            s_bad = 0;
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= a.batch) break;
@@ -479,7 +484,6 @@ __global__ void k_batched_svd_tiled(BatchedSvdArgs<T> a, int kq)
         const size_t ntp = batched_tri_pad(k);
         T* G = a.G[mat];
         const size_t ldg = (size_t)a.ldg[mat];
-        if (tid == 0) s_bad = 0;
         for (int idx = tid; idx < k * k; idx += nt) Vacc[idx] = (idx % k == idx / k) ? T(1) : T(0);
         int bad = 0;
         for (int idx = tid; idx < m * n; idx += nt) {

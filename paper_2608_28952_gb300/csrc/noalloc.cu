@@ -12,7 +12,11 @@
 // synchronisation and unpredictable latency of an allocation.
 //
 // The array holds at most an order of kNoAllocMaxN = 768 and a block size of
-// kNoAllocMaxB = 128; larger sizes are rejected with JACOBI_ERR_UNSUPPORTED.
+// kNoAllocMaxB = 128; larger sizes are rejected with JACOBI_ERR_UNSUPPORTED,
+// and so are the modes whose buffers it does not hold (emulated FP64
+// products, the QRCP pivoting step).  The pivot solves run one CTA per pair,
+// so the step agrees with jacobi_syev_step to rounding (bit for bit when that
+// call runs one CTA per pair as well).
 // It is statically sized, so every process that loads this library keeps it
 // resident on every GPU it uses until the process exits (about 24 MB).
 //
@@ -24,12 +28,14 @@
 // Set-up: the first call on a device looks up the array's device address
 // (cudaGetSymbolAddress, with that device current) and keeps it for later
 // calls on that device.  Make that first call before any stream capture.
+// The address is not looked up again, so after cudaDeviceReset the entry
+// point must not be used on that device in the same process.
 #include <cuda_runtime.h>
 #include <string.h>
 
 #include <atomic>
 
-#include "internal.h"
+#include "host.h"
 
 using namespace jac;
 
@@ -109,10 +115,16 @@ extern "C" int jacobi_syev_step_noalloc(int np, double* A, int lda, double* Q, i
 {
     jacobi_params p;
     if (pin) p = *pin; else jacobi_params_default(&p);
-    if (p.b < 1 || p.b > kNoAllocMaxB) return p.b < 1 ? -6 : JACOBI_ERR_UNSUPPORTED;
-    if (p.ordering != JACOBI_ORDER_ROUND_ROBIN && p.ordering != JACOBI_ORDER_ANTI_DIAGONAL) return -6;
+    // The same parameter checks as jacobi_syev_step, then the limits of this
+    // entry point: plain FP64 products (the emulated products need a stage-1
+    // buffer sized by the step), no QRCP pivoting step (its scratch is sized
+    // by the pairs), and the array's size.
+    const int e = check_params(p);
+    if (e) return e == -7 ? -6 : e;
+    if (p.precision != JACOBI_PREC_FP64 || p.fp64_products != 0 || p.pivot_order == 2)
+        return JACOBI_ERR_UNSUPPORTED;
+    if (p.b > kNoAllocMaxB) return JACOBI_ERR_UNSUPPORTED;
     if (p.inner_max_sweeps == 0) p.inner_max_sweeps = 1;  // automatic, as in jacobi_syev_step
-    if (p.inner_max_sweeps < 1 || !(p.inner_tol >= 0.0) || (p.pivot_order != 0 && p.pivot_order != 1)) return -6;
     if (np < 2 * p.b || np % p.b || (np / p.b) % 2) return -1;
     if (np > kNoAllocMaxN) return JACOBI_ERR_UNSUPPORTED;
     if (!A) return -2;

@@ -223,3 +223,30 @@ def test_binding_rejects_buffers_too_small_for_the_call(jg):
         jg.jacobi_gesvd_h(G, torch.zeros(5, dtype=torch.float64), None)
     with pytest.raises(ValueError):
         jg.jacobi_gesvd_h(G, torch.zeros(6, dtype=torch.float64), torch.zeros(6, 5, dtype=torch.float64))
+
+
+def test_noalloc_argument_checks_come_before_any_device_work(jg):
+    """jacobi_syev_step_noalloc checks its parameters as jacobi_syev_step does
+    (-6 for an invalid one) and refuses, with JACOBI_ERR_UNSUPPORTED, what its
+    fixed array does not hold (orders above 768, b above 128, emulated FP64
+    products, the QRCP pivoting step) before any CUDA call."""
+    f = jg.lib().jacobi_syev_step_noalloc
+    fake = C.c_void_p(0x1000)   # never dereferenced on these paths
+    null = C.c_void_p(0)
+
+    def call(np_, A, lda, Q, ldq, prm):
+        return f(np_, A, lda, Q, ldq, C.byref(prm), 0, null)
+
+    for bad in (dict(b=0), dict(ordering=3), dict(tol=-1.0), dict(conv=5), dict(pivot_order=4),
+                dict(precision=11), dict(inner_max_sweeps=-1)):
+        assert call(64, fake, 64, fake, 64, jg.params(**{"b": 8, **bad})) == -6, bad
+    for unsup in (dict(precision=jg.PREC_FP64_EMU), dict(precision=jg.PREC_MIXED_BF16X3),
+                  dict(precision=jg.PREC_MIXED_TF32), dict(fp64_products=1), dict(pivot_order=2),
+                  dict(b=129)):
+        assert call(64, fake, 64, fake, 64, jg.params(**{"b": 8, **unsup})) == jg.ERR_UNSUPPORTED, unsup
+    assert call(1024, fake, 1024, fake, 1024, jg.params(b=64)) == jg.ERR_UNSUPPORTED
+    assert call(60, fake, 64, fake, 64, jg.params(b=8)) == -1     # np not a multiple of b
+    assert call(24, fake, 24, fake, 24, jg.params(b=8)) == -1     # N = 3 blocks: odd
+    assert call(64, null, 64, fake, 64, jg.params(b=8)) == -2
+    assert call(64, fake, 63, fake, 64, jg.params(b=8)) == -3
+    assert call(64, fake, 64, fake, 63, jg.params(b=8)) == -5
