@@ -180,7 +180,29 @@ typedef struct {
                                 factorisation and of forming U = Q W           */
     double flops_precond;    /* the FP64 flops issued there (also counted in
                                 flops_fp64)                                    */
+    double rel_final;        /* EVD under JACOBI_CONV_REL: the relative
+                                measure max_{i!=j}|a_ij|/sqrt(|a_ii a_jj|) of
+                                the stop test at exit (0 under OFF_ABS)        */
+    double rel_hist[64];     /* the same measure after each sweep             */
 } jacobi_stats;
+
+/*
+ * jacobi_off_norm -- the stop statistic of the two-sided method on an
+ * arbitrary matrix: the off-diagonal norm Xi(A) = sqrt(sum_{i != j} a_ij^2)
+ * (Sec. 2.1, eq. (Omega_A); the quantity Algorithm 1's stop test compares
+ * with tol ||A||_F), ||A||_F, and, when want_rel != 0, the relative measure
+ * max_{i != j} |a_ij| / sqrt(|a_ii| |a_jj|) of JACOBI_CONV_REL (an entry
+ * with a_ii a_jj = 0 counts as 0 when it is 0 and as +inf otherwise).
+ * Computed by the same kernel and reduction order the sweeps use (sums of
+ * squares in FP64, never as ||A||_F^2 - sum a_ii^2).
+ *   n      order (n >= 1)
+ *   A      device, n x n, leading dimension lda >= n; every entry is read
+ *   h_out  host, 3 doubles: Xi(A), ||A||_F, the relative measure (0 when
+ *          want_rel = 0)
+ * Allocates a small workspace stream-ordered and blocks until done.
+ * Returns 0, -k for an invalid argument k, JACOBI_ERR_ALLOC, JACOBI_ERR_CUDA.
+ */
+int jacobi_off_norm(int n, const double* A, int lda, int want_rel, double* h_out, void* stream);
 
 /* Fill *p with the defaults above.  Returns 0. */
 int jacobi_params_default(jacobi_params* p);

@@ -44,7 +44,8 @@ class _Stats(C.Structure):
                 ("steps", C.c_longlong), ("pair_solves", C.c_longlong),
                 ("rotations", C.c_longlong), ("inner_sweeps", C.c_longlong),
                 ("off_initial", C.c_double), ("off_final", C.c_double),
-                ("norm_fro", C.c_double), ("off_hist", C.c_double * 64)]
+                ("norm_fro", C.c_double), ("off_hist", C.c_double * 64),
+                ("rel_hist", C.c_double * 64)]
 
 
 @dataclass
@@ -60,12 +61,14 @@ class Stats:
     off_final: float
     norm_fro: float
     off_hist: list = field(default_factory=list)
+    rel_hist: list = field(default_factory=list)
 
 
 def _stats(s: _Stats) -> Stats:
+    k = max(0, min(64, s.sweeps))
     return Stats(s.status, s.sweeps, s.stalled, s.steps, s.pair_solves, s.rotations,
                  s.inner_sweeps, s.off_initial, s.off_final, s.norm_fro,
-                 list(s.off_hist)[: max(0, min(64, s.sweeps))])
+                 list(s.off_hist)[:k], list(s.rel_hist)[:k])
 
 
 _LIB = None
@@ -168,6 +171,14 @@ def off_norm(A: np.ndarray) -> float:
     """Xi(A) = sqrt(sum_{i != j} A(i,j)^2), Sec. 2.1 eq. (Omega_A)."""
     A = _f64F(A)
     return lib().oracle_off_norm(A.shape[0], _dp(A), A.shape[0])
+
+
+def rel_off(A: np.ndarray) -> float:
+    """max_{i != j} |A(i,j)| / sqrt(|A(i,i)| |A(j,j)|), the relative stop
+    measure (an entry over a zero diagonal product counts as 0 when it is 0,
+    else +inf)."""
+    A = _f64F(A)
+    return lib().oracle_rel_off(A.shape[0], _dp(A), A.shape[0])
 
 
 def pivot_solve(Ahat: np.ndarray, tol_rel: float = 4 * U64, max_sweeps: int = 30):

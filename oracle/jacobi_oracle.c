@@ -119,6 +119,7 @@ typedef struct {
     double off_final;
     double norm_fro;
     double off_hist[64];
+    double rel_hist[64];      /* under ORC_CONV_REL: the relative measure per sweep */
 } orc_stats;
 
 /* ------------------------------------------------------------------ */
@@ -766,6 +767,7 @@ int oracle_syev_blocked(int n, double *A, int lda, double *w, double *Q, int ldq
             }
             meas = p->conv == ORC_CONV_REL ? rel_off(np, Aw, np) : off_norm(np, Aw, np);
             if (sw < 64) s.off_hist[sw] = off_norm(np, Aw, np);
+            if (sw < 64 && p->conv == ORC_CONV_REL) s.rel_hist[sw] = meas;
             if (meas <= target) { status = 0; sw++; break; }
             if (meas <= 100.0 * target && meas > 0.5 * prev) { status = 0; s.stalled = 1; sw++; break; }
             prev = meas;
@@ -826,6 +828,7 @@ int oracle_syev_scalar(int n, double *A, int lda, double *w, double *Q, int ldq,
             s.rotations += in_sweep;
             meas = p->conv == ORC_CONV_REL ? rel_off(n, Aw, n) : off_norm(n, Aw, n);
             if (sw < 64) s.off_hist[sw] = off_norm(n, Aw, n);
+            if (sw < 64 && p->conv == ORC_CONV_REL) s.rel_hist[sw] = meas;
             if (meas <= target || in_sweep == 0) { status = 0; sw++; break; }
             if (meas <= 100.0 * target && meas > 0.5 * prev) { status = 0; s.stalled = 1; sw++; break; }
             prev = meas;

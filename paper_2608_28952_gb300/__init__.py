@@ -58,7 +58,8 @@ class jacobi_stats(C.Structure):
                 ("ms_lowp", C.c_double), ("ms_refine", C.c_double),
                 ("ms_pivot_lowp", C.c_double), ("ms_update_lowp", C.c_double),
                 ("flops_refine", C.c_double), ("ms_precond", C.c_double),
-                ("flops_precond", C.c_double)]
+                ("flops_precond", C.c_double), ("rel_final", C.c_double),
+                ("rel_hist", C.c_double * 64)]
 
 
 @dataclass
@@ -91,7 +92,9 @@ class Stats:
     flops_refine: float
     ms_precond: float
     flops_precond: float
+    rel_final: float = 0.0
     off_hist: list = field(default_factory=list)
+    rel_hist: list = field(default_factory=list)
 
 
 def _stats(s: jacobi_stats) -> Stats:
@@ -100,7 +103,9 @@ def _stats(s: jacobi_stats) -> Stats:
                  s.ms_total, s.ms_pivot, s.ms_update, s.launches, s.pivot_launches,
                  s.update_launches, s.flops_fp64, s.flops_update, s.flops_fp32, s.flops_lowp,
                  s.ms_lowp, s.ms_refine, s.ms_pivot_lowp, s.ms_update_lowp, s.flops_refine,
-                 s.ms_precond, s.flops_precond, list(s.off_hist)[: max(0, min(64, s.sweeps))])
+                 s.ms_precond, s.flops_precond, s.rel_final,
+                 list(s.off_hist)[: max(0, min(64, s.sweeps))],
+                 list(s.rel_hist)[: max(0, min(64, s.sweeps))])
 
 
 # Every symbol include/jacobi.h declares, with its ctypes signature.
@@ -131,6 +136,7 @@ SIGNATURES = {
     "jacobi_syev_step_lowp": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_f64emu_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
     "jacobi_rotation_params": (_I, [_I, _P, _P, _P, _D, _P, _P]),
+    "jacobi_off_norm": (_I, [_I, _P, _I, _I, C.POINTER(C.c_double), _P]),
 }
 
 _LIB = None
@@ -305,6 +311,17 @@ def jacobi_gesvd_h(G, sigma, V, p: jacobi_params | None = None, stream=None):
                               C.byref(p) if p is not None else None, C.byref(st),
                               _stream_ptr(stream))
     return rc, _stats(st)
+
+
+def jacobi_off_norm(A, want_rel: bool = True, stream=None):
+    """C ``jacobi_off_norm`` on a column-major float64 CUDA tensor A (n x n):
+    returns (status, off(A), ||A||_F, relative measure)."""
+    _need("float64", "cuda", A)
+    n = A.shape[0]
+    _fits(n, n, A)
+    out = (C.c_double * 3)()
+    rc = lib().jacobi_off_norm(n, _ptr(A), _colmajor_ld(A), int(want_rel), out, _stream_ptr(stream))
+    return rc, out[0], out[1], out[2]
 
 
 def jacobi_syev_step(A, Q, step: int, p: jacobi_params | None = None, stream=None):

@@ -153,8 +153,12 @@ SweepResult run_evd_sweeps(EvdState& E, const jacobi_params& p, int& cur, double
         st->update_launches += E.ord.S;
         const double off = sqrt(h_res[0]);
         const double meas = use_rel ? h_res[2] : off;
-        if (sw < 64) st->off_hist[sw] = off;
+        if (sw < 64) {
+            st->off_hist[sw] = off;
+            st->rel_hist[sw] = use_rel ? h_res[2] : 0.0;
+        }
         st->off_final = off;
+        st->rel_final = use_rel ? h_res[2] : 0.0;
         if (meas <= target) return {0, sw + 1};
         if (meas <= 100.0 * target && meas > 0.5 * prev) {
             st->stalled = 1;
@@ -228,6 +232,7 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         st->off_initial = sqrt(h_res[0]);
         st->off_final = st->off_initial;
         const bool rel = p.conv == JACOBI_CONV_REL;
+        st->rel_final = rel ? h_res[2] : 0.0;
         const double target = rel ? p.tol : p.tol * st->norm_fro;
         const double meas0 = rel ? h_res[2] : st->off_initial;
         int cur = 0;
@@ -651,6 +656,31 @@ extern "C" int jacobi_gesvd_h(int m, int n, double* h_G, int ldg, double* h_sigm
         if (cudaStreamSynchronize(s) != cudaSuccess) return JACOBI_ERR_CUDA;
     }
     return rc;
+}
+
+// ============================================================================ stop statistic
+extern "C" int jacobi_off_norm(int n, const double* A, int lda, int want_rel, double* h_out, void* stream)
+{
+    if (n < 1) return -1;
+    if (!A) return -2;
+    if (lda < n) return -3;
+    if (!h_out) return -5;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws(s);
+    double* partial = ws.get<double>(3 * (size_t)reduce_blocks_for(n));
+    unsigned* ticket = ws.get<unsigned>(1);
+    double* result = ws.get<double>(3);
+    if (ws.failed) return JACOBI_ERR_ALLOC;
+    double h[3];
+    if (cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess ||
+        launch_offnorm_ld(n, A, lda, partial, ticket, result, want_rel != 0, s) != cudaSuccess ||
+        cudaMemcpyAsync(h, result, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return JACOBI_ERR_CUDA;
+    h_out[0] = sqrt(h[0]);
+    h_out[1] = sqrt(h[1]);
+    h_out[2] = want_rel ? h[2] : 0.0;
+    return 0;
 }
 
 // ============================================================================ single steps

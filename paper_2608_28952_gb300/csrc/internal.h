@@ -58,6 +58,9 @@ cudaError_t launch_load_sym(int n, int np, const double* A, int lda, double* Aw,
 int reduce_blocks_for(int np);
 cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned int* ticket,
                            double* result, bool want_rel, cudaStream_t s);
+// The same reduction on an n x n matrix with leading dimension ld.
+cudaError_t launch_offnorm_ld(int n, const double* A, int ld, double* partial, unsigned int* ticket,
+                              double* result, bool want_rel, cudaStream_t s);
 
 // Pivot solves of one step (one CTA per pair): reads Ain's pivot blocks
 // (EVD) or sums the Gram partials (SVD), runs the FP64 inner Jacobi, writes

@@ -124,8 +124,11 @@ int reduce_blocks_for(int np)
     return g < 1 ? 1 : g;
 }
 
+// Column j of the np x np matrix (leading dimension ld) is read by CTA
+// j mod G, its rows strided over the CTA's threads; per-thread sums, a tree
+// over the CTA, then one thread sums the CTA partials in index order.
 template <typename TA>
-__global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict__ Aw,
+__global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict__ Aw, int ld,
                                                    double* partial, unsigned int* ticket,
                                                    double* result, int want_rel)
 {
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict_
     const int tid = threadIdx.x, G = gridDim.x;
     double off = 0.0, all = 0.0, rel = 0.0;
     for (int j = blockIdx.x; j < np; j += G) {
-        const TA* col = Aw + (size_t)np * j;
+        const TA* col = Aw + (size_t)ld * j;
         const double ajj = fabs((double)col[j]);
         for (int i = tid; i < np; i += RED_T) {
             double v = (double)col[i];
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict_
             if (i != j) {
                 off += v2;
                 if (want_rel && v != 0.0) {
-                    double d = fabs((double)Aw[(size_t)np * i + i]) * ajj;
+                    double d = fabs((double)Aw[(size_t)ld * i + i]) * ajj;
                     double r = d > 0.0 ? v2 / d : INFINITY;
                     rel = fmax(rel, r);
                 }
@@ -189,14 +192,20 @@ __global__ void __launch_bounds__(RED_T) k_offnorm(int np, const TA* __restrict_
 cudaError_t launch_offnorm(int np, const double* Aw, double* partial, unsigned int* ticket,
                            double* result, bool want_rel, cudaStream_t s)
 {
-    k_offnorm<double><<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, want_rel);
+    return launch_offnorm_ld(np, Aw, np, partial, ticket, result, want_rel, s);
+}
+
+cudaError_t launch_offnorm_ld(int n, const double* A, int ld, double* partial, unsigned int* ticket,
+                              double* result, bool want_rel, cudaStream_t s)
+{
+    k_offnorm<double><<<reduce_blocks_for(n), RED_T, 0, s>>>(n, A, ld, partial, ticket, result, want_rel);
     return cudaGetLastError();
 }
 
 cudaError_t launch_offnorm32(int np, const float* Aw, double* partial, unsigned int* ticket,
                              double* result, cudaStream_t s)
 {
-    k_offnorm<float><<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, partial, ticket, result, 0);
+    k_offnorm<float><<<reduce_blocks_for(np), RED_T, 0, s>>>(np, Aw, np, partial, ticket, result, 0);
     return cudaGetLastError();
 }
 

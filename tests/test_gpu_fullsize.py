@@ -1,0 +1,164 @@
+"""Full-size GPU tests of the stated workloads that the per-case parity tests
+cover only at smaller sizes.
+
+* n = 8192, b = 128 (the mixed-precision workload's matrix: lambda ~ U[-1,1],
+  Haar Q, seed 6): the first FP64 step element-wise against the oracle's
+  step (k = 256 pivots: clusters / global scratch), the first low-precision
+  step against the oracle's FP64 step within the split-product bound, then
+  the converged plain FP64 solve and the converged mixed BF16x3 solve with
+  FP64-accurate refinement and closing-sweep products, both against the
+  constructed spectrum at the FP64 gates (eigenvalues 1e-13 ||A||_2,
+  residual 1e-12 ||A||_F, orthogonality 1e-13 n).
+* n = 4096, b = 64, graded lambda_i = +-10^(-12 i/(n-1)) (seed 3): absolute
+  1e-13 ||A||_2 everywhere, relative 1e-12 for |lambda| >= 1e-3 ||A||_2.
+* graded SPD A = D H D at n = 1024, b = 64 under the relative stop criterion:
+  every eigenvalue within 1e-12 relative of the oracle's.
+
+Residuals and orthogonality of the large solves are evaluated on the GPU with
+torch's FP64 matrix products (test arithmetic, not the library's).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import jacobi_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def jg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_28952_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return gen.sym_known(8192, "uniform", seed=gen.SEEDS["c4"])
+
+
+def _gates(jg, A, w, Q, lam_ref, eig=1e-13, res=1e-12, orth=1e-13):
+    """Eigenvalue error against lam_ref, ||AQ - QD||_F / ||A||_F and
+    ||Q^T Q - I||_F / n (FP64 products on the GPU)."""
+    import torch
+    n = A.shape[0]
+    wv = w.cpu().numpy()
+    e = np.abs(wv - lam_ref).max() / np.abs(lam_ref).max()
+    Ad = torch.from_numpy(np.asarray(A)).to("cuda")
+    r = float(torch.linalg.norm(Ad @ Q - Q * w[None, :]) / torch.linalg.norm(Ad))
+    o = float(torch.linalg.norm(Q.t() @ Q - torch.eye(n, dtype=torch.float64, device="cuda"))) / n
+    del Ad
+    assert e <= eig, e
+    assert r <= res, r
+    assert o <= orth, o
+    return e, r, o
+
+
+def _pivot_vector_tol(A0, b, pairs):
+    cond = 1.0
+    for (I, J) in pairs:
+        idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+        ev = np.linalg.eigvalsh(A0[np.ix_(idx, idx)])
+        gap = max(np.diff(ev).min(), 1e-300)
+        cond = max(cond, np.abs(ev).max() / gap)
+    return 32 * (2 * b) * U * cond
+
+
+def test_c4_first_fp64_step_matches_oracle(jg, c4):
+    """Step 0 of the n = 8192, b = 128 solve (32 pairs of 256 x 256 pivots),
+    element-wise against the oracle's step within the eigenvector
+    conditioning bound of the step's pivots."""
+    import torch
+    A, lam = c4
+    b = 128
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, A.shape[0] // b)
+    A_or, _, _ = oracle.syev_step(A, None, b, tab[0])
+    Ad = jg.colmajor(A, device="cuda", dtype=torch.float64)
+    assert jg.jacobi_syev_step(Ad, None, 0, jg.params(b=b)) == 0
+    tol_v = _pivot_vector_tol(A, b, tab[0])
+    err = np.abs(Ad.cpu().numpy() - A_or).max() / np.abs(lam).max()
+    assert err <= max(1e-13, 4 * tol_v), (err, tol_v)
+
+
+def test_c4_first_lowp_step_within_split_bound(jg, c4):
+    """Step 0 of the low-precision phase at full size (FP32 A and Q = I,
+    bf16 hi/lo products on the tensor cores) against the oracle's FP64 step
+    on the same FP32 input: |A' - A'_or| <= (2^-15 + 4 k u32) |V|^T |A| |V|
+    and |Q' - V| <= (2^-15 + 4 k u32) |V| (the bound of test_gpu_mixed)."""
+    import torch
+    A, _ = c4
+    n, b = A.shape[0], 128
+    k = 2 * b
+    A32 = np.asfortranarray(A.astype(np.float32))
+    A64 = A32.astype(np.float64)
+    tab = oracle.ordering(oracle.ORDER_ROUND_ROBIN, n // b)
+    A_or, V, _ = oracle.syev_step(A64, np.eye(n), b, tab[0])   # Q = I: Q' is the step's V
+    Ad = jg.colmajor(A32, device="cuda", dtype=torch.float32)
+    Qd = jg.colmajor(torch.eye(n, dtype=torch.float32), device="cuda")
+    assert jg.jacobi_syev_step_lowp(Ad, Qd, 0, jg.params(b=b, precision=jg.PREC_MIXED_BF16X3)) == 0
+    c = 2.0 ** -15 + 4 * k * U32
+    aV = torch.from_numpy(np.abs(V)).to("cuda")
+    aA = torch.from_numpy(np.abs(A64)).to("cuda")
+    boundA = c * (aV.t() @ aA @ aV) + 1e-30
+    del aA
+    ra = float(((Ad.double() - torch.from_numpy(A_or).to("cuda")).abs() / boundA).max())
+    del boundA
+    rq = float(((Qd.double() - torch.from_numpy(V).to("cuda")).abs() / (c * aV + 1e-30)).max())
+    assert ra <= 1.0, ra
+    assert rq <= 1.0, rq
+
+
+def test_c4_plain_fp64_solve(jg, c4):
+    """The plain FP64 solve of the n = 8192 matrix (the mixed form's
+    comparison point) at the FP64 gates."""
+    A, lam = c4
+    w, Q, _, st = jg.syev(A, b=128)
+    assert st.status == 0
+    assert st.off_final <= 1e-14 * st.norm_fro or st.stalled
+    _gates(jg, A, w, Q, np.sort(lam))
+
+
+def test_c4_mixed_bf16x3_with_fp64_products(jg, c4):
+    """The mixed form at full size (BF16x3 low-precision sweeps, FP64 pivots,
+    refinement and closing sweeps with FP64-accurate tensor-core products):
+    the FP64 gates themselves, ten times tighter than the mixed target."""
+    A, lam = c4
+    w, Q, _, st = jg.syev(A, b=128, precision=jg.PREC_MIXED_BF16X3, fp64_products=1)
+    assert st.status == 0 and st.sweeps_lowp >= 1 and st.flops_lowp > 0
+    _gates(jg, A, w, Q, np.sort(lam))
+
+
+def test_graded_n4096_b64(jg):
+    """Config 2's graded spectrum at full size: absolute 1e-13 ||A||_2 for
+    every eigenvalue, relative 1e-12 where |lambda| >= 1e-3 ||A||_2 (the
+    stored entries fix smaller eigenvalues only to ~u ||A|| absolutely)."""
+    A, lam = gen.sym_known(4096, "graded", seed=gen.SEEDS["c2g"])
+    w, Q, _, st = jg.syev(A, b=64)
+    assert st.status == 0
+    ref = np.sort(lam)
+    _gates(jg, A, w, Q, ref)
+    wv = w.cpu().numpy()
+    big = np.abs(ref) >= 1e-3 * np.abs(ref).max()
+    assert (np.abs(wv - ref)[big] / np.abs(ref[big])).max() <= 1e-12
+
+
+def test_graded_dhd_n1024_relative(jg):
+    """Graded SPD A = D H D (kappa(H) <= 10, D = diag(10^(-6 i/(n-1))),
+    eigenvalues over 12 decades) with the relative stop criterion: every
+    eigenvalue within 1e-12 relative of the oracle's (Jacobi's relative
+    accuracy on such matrices, Sec. 1)."""
+    A, _, _ = gen.graded_dhd(1024, seed=gen.SEEDS["c2dhd"])
+    w_or, *_ , s_or = oracle.syev(A, b=64, conv=oracle.CONV_REL, tol=4 * U)
+    w, Q, _, st = jg.syev(A, b=64, conv=jg.CONV_REL, tol=4 * U)
+    assert s_or == 0 and st.status == 0
+    assert st.rel_final <= 4 * U or st.stalled
+    wv = w.cpu().numpy()
+    assert (np.abs(wv - w_or) / np.abs(w_or)).max() <= 1e-12

@@ -87,6 +87,49 @@ def test_zero_entry_is_not_rotated():
     assert not applied and np.array_equal(A2, A) and np.array_equal(Q2, np.eye(3))
 
 
+# ------------------------------------------------------------------ stop statistics
+def test_off_norm_exact_on_integer_matrices():
+    """Xi(A)^2 = sum_{i != j} a_ij^2 (Sec. 2.1, eq. (Omega_A)) in exact integer
+    arithmetic: small integer entries make every square and partial sum exact
+    in binary64, so the oracle's value is the correctly rounded square root
+    of the exact integer, and Xi(A)^2 + sum a_ii^2 = ||A||_F^2 exactly."""
+    r = np.random.default_rng(71)
+    for n in (1, 2, 5, 17):
+        M = r.integers(-1000, 1001, (n, n))
+        exact_off = sum(int(M[i, j]) ** 2 for i in range(n) for j in range(n) if i != j)
+        exact_all = sum(int(v) ** 2 for v in M.ravel())
+        assert oracle.off_norm(M.astype(float)) == np.sqrt(float(exact_off))
+        assert exact_off + sum(int(M[i, i]) ** 2 for i in range(n)) == exact_all
+        # invariant under a symmetric permutation (the same set of entries)
+        p = r.permutation(n)
+        assert oracle.off_norm(M[np.ix_(p, p)].astype(float)) == np.sqrt(float(exact_off))
+
+
+def test_relative_measure_closed_forms_and_scaling():
+    """max_{i != j} |a_ij| / sqrt(|a_ii a_jj|): the 2 x 2 closed form, the
+    zero-diagonal rule, and invariance under a two-sided diagonal scaling
+    D A D (the property the relative stop test is for; powers of two keep
+    the scaled entries exact)."""
+    assert oracle.rel_off(np.array([[4.0, 3.0], [3.0, 9.0]])) == 0.5
+    assert oracle.rel_off(np.array([[4.0, -6.0], [-6.0, 1.0]])) == 3.0
+    assert oracle.rel_off(np.diag([1.0, 2.0, 3.0])) == 0.0
+    Z = np.array([[0.0, 1e-9], [1e-9, 1.0]])
+    assert np.isinf(oracle.rel_off(Z))
+    assert oracle.rel_off(np.array([[0.0, 0.0], [0.0, 1.0]])) == 0.0
+    r = np.random.default_rng(72)
+    n = 12
+    A = gen.sym_gaussian(n, 73) + np.diag(r.uniform(1.0, 2.0, n))
+    d = 2.0 ** r.integers(-30, 30, n)
+    B = d[:, None] * A * d[None, :]
+    assert abs(oracle.rel_off(B) - oracle.rel_off(A)) <= 8 * U * oracle.rel_off(A)
+    # the maximum is attained at the entry with the largest normalised size
+    i, j = 3, 8
+    A2 = np.diag(np.full(n, 4.0))
+    A2[i, j] = A2[j, i] = 2.0
+    A2[1, 2] = A2[2, 1] = 1.0
+    assert oracle.rel_off(A2) == 0.5
+
+
 # ------------------------------------------------------------------ special inputs
 @pytest.mark.parametrize("scalar", [False, True])
 def test_diagonal_input_no_rotation(scalar):
