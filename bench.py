@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 blocked Jacobi library.
 
-Default workload: plain FP64 two-sided blocked Jacobi EVD of a dense
-symmetric n = 4096 matrix, b = 64, round-robin ordering, eigenvalues plus the
-full eigenvector matrix, stop at off(A) <= 1e-14 ||A||_F.  Input: A = Q diag(lam)
-Q^T, lam ~ U[-1, 1], Q Haar (Householder QR of a seeded Gaussian), seed 2.
-Other workloads (--workload): the n = 256 case, the graded spectrum, the
-one-sided SVD, the mixed-precision form at n = 4096 and n = 8192 (with the
-plain FP64 solve of the same n = 8192 matrix beside it), and the batched forms
-(20000 symmetric matrices, n ~ U{8..512}, FP32 or FP64; 4096 tall 1024 x 64
-FP32 SVDs).
+Default workload (the metric's own comparison, mixed + batched vs plain
+FP64 at the same error): the mixed-precision two-sided blocked Jacobi EVD of a
+dense symmetric n = 8192 matrix, b = 128 -- bf16 hi/lo x3 tensor-core updates
+in the early sweeps, FP64 pivot solves, FP64 refinement and closing sweeps
+with FP64-accurate tensor-core products -- eigenvalues plus the full
+eigenvector matrix, gated at the FP64 tolerances.  Input: A = Q diag(lam) Q^T,
+lam ~ U[-1, 1], Q Haar (Householder QR of a seeded Gaussian), seed 6.  Beside
+it in the same line: the plain FP64 solve of the same matrix (`plain_fp64`,
+one timed call, its accuracy at the same gates, and the ratio), and the three
+batched forms (20000 symmetric matrices, n ~ U{8..512}, FP64 and FP32; 4096
+tall 1024 x 64 FP32 SVDs), each next to the per-matrix plain FP64 path
+(`batched`).  `--no-compare` leaves those out.  Other workloads
+(--workload): the n = 256 and n = 4096 FP64 cases, the graded spectrum, the
+one-sided SVD (direct, QR-preconditioned, emulated products), the other
+mixed forms, and each batched form alone.
 
 One step = one complete call (every sweep to convergence plus the
 finalisation) on the resident input: jacobi_syev / jacobi_gesvd for a single
@@ -67,7 +73,7 @@ WORKLOADS = {
     "evd4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, ref_sweeps=14,
                     desc="plain FP64 two-sided block Jacobi EVD, n=4096, b=64, round-robin, "
                          "eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
-    "evd4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=5, ref_sweeps=14,
+    "evd4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=5, ref_sweeps=14, compare_plain=True,
                        desc="two-sided block Jacobi EVD with FP64-accurate update products on the bf16 "
                             "tensor cores (eight 7-bit slices per operand), FP64 pivots and off-norm, "
                             "n=4096, b=64, round-robin, eigenvalues + full Q, off(A) <= 1e-14 ||A||_F"),
@@ -98,12 +104,12 @@ WORKLOADS = {
                              desc="one-sided block Jacobi SVD with the Gram and column products FP64-accurate "
                                   "on the bf16 tensor cores, FP64 pivots, 16384 x 2048, b=64, "
                                   "sigma_i = 10^(-10 i/(n-1)), U, sigma, V"),
-    "mixed4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=14,
+    "mixed4096": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=14, compare_plain=True,
                       refine_steps=2,
                       desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                            "updates, FP64 pivots, FP64 refinement + closing sweeps), n=4096, "
                            "b=64, lam ~ U[-1,1], eigenvalues + full Q, off <= 1e-14 ||A||_F"),
-    "mixed8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14,
+    "mixed8192": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14, compare_plain=True,
                       refine_steps=1,
                       desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                            "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, "
@@ -128,13 +134,13 @@ WORKLOADS = {
                           desc="mixed-precision two-sided block Jacobi EVD (tf32 big/small x3 tensor-core "
                                "updates, FP64 pivots, FP64 refinement + closing sweeps), n=8192, b=128, "
                                "lam ~ U[-1,1], eigenvalues + full Q"),
-    "mixed4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=14,
+    "mixed4096emu": dict(kind="evd", n=4096, b=64, spectrum="uniform", seed=2, precision=2, ref_sweeps=14, compare_plain=True,
                          refine_steps=2, fp64_products=1,
                          desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                               "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
                               "on the bf16 tensor cores), n=4096, b=64, lam ~ U[-1,1], eigenvalues + full Q"),
     "mixed8192emu": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14,
-                         refine_steps=1, fp64_products=1,
+                         refine_steps=1, fp64_products=1, compare_plain=True, compare_batched=True,
                          desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                               "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
                               "on the bf16 tensor cores), n=8192, b=128, lam ~ U[-1,1], eigenvalues + full Q"),
@@ -348,7 +354,8 @@ def cpu_baseline(wl, sweeps: int, budget_s: float = 12.0):
                       f"({S} per sweep, with vectors){qr}, "
                       f"{sum(times):.1f} s, extrapolated x{S} steps x{sweeps} sweeps "
                       f"(the GPU run's sweep count); OpenMP over the pairs of a step",
-            "seconds_per_step": t_step}
+            "seconds_per_step": t_step, "measured_s": sum(times), "steps_sampled": len(times),
+            "extrapolated": True, "extrapolation_factor": S * sweeps}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -357,33 +364,62 @@ def run_reference_batched(args, wl):
     B = len(shapes)
     mats = batched_host_sample(wl, shapes, 256)
     rates = []
+    cores = len(os.sched_getaffinity(0))
+    secs_all = []
     for i in range(args.warmup + args.steps):
-        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=6.0)
+        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=6.0, threads=cores)
         mats = mats[done:] + mats[:done]  # the next step starts where this one ended
         rates.append(secs / frac)
+        secs_all.append(secs)
     t_batch = sum(rates[args.warmup:]) / args.steps
     value = B / t_batch
     evd = wl["kind"] == "batched_evd"
     sample = (f"each step = the FP64 oracle (scalar parallel-ordered Jacobi per matrix, one "
-              f"thread) on consecutive matrices of the batch for 6 s, extrapolated by "
-              f"{'n^3' if evd else 'm n^2'} work to all {B} matrices")
-    return value, 1e3 * t_batch, sample
+              f"matrix per thread on {cores} threads) on consecutive matrices of the batch for 6 s, "
+              f"extrapolated by {'n^3' if evd else 'm n^2'} work to all {B} matrices")
+    ms_sample = 1e3 * sum(secs_all[args.warmup:]) / args.steps
+    return value, ms_sample, sample, t_batch / (ms_sample / 1e3)
+
+
+def workload_config(wl, world: int) -> dict:
+    """The `config` object of a workload's bench line: what is solved, with
+    its sizes and seed (the same object in the GPU arm and the reference
+    arm, so the two lines name the same configuration)."""
+    if wl["kind"] in ("batched_evd", "batched_svd"):
+        evd = wl["kind"] == "batched_evd"
+        return {"workload": wl["desc"], "count": wl["count"], "seed": wl["seed"],
+                **({"n_range": [wl["lo"], wl["hi"]]} if evd else {"m": wl["m"], "n": wl["n"]}),
+                "parallelism": f"one batch per rank x{world}",
+                "l2": "inputs larger than L2 (the whole batch, GBs)"}
+    prec = wl.get("precision", 0)
+    return {"workload": wl["desc"], "b": wl["b"], "n": wl["n"],
+            **({"m": wl["m"]} if "m" in wl else {}),
+            "seed": wl["seed"], "parallelism": f"replicas x{world}",
+            **({"svd_qr": True} if wl.get("svd_qr") else {}),
+            **({"pivot_order": wl["pivot_order"]} if "pivot_order" in wl else {}),
+            **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3",
+                              5: "fp64 emulated products"}[prec],
+                "refine_steps": wl.get("refine_steps")} if prec else {}),
+            **({"fp64_products": True} if wl.get("fp64_products") else {}),
+            "l2": "inputs larger than L2 (working A, Q double-buffered: 4 x n^2 x 8 B)"}
 
 
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    cores = len(os.sched_getaffinity(0))
     if wl["kind"] in ("batched_evd", "batched_svd"):
-        value, ms_step, sample = run_reference_batched(args, wl)
-        cores = len(os.sched_getaffinity(0))
+        value, ms_step, sample, factor = run_reference_batched(args, wl)
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl["desc"]},
+                "config": workload_config(wl, args.gpus),
                 "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores,
-                                 "kind": "oracle", "sample": sample},
+                                 "kind": "oracle", "sample": sample, "extrapolated": True,
+                                 "extrapolation_factor": factor},
+                "ms_per_step_basis": "measured wall time of one sampled step (6 s of oracle work)",
                 "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -393,18 +429,21 @@ def run_reference(args, wl):
     timed = times[args.warmup:]
     t_step = sum(timed) / len(timed)
     value = 1.0 / (t_step * S * sweeps + extra)
-    cores = len(os.sched_getaffinity(0))
-    sample = (f"each step = one parallel step (of {S} per sweep) of the oracle on the workload, "
-              f"extrapolated x{S} x{sweeps} sweeps (the oracle's sweep count on this input, from a "
-              f"full solve); first-sweep steps cost more than later ones, so this overstates the "
-              f"full solve's time")
+    sample = (f"each step = one parallel step (of {S} per sweep, with vectors) of the FP64 oracle on "
+              f"the workload's matrix, OpenMP over the pairs of the step on {cores} cores; the rate is "
+              f"extrapolated x{S} steps x{sweeps} sweeps (the oracle's own sweep count on this input, "
+              f"from a full solve); first-sweep steps cost more than later ones, so this overstates "
+              f"the full solve's time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * (t_step * S * sweeps + extra), "higher_is_better": True,
+            "ms_per_step": 1e3 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"]},
+            "config": workload_config(wl, args.gpus),
             "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "extrapolated": True,
+                             "extrapolation_factor": S * sweeps, "seconds_per_step": t_step},
+            "ms_per_step_basis": "measured wall time of one sampled oracle step (one parallel "
+                                 "step of the sweep); value = 1 / (that time x steps x sweeps)",
             "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -550,6 +589,73 @@ def svd_kernel_classes(stats, wl, peaks):
     return kernels
 
 
+def evd_accuracy(X, lam_true, w, V, dev) -> dict:
+    """Eigenvalue errors against the constructed spectrum, residual and
+    orthogonality of a solve (FP64 products on the GPU)."""
+    import numpy as np
+    import torch
+    n = X.shape[0]
+    wv = w.cpu().numpy()
+    lam = np.sort(lam_true)
+    big = np.abs(lam) >= 1e-3 * np.abs(lam).max()
+    acc = {"max_abs_eig_err_over_norm2": float(np.abs(wv - lam).max() / np.abs(lam).max()),
+           "max_rel_eig_err_abs_ge_1e-3": float((np.abs(wv - lam)[big] / np.abs(lam[big])).max())}
+    A64 = torch.from_numpy(np.asarray(X)).to(dev)
+    R = A64 @ V - V * w[None, :]
+    acc["residual_fro_over_normA"] = float(torch.linalg.norm(R) / torch.linalg.norm(A64))
+    del R
+    acc["orth_fro_over_n"] = float(torch.linalg.norm(V.t() @ V - torch.eye(n, device=dev,
+                                                                           dtype=torch.float64)) / n)
+    del A64
+    return acc
+
+
+def evd_gates(acc: dict) -> dict:
+    """The FP64 gates of the two-sided solve (the stated target for plain
+    FP64; the mixed forms are held to the same gates here)."""
+    g = {"eig_le_1e-13": acc["max_abs_eig_err_over_norm2"] <= 1e-13,
+         "residual_le_1e-12": acc["residual_fro_over_normA"] <= 1e-12,
+         "orth_le_1e-13_n": acc["orth_fro_over_n"] <= 1e-13}
+    g["all"] = all(g.values())
+    return g
+
+
+def plain_fp64_solve(wl, X, lam, dev, stream) -> dict:
+    """The plain FP64 solve (DFMA products, the library's defaults) of the
+    workload's matrix at the same block size: one jacobi_syev call on the
+    resident input, timed with CUDA events on the stream."""
+    import torch
+
+    import paper_2608_28952_gb300 as jg
+    n = X.shape[0]
+    p = jg.params(b=wl["b"])
+    Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
+    w = torch.empty(n, dtype=torch.float64, device=dev)
+    V = jg.colmajor_empty(n, n, torch.float64, dev)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    rc, st = jg.jacobi_syev(Xd, w, V, p, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if rc != 0:
+        raise RuntimeError(f"plain FP64 solve: status {rc}")
+    ms = e0.elapsed_time(e1)
+    del Xd
+    acc = evd_accuracy(X, lam, w, V, dev)
+    del w, V
+    return {"value": 1e3 / ms, "unit": "matrices/s", "ms": ms, "sweeps": st.sweeps,
+            "steps": 1, "warmup": 0, "precision": "fp64 (DFMA products)", "b": wl["b"],
+            "timing": "CUDA events around one jacobi_syev call on the resident input, after the "
+                      "timed steps (context and modules loaded)",
+            "phases_ms": {"pivot": st.ms_pivot, "update": st.ms_update, "total": st.ms_total},
+            "eff_tflops_issued": st.flops_fp64 / (st.ms_total / 1e3) / 1e12,
+            "accuracy": acc, "accuracy_gates": evd_gates(acc), "clocks": clocks}
+
+
 def run_gpu(args, wl):
     if wl["kind"] in ("batched_evd", "batched_svd"):
         return run_batched(args, wl)
@@ -612,20 +718,10 @@ def run_gpu(args, wl):
     value = total / (ms_max / 1e3)
 
     # accuracy of the last step (outside the timed region)
-    acc = {}
     if wl["kind"] == "evd":
-        w = out.cpu().numpy()
-        lam = np.sort(ref)
-        acc["max_abs_eig_err_over_norm2"] = float(np.abs(w - lam).max() / np.abs(lam).max())
-        big = np.abs(lam) >= 1e-3 * np.abs(lam).max()
-        acc["max_rel_eig_err_abs_ge_1e-3"] = float((np.abs(w - lam)[big] / np.abs(lam[big])).max())
-        A64 = torch.from_numpy(np.asarray(X)).to(dev)
-        R = A64 @ V - V * out[None, :]
-        acc["residual_fro_over_normA"] = float(torch.linalg.norm(R) / torch.linalg.norm(A64))
-        acc["orth_fro_over_n"] = float(torch.linalg.norm(V.t() @ V - torch.eye(n, device=dev,
-                                                           dtype=torch.float64)) / n)
-        del A64, R
+        acc = evd_accuracy(X, ref, out, V, dev)
     else:
+        acc = {}
         s = out.cpu().numpy()
         acc["max_abs_sigma_err_over_sigma_max"] = float(np.abs(s - ref).max() / ref[0])
         big = ref >= 1e-3 * ref[0]
@@ -721,6 +817,24 @@ def run_gpu(args, wl):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, sweeps)
 
+    # the metric's comparisons (one GPU, rank 0 alone): the plain FP64 solve of
+    # the same matrix, and the batched forms next to the per-matrix FP64 path
+    plain = batched = None
+    if world == 1 and not args.no_compare and wl.get("compare_plain"):
+        del Wd, V, out
+        torch.cuda.empty_cache()
+        plain = plain_fp64_solve(wl, X, ref, dev, stream)
+    if world == 1 and not args.no_compare and wl.get("compare_batched"):
+        batched = {}
+        for name in ("batched_f64", "batched_f32", "batched_svd_f32"):
+            torch.cuda.empty_cache()
+            bl = measure_batched(WORKLOADS[name], 1, 1, 0, not args.no_cpu_baseline, 1, dev, stream,
+                                 plain_loop_s=6.0)
+            batched[name] = {k: bl.get(k) for k in (
+                "value", "unit", "dtype", "ms_per_step", "steps", "warmup", "config", "plan",
+                "accuracy", "roofline", "cpu_baseline", "plain_fp64_loop", "vs_plain_fp64_loop",
+                "gpu_launches", "clocks")}
+
     if rank == 0:
         st = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
@@ -729,16 +843,7 @@ def run_gpu(args, wl):
                 "dtype": "f64" if prec == 0 else ("f64 (products from bf16 slices)" if prec == 5 else
                                                   {2: "bf16x3", 3: "fp16x3", 4: "tf32x3"}[prec] + "+f32+f64"),
                 "data": "synthetic (seeded; see config)",
-                "config": {"workload": wl["desc"], "b": b,
-                           "n": wl["n"], **({"m": wl["m"]} if "m" in wl else {}),
-                           "seed": wl["seed"], "parallelism": f"replicas x{world}",
-                           **({"svd_qr": True} if wl.get("svd_qr") else {}),
-                           **({"pivot_order": wl["pivot_order"]} if "pivot_order" in wl else {}),
-                           **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3",
-                                             5: "fp64 emulated products"}[prec],
-                               "refine_steps": wl.get("refine_steps")} if prec else {}),
-                           "l2": "inputs larger than L2 (working A, Q double-buffered: "
-                                 "4 x n^2 x 8 B)"},
+                "config": workload_config(wl, world),
                 "eff_tflops_issued": (sum(st_.flops_fp64 + st_.flops_lowp for st_ in stats)
                                       / (sum(st_.ms_total for st_ in stats) / 1e3) / 1e12),
                 "sweeps": sweeps, "sweeps_lowp": st.sweeps_lowp,
@@ -753,6 +858,16 @@ def run_gpu(args, wl):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 "source_sha256": source_hash()}
+        if wl["kind"] == "evd":
+            line["accuracy_gates"] = evd_gates(acc)
+        if plain is not None:
+            line["plain_fp64"] = plain
+            line["vs_plain_fp64"] = value / plain["value"]
+            line["same_error"] = {"this": evd_gates(acc), "plain_fp64": plain["accuracy_gates"],
+                                  "gates": "|lambda - lambda_true| <= 1e-13 ||A||_2, "
+                                           "||AQ - QD||_F <= 1e-12 ||A||_F, ||Q^T Q - I||_F <= 1e-13 n"}
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -776,31 +891,53 @@ def batch_shapes(wl):
     return [(wl["m"], wl["n"])] * wl["count"]
 
 
-def batched_cpu_sample(wl, shapes, mats_host, budget_s: float, max_items: int | None = None):
+def batched_cpu_sample(wl, shapes, mats_host, budget_s: float, max_items: int | None = None,
+                       threads: int = 1):
     """The oracle on consecutive matrices of the batch (LPT order is not
-    used: matrices are taken as listed) until budget_s has passed.  Returns
-    (seconds, matrices done, work done / work of the whole batch)."""
+    used: matrices are taken as listed) until budget_s has passed, one
+    matrix per thread at a time on `threads` threads (the ctypes calls
+    release the interpreter lock; each oracle call runs on one core).
+    Returns (wall seconds, matrices done, work done / work of the whole
+    batch)."""
+    import threading
+
     import numpy as np
     import oracle
     evd = wl["kind"] == "batched_evd"
     work = lambda mn: mn[1] ** 3 if evd else mn[0] * mn[1] ** 2
     total_work = sum(work(x) for x in shapes)
-    t0, done, w = time.perf_counter(), 0, 0
-    for i, A in enumerate(mats_host):
-        if evd:
-            n = A.shape[0]
-            k = n + (n & 1)
-            Ap = np.zeros((k, k))
-            Ap[:n, :n] = A
-            oracle.pivot_solve(Ap)
-        else:
-            n = A.shape[1]
-            oracle.gesvd(A, b=max(1, n // 2))
-        done += 1
-        w += work(shapes[i])
-        if time.perf_counter() - t0 >= budget_s or (max_items and done >= max_items):
-            break
-    return time.perf_counter() - t0, done, w / total_work
+    lim = len(mats_host) if not max_items else min(max_items, len(mats_host))
+    lock = threading.Lock()
+    state = {"next": 0, "done": 0, "work": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                i = state["next"]
+                if i >= lim or time.perf_counter() - t0 >= budget_s:
+                    return
+                state["next"] = i + 1
+            A = mats_host[i]
+            if evd:
+                n = A.shape[0]
+                k = n + (n & 1)
+                Ap = np.zeros((k, k))
+                Ap[:n, :n] = A
+                oracle.pivot_solve(Ap)
+            else:
+                n = A.shape[1]
+                oracle.gesvd(A, b=max(1, n // 2), threads=1)
+            with lock:
+                state["done"] += 1
+                state["work"] += work(shapes[i])
+
+    ts = [threading.Thread(target=worker) for _ in range(max(1, threads))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return time.perf_counter() - t0, state["done"], state["work"] / total_work
 
 
 def batched_host_sample(wl, shapes, count: int):
@@ -819,10 +956,8 @@ def batched_host_sample(wl, shapes, count: int):
 
 
 def run_batched(args, wl):
-    import numpy as np
     import torch
 
-    import jacobi_inputs as gen
     import paper_2608_28952_gb300 as jg
 
     rank, world, local = dist_env()
@@ -833,6 +968,30 @@ def run_batched(args, wl):
         dist.init_process_group("nccl", device_id=dev)
     jg.lib()
     stream = torch.cuda.current_stream(dev)
+    line = measure_batched(wl, args.steps, args.warmup, args.e2e_steps,
+                           rank == 0 and world == 1 and not args.no_cpu_baseline, world, dev, stream)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_batched(wl, steps, warmup, e2e_steps, want_cpu, world, dev, stream,
+                    plain_loop_s: float = 0.0):
+    """One batched workload: `warmup` untimed plan executions, `steps` timed
+    ones (CUDA events on the stream), accuracy on a spread sample, roofline,
+    end-to-end executions from pinned host memory, the CPU oracle and, when
+    plain_loop_s > 0, the per-matrix plain FP64 path (jacobi_syev /
+    jacobi_gesvd called matrix by matrix) sampled for that many seconds.
+    Returns the bench line (a dict)."""
+    import numpy as np
+    import torch
+
+    import jacobi_inputs as gen
+    import paper_2608_28952_gb300 as jg
+
     evd = wl["kind"] == "batched_evd"
     dtype = torch.float32 if wl["f32"] else torch.float64
     shapes = batch_shapes(wl)
@@ -864,7 +1023,7 @@ def run_batched(args, wl):
             raise RuntimeError(f"status {rc} ({jg.status_string(rc)})")
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     if int((info != 0).sum()) != 0:
@@ -875,14 +1034,14 @@ def run_batched(args, wl):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    stats = [step() for _ in range(args.steps)]
+    stats = [step() for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     ms_max = aggregate_max(ms, world, dev)
-    total = aggregate_sum(float(args.steps * B), world, dev)
+    total = aggregate_sum(float(steps * B), world, dev)
     value = total / (ms_max / 1e3)
     bad = int((info != 0).sum())
 
@@ -924,13 +1083,13 @@ def run_batched(args, wl):
                 "profile": os.path.relpath(prof, ROOT) if prof else None}
 
     e2e = None
-    if args.e2e_steps > 0:
+    if e2e_steps > 0:
         hx = flat0.cpu().pin_memory()
         hy = torch.empty_like(yflat, device="cpu").pin_memory()
         hz = torch.empty_like(zflat, device="cpu").pin_memory()
         hu = torch.empty_like(flat, device="cpu").pin_memory() if not evd else None
         tt = 0.0
-        for i in range(args.e2e_steps + 1):
+        for i in range(e2e_steps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             flat.copy_(hx, non_blocking=True)
@@ -946,51 +1105,87 @@ def run_batched(args, wl):
             if i > 0:
                 tt += t1 - t0
         tt_max = aggregate_max(tt, world, dev)
-        e_total = aggregate_sum(float(args.e2e_steps * B), world, dev)
+        e_total = aggregate_sum(float(e2e_steps * B), world, dev)
         esz = flat.element_size()
         e2e = {"value": e_total / tt_max, "unit": "matrices/s",
                "h2d_bytes_per_step": flat.numel() * esz,
                "d2h_bytes_per_step": (yflat.numel() + zflat.numel()
                                       + (flat.numel() if hu is not None else 0)) * esz,
-               "steps": args.e2e_steps,
+               "steps": e2e_steps,
                "timing": "wall clock: pinned host -> device copy of the batch, plan "
                          "execution, device -> pinned host copy of the results"}
         del hx, hy, hz, hu
+    plan.close()
+    del flat, yflat, zflat, X, Y, Z
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mats = batched_host_sample(wl, shapes, 64)
-        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=12.0)
-        cpu = {"value": B / (secs / frac), "unit": "matrices/s",
-               "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+    if want_cpu:
+        mats = batched_host_sample(wl, shapes, 512)
+        cores = len(os.sched_getaffinity(0))
+        secs, done, frac = batched_cpu_sample(wl, shapes, mats, budget_s=8.0, threads=cores)
+        cpu = {"value": B / (secs / frac), "unit": "matrices/s", "cores": cores, "kind": "oracle",
                "sample": f"the first {done} matrices of the batch ({frac:.2e} of its "
-                         f"{'n^3' if evd else 'm n^2'} work), {secs:.1f} s, extrapolated "
-                         f"by work to all {B}; FP64 oracle (scalar parallel-ordered "
-                         f"Jacobi per matrix), one thread"}
+                         f"{'n^3' if evd else 'm n^2'} work), {secs:.1f} s wall on {cores} threads "
+                         f"(one matrix per thread at a time), extrapolated by work to all {B}; "
+                         f"FP64 oracle (scalar parallel-ordered Jacobi per matrix)",
+               "extrapolated": True, "extrapolation_factor": 1.0 / frac, "measured_s": secs}
 
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if wl["f32"] else "f64", "data": "synthetic (seeded; see config)",
-                "config": {"workload": wl["desc"], "count": B, "seed": wl["seed"],
-                           **({"n_range": [wl["lo"], wl["hi"]]} if evd else
-                              {"m": wl["m"], "n": wl["n"]}),
-                           "plan_shape": {"threads": shape[0], "smem_kmax": shape[1],
-                                          "grid": shape[2]},
-                           "autotune_s": tune_s, "parallelism": f"one batch per rank x{world}",
-                           "l2": "inputs larger than L2 (the batch: "
-                                 f"{flat.numel() * flat.element_size() / 1e9:.1f} GB)"},
-                "eff_tflops_issued": achieved, "accuracy": acc,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(sum(s_.launches for s_ in stats)), "clocks": clocks,
-                "source_sha256": source_hash()}
-        print(json.dumps(line))
-    plan.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    plain = None
+    if plain_loop_s > 0:
+        plain = plain_loop_sample(wl, shapes, views0, plain_loop_s, dev, stream)
+    del flat0, views0
+
+    line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if wl["f32"] else "f64", "data": "synthetic (seeded; see config)",
+            "config": workload_config(wl, world),
+            "plan": {"shape": {"threads": shape[0], "smem_kmax": shape[1], "grid": shape[2]},
+                     "autotune_s": tune_s,
+                     "batch_gb": sum(m * n for m, n in shapes) * (4 if wl["f32"] else 8) / 1e9},
+            "eff_tflops_issued": achieved, "accuracy": acc,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(s_.launches for s_ in stats)), "clocks": clocks,
+            "source_sha256": source_hash()}
+    if plain is not None:
+        line["plain_fp64_loop"] = plain
+        line["vs_plain_fp64_loop"] = value / plain["value"] if plain["value"] else None
+    return line
+
+
+def plain_loop_sample(wl, shapes, views, budget_s, dev, stream):
+    """The per-matrix plain FP64 path on the batch: jacobi_syev (jacobi_gesvd
+    for the tall batch) called matrix by matrix on FP64 copies of the first
+    matrices, b = 16, until budget_s has passed; the rate is extrapolated to
+    the whole batch by n^3 (m n^2) work."""
+    import torch
+
+    import paper_2608_28952_gb300 as jg
+    evd = wl["kind"] == "batched_evd"
+    work = lambda mn: mn[1] ** 3 if evd else mn[0] * mn[1] ** 2
+    total_work = sum(work(x) for x in shapes)
+    secs, done, w = 0.0, 0, 0
+    p = jg.params(b=16)
+    for i, (m, n) in enumerate(shapes):
+        X = views[i].double().t().contiguous().t()
+        out = torch.empty(n, dtype=torch.float64, device=dev)
+        V = jg.colmajor_empty(n, n, torch.float64, dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, _ = (jg.jacobi_syev if evd else jg.jacobi_gesvd)(X, out, V, p, stream)
+        secs += time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError(f"plain FP64 path: status {rc}")
+        done += 1
+        w += work((m, n))
+        if secs >= budget_s:
+            break
+    frac = w / total_work
+    return {"value": len(shapes) / (secs / frac), "unit": "matrices/s",
+            "sample": f"{'jacobi_syev' if evd else 'jacobi_gesvd'} (FP64, b=16) on the first {done} "
+                      f"matrices ({frac:.2e} of the batch's {'n^3' if evd else 'm n^2'} work), "
+                      f"{secs:.1f} s wall clock around the calls, extrapolated by work",
+            "extrapolated": True, "extrapolation_factor": 1.0 / frac, "measured_s": secs}
 
 
 def run_ncu_case(args, wl):
@@ -1046,12 +1241,14 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="evd4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="mixed8192emu", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--inner-max-sweeps", type=int, default=0,
                     help="cap on the sweeps of one pivot solve (0 = the library's automatic choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain FP64 solve and the batched forms beside the default line")
     ap.add_argument("--ncu-case", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3 and not args.ncu_case:

@@ -219,3 +219,52 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the same configuration object as the GPU arm's line, the sample's real
+    # duration as ms_per_step and the extrapolation stated
+    assert d["config"] == bench.workload_config(bench.WORKLOADS["evd256"], 1)
+    assert d["config"]["n"] == 256 and d["config"]["b"] == 16 and d["config"]["seed"] == 1
+    assert cb["extrapolated"] is True and cb["extrapolation_factor"] == 15 * 10
+    assert abs(d["ms_per_step"] / 1e3 - cb["seconds_per_step"]) <= 1e-9 * d["ms_per_step"]
+    assert d["ms_per_step"] < 1e3 / d["value"]        # one sampled step, not the extrapolated solve
+
+
+def test_default_workload_is_the_metrics_comparison():
+    """The default line is the mixed form at n = 8192, b = 128 with the plain
+    FP64 solve of the same matrix and the three batched forms beside it."""
+    import argparse
+    wl = bench.WORKLOADS["mixed8192emu"]
+    assert wl["compare_plain"] and wl["compare_batched"]
+    assert wl["n"] == 8192 and wl["b"] == 128 and wl["seed"] == 6 and wl["precision"] == 2
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert 'ap.add_argument("--workload", default="mixed8192emu"' in src
+    cfg = bench.workload_config(wl, 1)
+    assert cfg["precision"] == "mixed bf16x3" and cfg["fp64_products"] is True
+    assert bench.workload_config(bench.WORKLOADS["batched_f64"], 1)["count"] == 20000
+
+
+def test_evd_gates():
+    ok = dict(max_abs_eig_err_over_norm2=5e-15, residual_fro_over_normA=6e-14, orth_fro_over_n=1e-15)
+    assert bench.evd_gates(ok)["all"] is True
+    bad = dict(ok, residual_fro_over_normA=2e-12)
+    g = bench.evd_gates(bad)
+    assert g["all"] is False and g["residual_le_1e-12"] is False and g["eig_le_1e-13"] is True
+
+
+def test_batched_cpu_sample_uses_threads_and_counts_work():
+    """The batched CPU baseline: the oracle on consecutive matrices, one per
+    thread at a time; the work fraction is the n^3 share of the batch done."""
+    import numpy as np
+    import jacobi_inputs as gen
+    wl = dict(kind="batched_evd")
+    shapes = [(n, n) for n in (8, 12, 16, 20, 24, 9)]
+    mats = [gen.sym_gaussian(n, 60 + n) for _, n in shapes]
+    secs, done, frac = bench.batched_cpu_sample(wl, shapes, mats, budget_s=30.0, threads=3)
+    assert done == len(shapes) and abs(frac - 1.0) < 1e-12 and secs > 0
+    secs, done, frac = bench.batched_cpu_sample(wl, shapes, mats, budget_s=30.0, max_items=2, threads=2)
+    tot = sum(n ** 3 for _, n in shapes)
+    assert done == 2 and abs(frac - (8 ** 3 + 12 ** 3) / tot) < 1e-12
+    wl_svd = dict(kind="batched_svd")
+    sh = [(64, 8)] * 4
+    G = [gen.tall_gaussian(64, 8, 70 + i, dtype=np.float64) for i in range(4)]
+    secs, done, frac = bench.batched_cpu_sample(wl_svd, sh, G, budget_s=30.0, threads=4)
+    assert done == 4 and abs(frac - 1.0) < 1e-12
