@@ -173,7 +173,8 @@ def test_stop_statistic_every_sweep(jg, case):
         b, conv, tol = 16, 1, 4 * U
     n = A.shape[0]
     _, _, _, st_or, s_or = oracle.syev(A, b=b, conv=conv, tol=tol)
-    w, Q, D, st = jg.syev(A, b=b, conv=conv, tol=tol)
+    w, Q, D_fin, st = jg.syev(A, b=b, conv=conv, tol=tol)
+    D_fin = D_fin.cpu().numpy()
     assert s_or == 0 and st.status == 0 and abs(st.sweeps - st_or.sweeps) <= 1
     S = min(st.sweeps, st_or.sweeps)
     (off_h, rel_h), its = _per_sweep(jg, A, b, conv, tol, S)
@@ -196,11 +197,12 @@ def test_stop_statistic_every_sweep(jg, case):
             s, off_h[s], st_or.off_hist[s], gap)
     # the final statistic passes the stop test and is the oracle's value on
     # the returned iterate
+    assert abs(st.off_final - oracle.off_norm(D_fin)) <= tol_sum * st.off_final + 1e-300
     if conv == 0:
         assert st.off_final <= tol * st.norm_fro or st.stalled
     else:
         assert st.rel_final <= tol or st.stalled
-        assert abs(st.rel_final - oracle.rel_off(D.cpu().numpy())) <= REL_TOL * st.rel_final
+        assert abs(st.rel_final - oracle.rel_off(D_fin)) <= REL_TOL * st.rel_final
 
 
 def test_trajectory_of_a_well_conditioned_solve(jg):
