@@ -480,6 +480,25 @@ int jacobi_syev_step_lowp(int np, float* A, int lda, float* Q, int ldq, const ja
                           int step, void* stream);
 
 /*
+ * jacobi_wait_selftest -- failure detection on the tensor cores, exercised:
+ * the paper has no counterpart.  The tcgen05 kernels (the mixed forms'
+ * updates, the emulated FP64 products, jacobi_lowp_gemm, jacobi_f64emu_gemm)
+ * wait on mbarriers that their own MMAs arrive at; every such wait is
+ * bounded (about 2 s by the global timer, and a cap on the polls), and a
+ * wait that runs out sets the call's error word, skips the rest of the
+ * tile, frees the CTA's tensor memory and returns, so the call returns
+ * JACOBI_ERR_TIMEOUT and the CUDA context stays usable.  This entry point
+ * runs one CTA through the same steps: allocate tensor memory, initialise an
+ * mbarrier, wait on it with the bound limit_ms (1 .. 2000 ms), free the
+ * tensor memory.  arrive = 1: one thread arrives, the wait completes,
+ * returns 0.  arrive = 0: nothing arrives, the wait runs out after about
+ * limit_ms, returns JACOBI_ERR_TIMEOUT.  Blocks until done.
+ * Returns 0, JACOBI_ERR_TIMEOUT, -1 (arrive not 0 or 1), -2 (limit_ms out
+ * of range), JACOBI_ERR_ALLOC, JACOBI_ERR_CUDA.
+ */
+int jacobi_wait_selftest(int arrive, double limit_ms, void* stream);
+
+/*
  * jacobi_ordering_table -- the library's pair schedule for N blocks
  * (host-side logic, no GPU needed): kind is JACOBI_ORDER_*; pairs receives
  * 2 ints (I < J, 0-based) per pair, step after step (room for N*(N-1) ints);

@@ -137,6 +137,7 @@ SIGNATURES = {
     "jacobi_f64emu_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
     "jacobi_rotation_params": (_I, [_I, _P, _P, _P, _D, _P, _P]),
     "jacobi_off_norm": (_I, [_I, _P, _I, _I, C.POINTER(C.c_double), _P]),
+    "jacobi_wait_selftest": (_I, [_I, _D, _P]),
 }
 
 _LIB = None
@@ -411,6 +412,13 @@ def jacobi_syev_step_lowp(A, Q, step: int, p: jacobi_params | None = None, strea
                                        _colmajor_ld(Q) if Q is not None else np_,
                                        C.byref(p) if p is not None else None, step,
                                        _stream_ptr(stream))
+
+
+def jacobi_wait_selftest(arrive: bool, limit_ms: float, stream=None) -> int:
+    """C ``jacobi_wait_selftest``: one CTA waits on an mbarrier with the
+    tensor-core kernels' bounded wait (limit_ms); 0 when arrive, else
+    JACOBI_ERR_TIMEOUT once the limit has passed."""
+    return lib().jacobi_wait_selftest(int(arrive), float(limit_ms), _stream_ptr(stream))
 
 
 def jacobi_ordering_table(kind: int, N: int):

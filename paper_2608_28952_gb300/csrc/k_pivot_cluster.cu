@@ -20,8 +20,29 @@
 // Quads (2x2 cross-pair blocks) are spread over all C * blockDim threads.
 // Every loop runs the same trip count in all CTAs of a cluster, so the
 // cluster barriers always match.
+//
+// Two schedules of the rounds, with the same arithmetic (bit for bit the
+// same results):
+//   * split (kFused = false): phase A rotates the quads of round g; after a
+//     cluster barrier every CTA chooses all rotations of round g + 1 from its
+//     own diagonal replica while the other threads rotate V by round g; a
+//     split cluster barrier separates that choice from the next zeroing;
+//   * fused (kFused = true, the default): one phase and one cluster barrier
+//     per round.  Round g + 1 pairs every index with one of round g's other
+//     pairs, so each of its pivot entries a_p'q' is one entry of one quad of
+//     round g.  Those few quads ("leading quads") are rotated first, by the
+//     first warp(s) of the CTAs, and the thread that rotates one takes the
+//     diagonal of p' and q' through round g and chooses round g + 1's
+//     rotation right away, writing its parameters and the two diagonal
+//     entries into every CTA of the cluster (double-buffered by round
+//     parity).  The other threads rotate the remaining quads and this CTA's
+//     rows of V by round g meanwhile.  Each rotation is chosen once per
+//     cluster instead of once per CTA, and the choice overlaps the round's
+//     bulk FP64 work instead of following it.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "internal.h"
 #include "jacobi_core.cuh"
@@ -45,10 +66,38 @@ size_t pivot_cluster_smem(int k, int C)
     const int half = k / 2;
     const size_t chunk = (size_t)split_max_chunk(k, C);
     const size_t vrows = (size_t)(k / C) * k;
-    return (chunk + vrows + 2 * (size_t)k + 8 * (size_t)half) * sizeof(double) +
+    return (chunk + vrows + 4 * (size_t)k + 8 * (size_t)half) * sizeof(double) +
            6 * (size_t)half * sizeof(int) + 64;
 }
 
+// The round-robin order over k indices (nr = k - 1 rounds): position 0 holds
+// index 0; position pos >= 1 holds index 1 + (pos - 1 + rd) mod nr; pair ee
+// joins positions ee and k - 1 - ee (the rule of choose() below).
+__device__ __forceinline__ int rr_index_at(int pos, int rd, int nr)
+{
+    if (pos == 0) return 0;
+    int v = pos - 1 + rd;
+    if (v >= nr) v -= nr;
+    return 1 + v;
+}
+__device__ __forceinline__ int rr_position_of(int x, int rd, int nr)
+{
+    if (x == 0) return 0;
+    int v = x - 1 - rd;
+    if (v < 0) v += nr;
+    return 1 + v;
+}
+__device__ __forceinline__ int rr_pair_of(int x, int rd, int k)
+{
+    const int pos = rr_position_of(x, rd, k - 1);
+    return pos < k - 1 - pos ? pos : k - 1 - pos;
+}
+__device__ __forceinline__ int rr_partner_of(int x, int rd, int k)
+{
+    return rr_index_at(k - 1 - rr_position_of(x, rd, k - 1), rd, k - 1);
+}
+
+template <bool kFused>
 __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, const unsigned* qtab)
 {
     extern __shared__ __align__(16) double csm[];
@@ -76,9 +125,11 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     }();
     double* my_chunk = csm;
     double* Vl = my_chunk + chunk_max;       // rows x k (ld rows): V(r_lo + i, j) at Vl[i + rows j]
-    double* dhi = Vl + (size_t)rows * k;     // diagonal replica
+    double* dhi = Vl + (size_t)rows * k;     // diagonal replica (fused: round-parity buffer 0)
     double* dlo = dhi + k;
-    double* rtau = dlo + k;                  // rotation parameters, two slots of half each
+    double* dhi1 = dlo + k;                  // fused: round-parity buffer 1
+    double* dlo1 = dhi1 + k;
+    double* rtau = dlo1 + k;                 // rotation parameters, two slots of half each
     double* rs = rtau + 2 * half;
     double* rt = rs + 2 * half;
     double* rapq = rt + 2 * half;
@@ -86,6 +137,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     int* rq = rp + 2 * half;
     int* ron = rq + 2 * half;
     __shared__ int s_cnt[2];   // rotations chosen per sweep (by sweep parity)
+    __shared__ int s_cntg[4];  // fused: rank 0's copy counts a sweep's rotations (sweep mod 4)
     __shared__ double s_red[PC_T / 32];
     __shared__ double s_part[PC_MAXC8];
     __shared__ int s_dest[256];
@@ -188,86 +240,287 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
             }
         }
     };
-    if (max_sweeps > 0) {
-        if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
-        __syncthreads();
-        if (tid < half) choose(0, 0);
-        __syncthreads();
-        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-    }
-    for (int sw = 0; sw < max_sweeps; ++sw) {
-        for (int rd = 0; rd < nr; ++rd) {
-            const int g = sw * nr + rd, so = (g & 1) * half;
-            // phase A: quads over the whole cluster
-            for (int qi = gtid; qi < nq; qi += gnt) {
-                int e1, e2;
-                quad_of(qtab, qi, e1, e2);
-                const int on1 = ron[so + e1], on2 = ron[so + e2];
-                if (!(on1 | on2)) continue;
-                const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
-                double* a00 = ap.at(p1, p2);
-                double* a01 = ap.at(p1, q2);
-                double* a10 = ap.at(q1, p2);
-                double* a11 = ap.at(q1, q2);
-                double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
-                if (on1) {
-                    const double sv = rs[so + e1], tauv = rtau[so + e1];
-                    rot2(sv, tauv, x00, x10);
-                    rot2(sv, tauv, x01, x11);
-                }
-                if (on2) {
-                    const double sv = rs[so + e2], tauv = rtau[so + e2];
-                    rot2(sv, tauv, x00, x01);
-                    rot2(sv, tauv, x10, x11);
-                }
-                *a00 = x00;
-                *a01 = x01;
-                *a10 = x10;
-                *a11 = x11;
-            }
-            // diagonal replica (every CTA): the exact 2x2 diagonal form
-            for (int ee = tid; ee < half; ee += nt) {
-                if (!ron[so + ee]) continue;
-                const int p = rp[so + ee], q = rq[so + ee];
-                const double tv = rt[so + ee], apq = rapq[so + ee];
-                dd_add_prod(dhi[p], dlo[p], tv, -apq, 1.0);
-                dd_add_prod(dhi[q], dlo[q], tv, apq, 1.0);
-            }
-            // every CTA has read round g's a_pq: rank 0 zeroes them
-            __syncwarp();
-            asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-            if (r == 0)
-                for (int ee = tid; ee < half; ee += nt)
-                    if (ron[so + ee]) *ap.at(rq[so + ee], rp[so + ee]) = 0.0;
-            cluster.sync();
-            // phase B
-            if (tid < half) {
-                if (!(rd == nr - 1 && sw + 1 == max_sweeps)) choose(g + 1, (g + 1) & 1);
-            } else {
-                for (int it = tid - half; it < half * rows; it += nt - half) {
-                    const int ee = it / rows, i = it - ee * rows;
-                    if (!ron[so + ee]) continue;
-                    const int p = rp[so + ee], q = rq[so + ee];
-                    double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
-                    rot2(rs[so + ee], rtau[so + ee], vp, vq);
-                    Vl[i + (size_t)rows * p] = vp;
-                    Vl[i + (size_t)rows * q] = vq;
-                }
-            }
+    double* dfin = dhi;   // the final diagonal (hi, rounded once with lo)
+    if constexpr (!kFused) {
+        if (max_sweeps > 0) {
+            if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
+            __syncthreads();
+            if (tid < half) choose(0, 0);
             __syncthreads();
             asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
         }
-        const int cnt = s_cnt[sw & 1];
-        total_rot += cnt;
-        sweeps = sw + 1;
+        for (int sw = 0; sw < max_sweeps; ++sw) {
+            for (int rd = 0; rd < nr; ++rd) {
+                const int g = sw * nr + rd, so = (g & 1) * half;
+                // phase A: quads over the whole cluster
+                for (int qi = gtid; qi < nq; qi += gnt) {
+                    int e1, e2;
+                    quad_of(qtab, qi, e1, e2);
+                    const int on1 = ron[so + e1], on2 = ron[so + e2];
+                    if (!(on1 | on2)) continue;
+                    const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
+                    double* a00 = ap.at(p1, p2);
+                    double* a01 = ap.at(p1, q2);
+                    double* a10 = ap.at(q1, p2);
+                    double* a11 = ap.at(q1, q2);
+                    double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                    if (on1) {
+                        const double sv = rs[so + e1], tauv = rtau[so + e1];
+                        rot2(sv, tauv, x00, x10);
+                        rot2(sv, tauv, x01, x11);
+                    }
+                    if (on2) {
+                        const double sv = rs[so + e2], tauv = rtau[so + e2];
+                        rot2(sv, tauv, x00, x01);
+                        rot2(sv, tauv, x10, x11);
+                    }
+                    *a00 = x00;
+                    *a01 = x01;
+                    *a10 = x10;
+                    *a11 = x11;
+                }
+                // diagonal replica (every CTA): the exact 2x2 diagonal form
+                for (int ee = tid; ee < half; ee += nt) {
+                    if (!ron[so + ee]) continue;
+                    const int p = rp[so + ee], q = rq[so + ee];
+                    const double tv = rt[so + ee], apq = rapq[so + ee];
+                    dd_add_prod(dhi[p], dlo[p], tv, -apq, 1.0);
+                    dd_add_prod(dhi[q], dlo[q], tv, apq, 1.0);
+                }
+                // every CTA has read round g's a_pq: rank 0 zeroes them
+                __syncwarp();
+                asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+                if (r == 0)
+                    for (int ee = tid; ee < half; ee += nt)
+                        if (ron[so + ee]) *ap.at(rq[so + ee], rp[so + ee]) = 0.0;
+                cluster.sync();
+                // phase B
+                if (tid < half) {
+                    if (!(rd == nr - 1 && sw + 1 == max_sweeps)) choose(g + 1, (g + 1) & 1);
+                } else {
+                    for (int it = tid - half; it < half * rows; it += nt - half) {
+                        const int ee = it / rows, i = it - ee * rows;
+                        if (!ron[so + ee]) continue;
+                        const int p = rp[so + ee], q = rq[so + ee];
+                        double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                        rot2(rs[so + ee], rtau[so + ee], vp, vq);
+                        Vl[i + (size_t)rows * p] = vp;
+                        Vl[i + (size_t)rows * q] = vq;
+                    }
+                }
+                __syncthreads();
+                asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+            }
+            const int cnt = s_cnt[sw & 1];
+            total_rot += cnt;
+            sweeps = sw + 1;
+            __syncthreads();
+            if (tid == 0) s_cnt[sw & 1] = 0;   // reused by sweep sw + 2 (chosen after further barriers)
+            if (cnt == 0) break;
+        }
+        __syncwarp();
+        if (max_sweeps > 0) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+        for (int x = tid; x < k; x += nt) dhi[x] += dlo[x];  // hi + lo, rounded once
         __syncthreads();
-        if (tid == 0) s_cnt[sw & 1] = 0;   // reused by sweep sw + 2 (chosen after further barriers)
-        if (cnt == 0) break;
+    } else {
+        // ---- fused schedule: one phase and one cluster barrier per round
+        double* Dh[2] = {dhi, dhi1};
+        double* Dl[2] = {dlo, dlo1};
+        const int upc = (half + C - 1) / C;            // leading units per CTA (next-round pairs)
+        const int lw = (upc + 31) / 32 * 32;           // threads of the leading warps
+        const int bt = nt - lw, btid = tid - lw;       // the bulk threads
+        int* cnt0 = cluster.map_shared_rank(s_cntg, 0);
+        int G = 0;                                     // rounds run
+        // rotation of round g + 1 for the pair (x, y) of that round (index epc),
+        // x, y already rotated by round g (their entry axy and diagonals given),
+        // written with the two diagonal entries into every CTA of the cluster
+        auto publish = [&](int sn, int nb, int epc, int x, int y, double axy, double hx, double lx,
+                           double hy, double ly, bool want, int cslot) {
+            const int p = x < y ? x : y, q = x < y ? y : x;
+            const double app = p == x ? hx : hy, aqq = p == x ? hy : hx;
+            bool on = false;
+            double sv = 0.0, tv = 0.0, tauv = 0.0;
+            if (want) {
+                on = rotation_wanted(app, aqq, axy, tol);
+                if (on) schur2(app, aqq, axy, sv, tv, tauv);
+            }
+            const int o = sn + epc;
+            for (int u = 0; u < C; ++u) {
+                *cluster.map_shared_rank(&Dh[nb][x], u) = hx;
+                *cluster.map_shared_rank(&Dl[nb][x], u) = lx;
+                *cluster.map_shared_rank(&Dh[nb][y], u) = hy;
+                *cluster.map_shared_rank(&Dl[nb][y], u) = ly;
+                if (!want) continue;
+                *cluster.map_shared_rank(&rp[o], u) = p;
+                *cluster.map_shared_rank(&rq[o], u) = q;
+                *cluster.map_shared_rank(&ron[o], u) = on ? 1 : 0;
+                if (on) {
+                    *cluster.map_shared_rank(&rtau[o], u) = tauv;
+                    *cluster.map_shared_rank(&rs[o], u) = sv;
+                    *cluster.map_shared_rank(&rt[o], u) = tv;
+                    *cluster.map_shared_rank(&rapq[o], u) = axy;
+                }
+            }
+            if (on) atomicAdd(&cnt0[cslot & 3], 1);
+        };
+        if (max_sweeps > 0) {
+            if (tid < 4) s_cntg[tid] = 0;
+            __syncthreads();
+            // round 0, chosen by every CTA from its own copy (counted by rank 0)
+            for (int ee = tid; ee < half; ee += nt) {
+                const int pa = ee, pb = k - 1 - ee;
+                const int ia = rr_index_at(pa, 0, nr), ib = rr_index_at(pb, 0, nr);
+                const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
+                const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
+                const bool on = rotation_wanted(app, aqq, apq, tol);
+                rp[ee] = p;
+                rq[ee] = q;
+                ron[ee] = on;
+                if (on) {
+                    double sv, tv, tauv;
+                    schur2(app, aqq, apq, sv, tv, tauv);
+                    rtau[ee] = tauv;
+                    rs[ee] = sv;
+                    rt[ee] = tv;
+                    rapq[ee] = apq;
+                    if (r == 0) atomicAdd(&s_cntg[0], 1);
+                }
+            }
+            cluster.sync();
+        }
+        for (int sw = 0; sw < max_sweeps; ++sw) {
+            // the counter of sweep sw + 2 was last read after sweep sw - 2
+            if (r == 0 && tid == 0) s_cntg[(sw + 2) & 3] = 0;
+            for (int rd = 0; rd < nr; ++rd) {
+                const int g = sw * nr + rd, so = (g & 1) * half, sn = half - so;
+                const int cb = g & 1, nb = cb ^ 1;
+                const bool last = rd == nr - 1 && sw + 1 == max_sweeps;
+                const int rdn = rd + 1 == nr ? 0 : rd + 1;
+                const int cslot = rd + 1 == nr ? sw + 1 : sw;
+                // diagonal entry x through round g (the exact 2x2 diagonal form)
+                auto diag_after = [&](int x, double& h, double& l) {
+                    h = Dh[cb][x];
+                    l = Dl[cb][x];
+                    const int eg = rr_pair_of(x, rd, k);
+                    if (ron[so + eg]) {
+                        if (x == rp[so + eg]) dd_add_prod(h, l, rt[so + eg], -rapq[so + eg], 1.0);
+                        else dd_add_prod(h, l, rt[so + eg], rapq[so + eg], 1.0);
+                    }
+                };
+                if (tid < lw) {
+                    const int ep = r + C * tid;   // this unit's pair of round g + 1
+                    if (ep < half) {
+                        const int x0 = rr_index_at(ep, rdn, nr), y0 = rr_index_at(k - 1 - ep, rdn, nr);
+                        if (last) {
+                            double hx, lx, hy, ly;
+                            diag_after(x0, hx, lx);
+                            diag_after(y0, hy, ly);
+                            publish(sn, nb, ep, x0, y0, 0.0, hx, lx, hy, ly, false, 0);
+                        } else {
+                            const int ea = rr_pair_of(x0, rd, k), eb = rr_pair_of(y0, rd, k);
+                            const int e1 = ea < eb ? ea : eb, e2 = ea < eb ? eb : ea;
+                            const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
+                            const int pp1 = rr_partner_of(p1, rdn, k), pq1 = rr_partner_of(q1, rdn, k);
+                            const bool h1 = pp1 == p2 || pp1 == q2, h2 = pq1 == p2 || pq1 == q2;
+                            const int ep1 = h1 ? rr_pair_of(p1, rdn, k) : half;
+                            const int ep2 = h2 ? rr_pair_of(q1, rdn, k) : half;
+                            if ((ep1 < ep2 ? ep1 : ep2) == ep) {   // this unit leads quad (e1, e2)
+                                const int on1 = ron[so + e1], on2 = ron[so + e2];
+                                double* a00 = ap.at(p1, p2);
+                                double* a01 = ap.at(p1, q2);
+                                double* a10 = ap.at(q1, p2);
+                                double* a11 = ap.at(q1, q2);
+                                double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                                if (on1) {
+                                    const double sv = rs[so + e1], tauv = rtau[so + e1];
+                                    rot2(sv, tauv, x00, x10);
+                                    rot2(sv, tauv, x01, x11);
+                                }
+                                if (on2) {
+                                    const double sv = rs[so + e2], tauv = rtau[so + e2];
+                                    rot2(sv, tauv, x00, x01);
+                                    rot2(sv, tauv, x10, x11);
+                                }
+                                if (on1 | on2) {
+                                    *a00 = x00;
+                                    *a01 = x01;
+                                    *a10 = x10;
+                                    *a11 = x11;
+                                }
+                                if (h1) {
+                                    double hx, lx, hy, ly;
+                                    diag_after(p1, hx, lx);
+                                    diag_after(pp1, hy, ly);
+                                    publish(sn, nb, ep1, p1, pp1, pp1 == p2 ? x00 : x01, hx, lx, hy, ly, true, cslot);
+                                }
+                                if (h2) {
+                                    double hx, lx, hy, ly;
+                                    diag_after(q1, hx, lx);
+                                    diag_after(pq1, hy, ly);
+                                    publish(sn, nb, ep2, q1, pq1, pq1 == p2 ? x10 : x11, hx, lx, hy, ly, true, cslot);
+                                }
+                            }
+                        }
+                    }
+                    // round g's pivot entries (read when round g was chosen, before
+                    // the last barrier; no quad of round g holds them)
+                    if (ep < half && ron[so + ep]) *ap.at(rq[so + ep], rp[so + ep]) = 0.0;
+                } else {
+                    // the other quads of round g over the cluster's bulk threads
+                    for (int qi = r * bt + btid; qi < nq; qi += C * bt) {
+                        int e1, e2;
+                        quad_of(qtab, qi, e1, e2);
+                        const int on1 = ron[so + e1], on2 = ron[so + e2];
+                        if (!(on1 | on2)) continue;
+                        const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
+                        if (!last) {   // a leading quad: rotated by its leading unit
+                            const int pp1 = rr_partner_of(p1, rdn, k), pq1 = rr_partner_of(q1, rdn, k);
+                            if (pp1 == p2 || pp1 == q2 || pq1 == p2 || pq1 == q2) continue;
+                        }
+                        double* a00 = ap.at(p1, p2);
+                        double* a01 = ap.at(p1, q2);
+                        double* a10 = ap.at(q1, p2);
+                        double* a11 = ap.at(q1, q2);
+                        double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                        if (on1) {
+                            const double sv = rs[so + e1], tauv = rtau[so + e1];
+                            rot2(sv, tauv, x00, x10);
+                            rot2(sv, tauv, x01, x11);
+                        }
+                        if (on2) {
+                            const double sv = rs[so + e2], tauv = rtau[so + e2];
+                            rot2(sv, tauv, x00, x01);
+                            rot2(sv, tauv, x10, x11);
+                        }
+                        *a00 = x00;
+                        *a01 = x01;
+                        *a10 = x10;
+                        *a11 = x11;
+                    }
+                    // this CTA's rows of V by round g
+                    for (int it = btid; it < half * rows; it += bt) {
+                        const int ee = it / rows, i = it - ee * rows;
+                        if (!ron[so + ee]) continue;
+                        const int p = rp[so + ee], q = rq[so + ee];
+                        double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                        rot2(rs[so + ee], rtau[so + ee], vp, vq);
+                        Vl[i + (size_t)rows * p] = vp;
+                        Vl[i + (size_t)rows * q] = vq;
+                    }
+                }
+                cluster.sync();
+                ++G;
+            }
+            const int cnt = *cluster.map_shared_rank(&s_cntg[sw & 3], 0);
+            total_rot += cnt;
+            sweeps = sw + 1;
+            if (cnt == 0) break;
+        }
+        dfin = Dh[G & 1];
+        double* dlfin = Dl[G & 1];
+        for (int x = tid; x < k; x += nt) dfin[x] += dlfin[x];  // hi + lo, rounded once
+        __syncthreads();
     }
-    __syncwarp();
-    if (max_sweeps > 0) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-    for (int x = tid; x < k; x += nt) dhi[x] += dlo[x];  // hi + lo, rounded once
-    __syncthreads();
 
     // ---- permutation (identical in every CTA: same diagonal replica; the
     // QRCP order of Sec. 2.1's pivoting step is computed by rank 0 on the
@@ -312,11 +565,11 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     for (int x = tid; x < k; x += nt) {
         int dest = x;
         if (a.order == 1 && total_rot > 0 && pc_pair_map(I, J, b, x) < a.n_real) {
-            const double dx = dhi[x];
+            const double dx = dfin[x];
             int rr = 0;
             for (int y = 0; y < k; ++y) {
                 if (y == x || pc_pair_map(I, J, b, y) >= a.n_real) continue;
-                const double dy = dhi[y];
+                const double dy = dfin[y];
                 rr += (dy > dx) || (dy == dx && y < x);
             }
             dest = s_pos[rr];
@@ -339,7 +592,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
             const int ii = idx % k, jj = idx / k;
             const int hi_row = ii >= jj ? ii : jj;
             if (hi_row < my_lo || hi_row >= my_hi) continue;
-            const double v = ii == jj ? dhi[ii] : my_chunk[tri(hi_row) + (ii >= jj ? jj : ii) - ap.sp.base[r]];
+            const double v = ii == jj ? dfin[ii] : my_chunk[tri(hi_row) + (ii >= jj ? jj : ii) - ap.sp.base[r]];
             const size_t g = pc_pair_map(I, J, b, s_dest[ii]) + (size_t)a.ld * pc_pair_map(I, J, b, s_dest[jj]);
             if (a.Aout32) a.Aout32[g] = (float)v;
             else a.Aout[g] = v;
@@ -375,14 +628,19 @@ int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
     return best;
 }
 
+// JACOBI_PIVOT_SCHEDULE=split selects the two-phase schedule (the same
+// results bit for bit); the fused schedule is the default.
 cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab, cudaStream_t s)
 {
     if (a.npairs <= 0) return cudaSuccess;
+    const char* env = getenv("JACOBI_PIVOT_SCHEDULE");
+    const bool fused = !(env && strcmp(env, "split") == 0);
+    auto kern = fused ? k_pivot_cluster<true> : k_pivot_cluster<false>;
     const size_t smem = pivot_cluster_smem(a.k, C);
-    cudaError_t e = cudaFuncSetAttribute(k_pivot_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_pivot_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -397,7 +655,7 @@ cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pivot_cluster, a, C, qtab);
+    return cudaLaunchKernelEx(&cfg, kern, a, C, qtab);
 }
 
 }  // namespace jac

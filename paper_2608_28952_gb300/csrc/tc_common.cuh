@@ -84,11 +84,13 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Wait until the mbarrier at `bar` completes the phase with parity `par`;
-// false if about 2 s pass first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par)
+// false if limit_ns (default about 2 s) pass first by the global timer, or
+// after 2^28 polls whatever the timer says.
+constexpr uint64_t kMbarWaitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par, uint64_t limit_ns = kMbarWaitNs)
 {
     const uint64_t t0 = global_ns();
-    for (;;) {
+    for (uint32_t polls = 0;; ++polls) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -97,7 +99,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par)
             : "r"(bar), "r"(par)
             : "memory");
         if (ok) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > limit_ns || polls >= (1u << 28)) return false;
     }
 }
 

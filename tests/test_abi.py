@@ -250,3 +250,12 @@ def test_noalloc_argument_checks_come_before_any_device_work(jg):
     assert call(64, null, 64, fake, 64, jg.params(b=8)) == -2
     assert call(64, fake, 63, fake, 64, jg.params(b=8)) == -3
     assert call(64, fake, 64, fake, 63, jg.params(b=8)) == -5
+
+
+def test_wait_selftest_argument_checks(jg):
+    """The self-test of the bounded wait checks its arguments on the host."""
+    L = jg.lib()
+    assert L.jacobi_wait_selftest(2, 10.0, C.c_void_p(0)) == -1
+    assert L.jacobi_wait_selftest(0, 0.5, C.c_void_p(0)) == -2
+    assert L.jacobi_wait_selftest(0, 5000.0, C.c_void_p(0)) == -2
+    assert L.jacobi_wait_selftest(1, float("nan"), C.c_void_p(0)) == -2

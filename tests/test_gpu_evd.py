@@ -399,3 +399,27 @@ def test_full_size_n4096_b64(jg):
     w, Q = _np(w), _np(Q)
     assert st.status == 0
     check(A, w, Q, np.sort(lam))
+
+
+@pytest.mark.parametrize("np_,b,cl", [(256, 32, "2"), (512, 64, "4"), (1024, 128, "4"), (768, 64, "8")])
+def test_pivot_schedules_agree_bit_for_bit(jg, monkeypatch, np_, b, cl):
+    """The cluster pivot kernel's fused schedule (one barrier per round; each
+    rotation chosen once per cluster by the thread that rotates the quad
+    holding its pivot entry) and its split schedule (JACOBI_PIVOT_SCHEDULE=
+    split) run the same operations on the same values: the steps, and a
+    full solve with several inner sweeps, agree bit for bit."""
+    import torch
+    monkeypatch.setenv("JACOBI_PIVOT_CLUSTER", cl)
+    A0 = gen.sym_gaussian(np_, 5500 + np_)
+    out = {}
+    for sched in ("split", "fused"):
+        monkeypatch.setenv("JACOBI_PIVOT_SCHEDULE", sched)
+        Ad, Qd = _dev(A0), _dev(np.eye(np_))
+        for s in (0, 1):
+            assert jg.jacobi_syev_step(Ad, Qd, s, jg.params(b=b, inner_max_sweeps=3)) == 0
+        w, Q, D, st = jg.syev(A0, b=b, inner_max_sweeps=2)
+        assert st.status == 0
+        out[sched] = (_np(Ad), _np(Qd), _np(w), _np(Q), st.rotations, st.inner_sweeps)
+    a, f = out["split"], out["fused"]
+    for x, y in zip(a, f):
+        assert np.array_equal(x, y)
