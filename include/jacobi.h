@@ -97,7 +97,10 @@ typedef struct {
                              (zero padding, exact: a zero row and column is
                              never rotated)                                    */
     int ordering;         /* JACOBI_ORDER_*                                     */
-    int max_sweeps;       /* outer sweep cap (default 30)                       */
+    int max_sweeps;       /* outer sweep cap (default 60: graded spectra with
+                             closely spaced eigenvalues converge linearly for
+                             many sweeps, e.g. 30 at n = 4096, b = 64 with
+                             lambda_i = +-10^(-12 i/(n-1)))                     */
     int inner_max_sweeps; /* cap on the sweeps of one pivot solve; a small cap
                              gives the approximate solve the paper allows
                              (Sec. 3, after Algorithm 3).  0 (default) =

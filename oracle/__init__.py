@@ -232,7 +232,7 @@ def syev_step(A: np.ndarray, Q: np.ndarray | None, b: int, pairs, tol_rel=4 * U6
 
 
 def syev(A: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float = 1e-14,
-         ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 1,
+         ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 60, inner_max_sweeps: int = 1,
          conv: int = CONV_OFF_ABS, inner_tol: float = 4 * U64, want_vectors: bool = True,
          threads: int = 0, pivot_order: int = 1):
     """Blocked (Algorithm 1 in the parallel order of Algorithm 2) or scalar
@@ -283,7 +283,7 @@ def gesvd_step(G: np.ndarray, V: np.ndarray | None, b: int, pairs, tol_rel: floa
 
 
 def gesvd(G: np.ndarray, b: int = 16, *, scalar: bool = False, tol: float | None = None,
-          ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 30, inner_max_sweeps: int = 30,
+          ordering: int = ORDER_ROUND_ROBIN, max_sweeps: int = 60, inner_max_sweeps: int = 30,
           want_vectors: bool = True, threads: int = 0, pivot_order: int = 1):
     """Blocked one-sided Jacobi SVD (Algorithm 6 in the parallel order) or the
     scalar Hestenes form.  Returns (U, sigma descending, V or None, Stats, status)."""

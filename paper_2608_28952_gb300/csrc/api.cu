@@ -26,7 +26,7 @@ extern "C" int jacobi_params_default(jacobi_params* p)
     memset(p, 0, sizeof(*p));
     p->b = 32;
     p->ordering = JACOBI_ORDER_ROUND_ROBIN;
-    p->max_sweeps = 30;
+    p->max_sweeps = 60;
     p->inner_max_sweeps = 0;
     p->tol = 1e-14;
     p->inner_tol = 4.0 * U64;
@@ -100,7 +100,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     ua.rot = E.rot;
     ua.cnt = E.cnt;
     if (E.T64) {
-        EmuUpdArgs ea{ua, E.T64, E.err, E.balance};
+        EmuUpdArgs ea{ua, E.T64, E.err, E.balance, E.vimg, E.vexp};
         return launch_emu_update(ea, cs);
     }
     return launch_update_evd(ua, cs);
@@ -207,6 +207,8 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         if (p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
+            E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
+            E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
         }
         E.balance = p.conv == JACOBI_CONV_REL;
         if (ws.failed) return JACOBI_ERR_ALLOC;
@@ -723,6 +725,8 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         if (p.precision == JACOBI_PREC_FP64_EMU || (p.precision == JACOBI_PREC_FP64 && p.fp64_products == 1)) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
+            E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
+            E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
         } else if (p.precision != JACOBI_PREC_FP64) {
             return JACOBI_ERR_UNSUPPORTED;
         }

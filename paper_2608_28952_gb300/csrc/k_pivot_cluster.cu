@@ -27,7 +27,7 @@
 //     cluster barrier every CTA chooses all rotations of round g + 1 from its
 //     own diagonal replica while the other threads rotate V by round g; a
 //     split cluster barrier separates that choice from the next zeroing;
-//   * fused (kFused = true, the default): one phase and one cluster barrier
+//   * fused (kFused = true; the default for k > 128): one phase and one cluster barrier
 //     per round.  Round g + 1 pairs every index with one of round g's other
 //     pairs, so each of its pivot entries a_p'q' is one entry of one quad of
 //     round g.  Those few quads ("leading quads") are rotated first, by the
@@ -142,7 +142,16 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     __shared__ double s_part[PC_MAXC8];
     __shared__ int s_dest[256];
     __shared__ int s_pos[256];
-    for (int u = 0; u < C; ++u) ap.ptr[u] = cluster.map_shared_rank(my_chunk, u);
+    // entry (i, j) of the distributed pivot: a row table (owner rank, offset of
+    // the row in the owner's chunk) and mapa addressing of the owner's window
+    __shared__ int s_rinfo[256];
+    for (int i = tid; i < k; i += nt) {
+        int ow = 0;
+        for (int u = 1; u < C; ++u)
+            if (i >= ap.sp.row0[u]) ow = u;
+        s_rinfo[i] = (ow << 20) | (tri(i) - ap.sp.base[ow]);
+    }
+    const DistRows<double> dr{(uint32_t)__cvta_generic_to_shared(my_chunk), s_rinfo};
 
     // ---- load: the entries this CTA owns, V rows = identity rows
     const int my_lo = ap.sp.row0[r], my_hi = ap.sp.row0[r + 1];
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     }
     cluster.sync();
     for (int x = tid; x < k; x += nt) {
-        dhi[x] = *ap.at(x, x);
+        dhi[x] = dsm_ld(dr.addr(x, x), 0.0);
         dlo[x] = 0.0;
     }
 
@@ -223,7 +232,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
             const int ia = pa == 0 ? 0 : 1 + (pa - 1 + rd) % (k - 1);
             const int ib = 1 + (pb - 1 + rd) % (k - 1);
             const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
-            const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
+            const double app = dhi[p], aqq = dhi[q], apq = dsm_ld(dr.addr(q, p), 0.0);
             const bool on = rotation_wanted(app, aqq, apq, tol);
             const int o = slot * half + ee;
             rp[o] = p;
@@ -259,11 +268,11 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                     const int on1 = ron[so + e1], on2 = ron[so + e2];
                     if (!(on1 | on2)) continue;
                     const int p1 = rp[so + e1], q1 = rq[so + e1], p2 = rp[so + e2], q2 = rq[so + e2];
-                    double* a00 = ap.at(p1, p2);
-                    double* a01 = ap.at(p1, q2);
-                    double* a10 = ap.at(q1, p2);
-                    double* a11 = ap.at(q1, q2);
-                    double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                    const uint32_t a00 = dr.addr(p1, p2);
+                    const uint32_t a01 = dr.addr(p1, q2);
+                    const uint32_t a10 = dr.addr(q1, p2);
+                    const uint32_t a11 = dr.addr(q1, q2);
+                    double x00 = dsm_ld(a00, 0.0), x01 = dsm_ld(a01, 0.0), x10 = dsm_ld(a10, 0.0), x11 = dsm_ld(a11, 0.0);
                     if (on1) {
                         const double sv = rs[so + e1], tauv = rtau[so + e1];
                         rot2(sv, tauv, x00, x10);
@@ -274,10 +283,10 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                         rot2(sv, tauv, x00, x01);
                         rot2(sv, tauv, x10, x11);
                     }
-                    *a00 = x00;
-                    *a01 = x01;
-                    *a10 = x10;
-                    *a11 = x11;
+                    dsm_st(a00, x00);
+                    dsm_st(a01, x01);
+                    dsm_st(a10, x10);
+                    dsm_st(a11, x11);
                 }
                 // diagonal replica (every CTA): the exact 2x2 diagonal form
                 for (int ee = tid; ee < half; ee += nt) {
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                 asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
                 if (r == 0)
                     for (int ee = tid; ee < half; ee += nt)
-                        if (ron[so + ee]) *ap.at(rq[so + ee], rp[so + ee]) = 0.0;
+                        if (ron[so + ee]) dsm_st(dr.addr(rq[so + ee], rp[so + ee]), 0.0);
                 cluster.sync();
                 // phase B
                 if (tid < half) {
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                 const int pa = ee, pb = k - 1 - ee;
                 const int ia = rr_index_at(pa, 0, nr), ib = rr_index_at(pb, 0, nr);
                 const int p = ia < ib ? ia : ib, q = ia < ib ? ib : ia;
-                const double app = dhi[p], aqq = dhi[q], apq = *ap.at(q, p);
+                const double app = dhi[p], aqq = dhi[q], apq = dsm_ld(dr.addr(q, p), 0.0);
                 const bool on = rotation_wanted(app, aqq, apq, tol);
                 rp[ee] = p;
                 rq[ee] = q;
@@ -426,11 +435,22 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                             const int ep2 = h2 ? rr_pair_of(q1, rdn, k) : half;
                             if ((ep1 < ep2 ? ep1 : ep2) == ep) {   // this unit leads quad (e1, e2)
                                 const int on1 = ron[so + e1], on2 = ron[so + e2];
-                                double* a00 = ap.at(p1, p2);
-                                double* a01 = ap.at(p1, q2);
-                                double* a10 = ap.at(q1, p2);
-                                double* a11 = ap.at(q1, q2);
-                                double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                                const uint32_t a00 = dr.addr(p1, p2);
+                                const uint32_t a01 = dr.addr(p1, q2);
+                                const uint32_t a10 = dr.addr(q1, p2);
+                                const uint32_t a11 = dr.addr(q1, q2);
+                                double x00 = dsm_ld(a00, 0.0), x01 = dsm_ld(a01, 0.0), x10 = dsm_ld(a10, 0.0), x11 = dsm_ld(a11, 0.0);
+                                // the diagonal through round g needs only round g's parameters:
+                                // formed while the quad's entries are in flight
+                                double hp1 = 0.0, lp1 = 0.0, hpp = 0.0, lpp = 0.0, hq1 = 0.0, lq1 = 0.0, hpq = 0.0, lpq = 0.0;
+                                if (h1) {
+                                    diag_after(p1, hp1, lp1);
+                                    diag_after(pp1, hpp, lpp);
+                                }
+                                if (h2) {
+                                    diag_after(q1, hq1, lq1);
+                                    diag_after(pq1, hpq, lpq);
+                                }
                                 if (on1) {
                                     const double sv = rs[so + e1], tauv = rtau[so + e1];
                                     rot2(sv, tauv, x00, x10);
@@ -442,29 +462,19 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                                     rot2(sv, tauv, x10, x11);
                                 }
                                 if (on1 | on2) {
-                                    *a00 = x00;
-                                    *a01 = x01;
-                                    *a10 = x10;
-                                    *a11 = x11;
+                                    dsm_st(a00, x00);
+                                    dsm_st(a01, x01);
+                                    dsm_st(a10, x10);
+                                    dsm_st(a11, x11);
                                 }
-                                if (h1) {
-                                    double hx, lx, hy, ly;
-                                    diag_after(p1, hx, lx);
-                                    diag_after(pp1, hy, ly);
-                                    publish(sn, nb, ep1, p1, pp1, pp1 == p2 ? x00 : x01, hx, lx, hy, ly, true, cslot);
-                                }
-                                if (h2) {
-                                    double hx, lx, hy, ly;
-                                    diag_after(q1, hx, lx);
-                                    diag_after(pq1, hy, ly);
-                                    publish(sn, nb, ep2, q1, pq1, pq1 == p2 ? x10 : x11, hx, lx, hy, ly, true, cslot);
-                                }
+                                if (h1) publish(sn, nb, ep1, p1, pp1, pp1 == p2 ? x00 : x01, hp1, lp1, hpp, lpp, true, cslot);
+                                if (h2) publish(sn, nb, ep2, q1, pq1, pq1 == p2 ? x10 : x11, hq1, lq1, hpq, lpq, true, cslot);
                             }
                         }
                     }
                     // round g's pivot entries (read when round g was chosen, before
                     // the last barrier; no quad of round g holds them)
-                    if (ep < half && ron[so + ep]) *ap.at(rq[so + ep], rp[so + ep]) = 0.0;
+                    if (ep < half && ron[so + ep]) dsm_st(dr.addr(rq[so + ep], rp[so + ep]), 0.0);
                 } else {
                     // the other quads of round g over the cluster's bulk threads
                     for (int qi = r * bt + btid; qi < nq; qi += C * bt) {
@@ -477,11 +487,11 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                             const int pp1 = rr_partner_of(p1, rdn, k), pq1 = rr_partner_of(q1, rdn, k);
                             if (pp1 == p2 || pp1 == q2 || pq1 == p2 || pq1 == q2) continue;
                         }
-                        double* a00 = ap.at(p1, p2);
-                        double* a01 = ap.at(p1, q2);
-                        double* a10 = ap.at(q1, p2);
-                        double* a11 = ap.at(q1, q2);
-                        double x00 = *a00, x01 = *a01, x10 = *a10, x11 = *a11;
+                        const uint32_t a00 = dr.addr(p1, p2);
+                        const uint32_t a01 = dr.addr(p1, q2);
+                        const uint32_t a10 = dr.addr(q1, p2);
+                        const uint32_t a11 = dr.addr(q1, q2);
+                        double x00 = dsm_ld(a00, 0.0), x01 = dsm_ld(a01, 0.0), x10 = dsm_ld(a10, 0.0), x11 = dsm_ld(a11, 0.0);
                         if (on1) {
                             const double sv = rs[so + e1], tauv = rtau[so + e1];
                             rot2(sv, tauv, x00, x10);
@@ -492,10 +502,10 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                             rot2(sv, tauv, x00, x01);
                             rot2(sv, tauv, x10, x11);
                         }
-                        *a00 = x00;
-                        *a01 = x01;
-                        *a10 = x10;
-                        *a11 = x11;
+                        dsm_st(a00, x00);
+                        dsm_st(a01, x01);
+                        dsm_st(a10, x10);
+                        dsm_st(a11, x11);
                     }
                     // this CTA's rows of V by round g
                     for (int it = btid; it < half * rows; it += bt) {
@@ -628,13 +638,16 @@ int pivot_cluster_size(int k, int npairs, int sms, size_t smem_cap)
     return best;
 }
 
-// JACOBI_PIVOT_SCHEDULE=split selects the two-phase schedule (the same
-// results bit for bit); the fused schedule is the default.
+// The fused schedule for pivots of order k > 128, the split one below (the
+// same results bit for bit); JACOBI_PIVOT_SCHEDULE=split or =fused forces
+// one.
 cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab, cudaStream_t s)
 {
     if (a.npairs <= 0) return cudaSuccess;
     const char* env = getenv("JACOBI_PIVOT_SCHEDULE");
-    const bool fused = !(env && strcmp(env, "split") == 0);
+    bool fused = a.k > 128;   // measured on GB300: fused 7 % faster at k = 256, 26 % slower at k = 128
+    if (env && strcmp(env, "split") == 0) fused = false;
+    if (env && strcmp(env, "fused") == 0) fused = true;
     auto kern = fused ? k_pivot_cluster<true> : k_pivot_cluster<false>;
     const size_t smem = pivot_cluster_smem(a.k, C);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported(jg):
 
 def test_params_default_matches_header(jg):
     p = jg.params()
-    assert p.b == 32 and p.max_sweeps == 30 and p.inner_max_sweeps == 0  # 0 = automatic
+    assert p.b == 32 and p.max_sweeps == 60 and p.inner_max_sweeps == 0  # 0 = automatic
     assert p.tol == 1e-14 and p.inner_tol == 4 * 2.0 ** -53
     assert p.precision == jg.PREC_FP64 and p.conv == jg.CONV_OFF_ABS
     assert p.want_vectors == 1 and p.warm_start == 0 and p.pivot_order == 1
