@@ -209,6 +209,9 @@ struct EvdState {
     // products and the timeout word
     double* T64 = nullptr;
     int* err = nullptr;
+    // the step's V sliced once (bf16 digit images) and its column scales
+    unsigned char* vimg = nullptr;
+    int* vexp = nullptr;
     // pivot_order == 2: the per-pair QRCP scratch of the pivoting step
     double* qrws = nullptr;
     // emulated products: balance by the diagonal (relative stop criterion)

@@ -213,8 +213,16 @@ struct EmuUpdArgs {
     // 1: balance the pair-blocks' columns by powers of two from the diagonal
     // (graded positive definite inputs under the relative stop criterion)
     int balance = 0;
+    // optional: the step's V sliced once into eight bf16 digit images
+    // (emu_update_vimg_bytes) and its column scales (emu_update_vexp_ints);
+    // the update tiles then stage V's slices by bulk copies instead of
+    // slicing V themselves
+    unsigned char* vimg = nullptr;
+    int* vexp = nullptr;
 };
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s);
+size_t emu_update_vimg_bytes(int npairs, int k);
+size_t emu_update_vexp_ints(int npairs, int k);
 // The one-sided step's products FP64-accurate on the tensor cores: Gram
 // partials per pair and row panel (the layout the pivot kernel reads), and
 // the column update of G and V.

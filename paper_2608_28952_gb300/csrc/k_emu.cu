@@ -153,19 +153,33 @@ __device__ __forceinline__ double i64_scaled(long long sv, int e)
 // exact in FP32) into 64-bit integer running sums held in registers, in
 // units of 2^{sh - 35} with sh = the shift that keeps |sum| below 2^63
 // (sh = 0 up to K = 8192).
-template <bool BIG, class FA, class FB, class ST>
-__device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST st, int* err)
+//
+// AIMG / BIMG: the operand's slices come pre-made from an image in global
+// memory instead (slice p of chunk c: E_ATILE / E_BTILE bytes in the MMA
+// layout at img + (8 c + p) img_stride, the tile's rows first), staged by
+// bulk copies of the tensor memory accelerator that complete on the stage's
+// "full" mbarrier; fa / fb are not called for that operand.
+template <bool BIG, bool AIMG = false, bool BIMG = false, class FA, class FB, class ST>
+__device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST st, int* err,
+                         const unsigned char* imgA = nullptr, const unsigned char* imgB = nullptr,
+                         size_t img_stride = 0)
 {
+    static_assert(!(BIG && (AIMG || BIMG)), "images serve K <= 256 only");
+    constexpr bool kImg = AIMG || BIMG;
+    constexpr uint32_t kImgBytes = (AIMG ? ENS * E_ATILE : 0) + (BIMG ? ENS * E_BTILE : 0);
     extern __shared__ __align__(1024) unsigned char esm[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_full[2];
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)esm + 1023) & ~(uintptr_t)1023);
     if (tid == 0) {
         s_fail = 0;
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < 2; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[s])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -236,28 +250,58 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
     // chunk's loads are issued before the current chunk's MMAs
     double xa[2][8], xb[8];
     auto load_chunk = [&](int c) {
+        if constexpr (!AIMG) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int it = tid + E_T * i, r = it & (EM - 1), k0 = c * EK + (it >> 7) * 8;
+            for (int i = 0; i < 2; ++i) {
+                const int it = tid + E_T * i, r = it & (EM - 1), k0 = c * EK + (it >> 7) * 8;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xa[i][u] = k0 + u < K ? fa(r, k0 + u) : 0.0;
+                for (int u = 0; u < 8; ++u) xa[i][u] = k0 + u < K ? fa(r, k0 + u) : 0.0;
+            }
         }
-        const int n = tid & (EN - 1), k0 = c * EK + (tid >> 6) * 8;
+        if constexpr (!BIMG) {
+            const int n = tid & (EN - 1), k0 = c * EK + (tid >> 6) * 8;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) xb[u] = k0 + u < K ? fb(k0 + u, n) : 0.0;
+            for (int u = 0; u < 8; ++u) xb[u] = k0 + u < K ? fb(k0 + u, n) : 0.0;
+        }
     };
+    // thread 0: the image slices of chunk c into stage c & 1 (free: its
+    // previous MMAs complete), completing on s_full
+    int img_issued = 0, img_waited = 0;
+    auto issue_img = [&](int c) {
+        unsigned char* sa = base + (c & 1) * E_STAGE;
+        unsigned char* sb = sa + ENS * E_ATILE;
+        const uint32_t fb_ = smem_u32(&s_full[c & 1]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb_), "r"(kImgBytes) : "memory");
+#pragma unroll
+        for (int p = 0; p < ENS; ++p) {
+            if constexpr (AIMG)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 smem_u32(sa + p * E_ATILE)),
+                             "l"(imgA + ((size_t)c * ENS + p) * img_stride), "r"(E_ATILE), "r"(fb_)
+                             : "memory");
+            if constexpr (BIMG)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 smem_u32(sb + p * E_BTILE)),
+                             "l"(imgB + ((size_t)c * ENS + p) * img_stride), "r"(E_BTILE), "r"(fb_)
+                             : "memory");
+        }
+        ++img_issued;
+    };
+    if (kImg && tid == 0) issue_img(0);
     load_chunk(0);
     for (int c = 0; c < nchk; ++c) {
         const int s = c & 1;
         unsigned char* st_a = base + s * E_STAGE;
         unsigned char* st_b = st_a + ENS * E_ATILE;
         if (c >= 2 && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
+        if constexpr (!AIMG) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int it = tid + E_T * i, r = it & (EM - 1);
-            store_slices(st_a, E_ATILE, r, (it >> 7) * 8, xa[i], eA[r]);
+            for (int i = 0; i < 2; ++i) {
+                const int it = tid + E_T * i, r = it & (EM - 1);
+                store_slices(st_a, E_ATILE, r, (it >> 7) * 8, xa[i], eA[r]);
+            }
         }
-        {
+        if constexpr (!BIMG) {
             const int n = tid & (EN - 1);
             store_slices(st_b, E_BTILE, n, (tid >> 6) * 8, xb, eB[n]);
         }
@@ -266,6 +310,13 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
         __syncthreads();
         if (s_fail) break;
         if (tid == 0) {
+            bool landed = true;
+            if constexpr (kImg) {
+                landed = mbar_wait(smem_u32(&s_full[s]), (uint32_t)(c >> 1) & 1u);
+                ++img_waited;
+                if (!landed) s_fail = 1;   // no MMA on slices that did not land; the commit still arrives
+            }
+            if (landed) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(st_a), b0 = smem_u32(st_b);
             const bool first = (c % CH) == 0;   // the first chunk of an exact accumulation
@@ -287,11 +338,18 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
                     }
                 }
             }
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&s_bar[s]))
                          : "memory");
         }
         uses[s]++;
+        if (kImg && tid == 0 && c + 1 < nchk && !s_fail) {
+            // the next chunk's slices, once the MMAs of chunk c - 1 (its stage) are complete
+            const int s1 = (c + 1) & 1;
+            if (c >= 1 && !mbar_wait(smem_u32(&s_bar[s1]), (uses[s1] - 1) & 1)) s_fail = 1;
+            else issue_img(c + 1);
+        }
         if (BIG && (c + 1) % CH == 0 && c + 1 < nchk) {
             // drain this exact accumulation before the next one overwrites it
             if (!mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
@@ -303,6 +361,9 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
             __syncthreads();
         }
     }
+    // image copies issued but not waited for (a failed tile breaks early)
+    if (kImg && tid == 0)
+        for (int c = img_waited; c < img_issued; ++c) mbar_wait(smem_u32(&s_full[c & 1]), (uint32_t)(c >> 1) & 1u);
     __syncthreads();
     if (!s_fail)
         for (int s = 0; s < 2; ++s)
@@ -547,6 +608,53 @@ __device__ __forceinline__ void edecode_pb(int pb, int& e1, int& e2)
     e1 = pb - t * (t - 1) / 2;
 }
 
+// ---------------------------------------------------------------- V sliced once per step
+// Rows of the image (the index n of V(kk, n)) are padded to a multiple of
+// 128 so that the 128-row tiles of stage 2 and the 64-row tiles of stage 1
+// are whole: per pair, nchk = ceil(k / 32) chunks x 8 slices x kr * 64
+// bytes (kr = k rounded up to 128), slice p of chunk c holding element
+// (n, kk) of V^T at tile_off(n, kk - 32 c).
+__host__ __device__ __forceinline__ int emu_img_rows(int k) { return (k + EM - 1) / EM * EM; }
+__host__ __device__ __forceinline__ size_t emu_img_slice_bytes(int k) { return (size_t)emu_img_rows(k) * EK * 2; }
+
+// Column scales of V per pair: vexp[e][n] = 1 + the largest exponent in
+// column n of V_e (0 for an all-zero or padding column) -- the scale
+// line_exponents takes for the same column.  One warp per column.
+__global__ void k_emu_vexp(const double* __restrict__ V, const int* __restrict__ rot, int k, int* __restrict__ vexp)
+{
+    const int kr = emu_img_rows(k);
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int e = blockIdx.y;
+    if (col >= kr) return;
+    int mx = -1100;
+    if (col < k && rot[e] != 0) {
+        const double* Vt = V + (size_t)e * 2 * k * k + (size_t)k * k;   // V^T(n, kk) at Vt[n + k kk]
+        for (int kk = lane; kk < k; kk += 32) mx = max(mx, exp2_of(Vt[col + (size_t)k * kk]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) vexp[(size_t)e * kr + col] = mx <= -1100 ? 0 : mx + 1;
+}
+
+// The eight slices of V^T per pair and K chunk (pairs without rotation are
+// skipped: their updates copy).  Block (c, e): items (n, g), eight K values
+// kk = 32 c + 8 g .. + 7 of row n.
+__global__ void __launch_bounds__(E_T) k_emu_slice_v(const double* __restrict__ V, const int* __restrict__ rot, int k,
+                                                     const int* __restrict__ vexp, unsigned char* __restrict__ img)
+{
+    const int c = blockIdx.x, e = blockIdx.y, kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+    if (rot[e] == 0) return;
+    const double* Vt = V + (size_t)e * 2 * k * k + (size_t)k * k;
+    const size_t sb = emu_img_slice_bytes(k);
+    unsigned char* dst = img + ((size_t)e * nchk + c) * ENS * sb;
+    for (int it = threadIdx.x; it < kr * 4; it += E_T) {
+        const int n = it % kr, g = it / kr, k0 = c * EK + g * 8;
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = (n < k && k0 + u < k) ? Vt[n + (size_t)k * (k0 + u)] : 0.0;
+        store_slices(dst, (int)sb, n, g * 8, x, vexp[(size_t)e * kr + n]);
+    }
+}
+
 // Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2 (FP64,
 // k x k per pair-block); items beyond: tile (rt, nt) of Q'(:,P) = Q(:,P) V_P.
 // V^T (stored after V by the pivot kernel) gives the coalesced operand loads.
@@ -599,12 +707,19 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
             return x;
         };
         line_exponents(EM, k, fa, s_eA, s_scr);
-        line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-        emu_tile<false>(k, fa, fb, s_eA, s_eB,
-                 [&](int m, int n, double v) {
-                     if (m0 + m < k && n0 + n < k) T[(m0 + m) + (size_t)k * (n0 + n)] = v;
-                 },
-                 a.err);
+        auto stT = [&](int m, int n, double v) {
+            if (m0 + m < k && n0 + n < k) T[(m0 + m) + (size_t)k * (n0 + n)] = v;
+        };
+        if (!BAL && a.vimg) {   // V2's slices from the step's image
+            const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+            for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e2 * kr + n0 + n];
+            __syncthreads();
+            const unsigned char* im = a.vimg + (size_t)e2 * nchk * ENS * emu_img_slice_bytes(k) + (size_t)n0 * EK * 2;
+            emu_tile<false, false, true>(k, fa, fb, s_eA, s_eB, stT, a.err, nullptr, im, emu_img_slice_bytes(k));
+        } else {
+            line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+            emu_tile<false>(k, fa, fb, s_eA, s_eB, stT, a.err);
+        }
         if (threadIdx.x == 0) {
             atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
             atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
@@ -633,12 +748,19 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
     };
     auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? Vt[(n0 + n) + (size_t)k * kk] : 0.0; };
     line_exponents(EM, k, fa, s_eA, s_scr);
-    line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-    emu_tile<false>(k, fa, fb, s_eA, s_eB,
-             [&](int m, int n, double v) {
-                 if (r0 + m < u.qrows && n0 + n < k) u.Qout[(r0 + m) + (size_t)u.ldq * emap(I, J, b, n0 + n)] = v;
-             },
-             a.err);
+    auto stQ = [&](int m, int n, double v) {
+        if (r0 + m < u.qrows && n0 + n < k) u.Qout[(r0 + m) + (size_t)u.ldq * emap(I, J, b, n0 + n)] = v;
+    };
+    if (a.vimg) {   // V_P's slices from the step's image (the Q items never balance)
+        const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+        for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e * kr + n0 + n];
+        __syncthreads();
+        const unsigned char* im = a.vimg + (size_t)e * nchk * ENS * emu_img_slice_bytes(k) + (size_t)n0 * EK * 2;
+        emu_tile<false, false, true>(k, fa, fb, s_eA, s_eB, stQ, a.err, nullptr, im, emu_img_slice_bytes(k));
+    } else {
+        line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+        emu_tile<false>(k, fa, fb, s_eA, s_eB, stQ, a.err);
+    }
     if (threadIdx.x == 0) {
         atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
         atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
@@ -699,13 +821,21 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd2(EmuUpdArgs a)
         if constexpr (BAL) return pow2_shift(x, s_cs[kk]);
         return x;
     };
-    line_exponents(EM, k, fa, s_eA, s_scr);
-    line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
-    emu_tile<false>(k, fa, fb, s_eA, s_eB,
-             [&](int m, int n, double v) {
-                 if (m0 + m < k && n0 + n < k) put(m0 + m, n0 + n, v);
-             },
-             a.err);
+    auto stO = [&](int m, int n, double v) {
+        if (m0 + m < k && n0 + n < k) put(m0 + m, n0 + n, v);
+    };
+    if (!BAL && a.vimg) {   // V1^T's slices from the step's image (rows of V1^T = columns of V1)
+        const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+        for (int m = threadIdx.x; m < EM; m += E_T) s_eA[m] = a.vexp[(size_t)e1 * kr + m0 + m];
+        __syncthreads();
+        line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+        const unsigned char* im = a.vimg + (size_t)e1 * nchk * ENS * emu_img_slice_bytes(k) + (size_t)m0 * EK * 2;
+        emu_tile<false, true, false>(k, fa, fb, s_eA, s_eB, stO, a.err, im, nullptr, emu_img_slice_bytes(k));
+    } else {
+        line_exponents(EM, k, fa, s_eA, s_scr);
+        line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
+        emu_tile<false>(k, fa, fb, s_eA, s_eB, stO, a.err);
+    }
     if (threadIdx.x == 0) {
         atomicAdd(&u.cnt->flops_update, 2ull * EM * EN * k);
         atomicAdd(&u.cnt->flops_lowp, 72ull * EM * EN * k);
@@ -830,11 +960,23 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_cols(EmuSvdArgs a, int n_g)
 }  // namespace
 
 size_t emu_update_tbuf_doubles(int npairs, int k) { return (size_t)(npairs * (npairs - 1) / 2) * k * k; }
+size_t emu_update_vimg_bytes(int npairs, int k)
+{
+    return (size_t)npairs * ((k + EK - 1) / EK) * ENS * emu_img_slice_bytes(k);
+}
+size_t emu_update_vexp_ints(int npairs, int k) { return (size_t)npairs * emu_img_rows(k); }
 
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
 {
     const UpdateArgs& u = a.u;
     const int nmt = (u.k + EM - 1) / EM, nnt = (u.k + EN - 1) / EN;
+    if (a.vimg && u.npairs > 0) {   // V sliced once for the whole step
+        const int kr = emu_img_rows(u.k);
+        k_emu_vexp<<<dim3((kr + 7) / 8, u.npairs), 256, 0, s>>>(u.V, u.rot, u.k, a.vexp);
+        k_emu_slice_v<<<dim3((u.k + EK - 1) / EK, u.npairs), E_T, 0, s>>>(u.V, u.rot, u.k, a.vexp, a.vimg);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     const int npb = u.npairs * (u.npairs - 1) / 2;
     const int n_sand = npb * nmt * nnt;
     const int n_q = u.Qin ? u.npairs * ((u.qrows + EM - 1) / EM) * nnt : 0;

@@ -232,26 +232,41 @@ struct KMajorF32 {
     }
 };
 
-// Pre-split image tile (hi and lo parts, 16 or 32 KB) copied 16 bytes at a time.
+// Pre-split image tile (hi and lo parts, 16 or 32 KB, contiguous in global
+// memory in the MMA operand layout): staged by the tensor memory accelerator
+// (one cp.async.bulk per chunk, completing on the stage's "full" mbarrier),
+// not through registers.
 template <int KIND>
 struct ImageTile {
-    static constexpr int NV = KT<KIND>::IMG / 16 / U_T;
+    static constexpr bool kBulk = true;
     const unsigned char* img;   // tile (tile index t, chunk c) at img + (t * nchk + c) * IMG
     int nchk;
     int t;
-    uint4 v[NV];
-    __device__ __forceinline__ void load(int c)
+    __device__ __forceinline__ const unsigned char* src(int c) const
     {
-        const uint4* src = reinterpret_cast<const uint4*>(img + ((size_t)t * nchk + c) * KT<KIND>::IMG);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = __ldg(src + threadIdx.x + U_T * i);
+        return img + ((size_t)t * nchk + c) * KT<KIND>::IMG;
     }
-    __device__ __forceinline__ void store(unsigned char* dst) const
-    {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) reinterpret_cast<uint4*>(dst)[threadIdx.x + U_T * i] = v[i];
-    }
+    __device__ __forceinline__ void load(int) {}
+    __device__ __forceinline__ void store(unsigned char*) const {}
 };
+
+template <class L, class = void>
+struct IsBulk {
+    static constexpr bool value = false;
+};
+template <class L>
+struct IsBulk<L, decltype((void)L::kBulk)> {
+    static constexpr bool value = L::kBulk;
+};
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 
 // ---------------------------------------------------------------- the tile
 // acc(128 x 128) = Aop * Bop over nchk chunks of 32.  LA / LB: loaders with
@@ -263,14 +278,19 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
     extern __shared__ __align__(1024) unsigned char usm[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_bar[U_NS];
+    __shared__ __align__(8) uint64_t s_full[U_NS];   // bulk (TMA) operand copies of a stage landed
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
+    constexpr bool kBA = IsBulk<LA>::value, kBB = IsBulk<LB>::value, kAnyBulk = kBA || kBB;
+    constexpr uint32_t kBulkBytes = (kBA ? KT<KIND>::IMG : 0) + (kBB ? KT<KIND>::IMG : 0);
 
     if (tid == 0) {
         s_fail = 0;
-        for (int s = 0; s < U_NS; ++s)
+        for (int s = 0; s < U_NS; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[s])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -290,6 +310,19 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
 #pragma unroll
     for (int s = 0; s < U_NS; ++s) uses[s] = 0;
 
+    // thread 0: the bulk operand copies of chunk c into stage c % U_NS (the
+    // stage must be free: its previous MMAs complete)
+    int bulk_issued = 0, bulk_waited = 0;
+    auto issue_bulk = [&](int c) {
+        const int s = c % U_NS;
+        unsigned char* st = base + s * KT<KIND>::STAGE;
+        const uint32_t fb = smem_u32(&s_full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kBulkBytes) : "memory");
+        if constexpr (kBA) bulk_g2s(smem_u32(st), la.src(c), KT<KIND>::IMG, fb);
+        if constexpr (kBB) bulk_g2s(smem_u32(st + 2 * TB), lb.src(c), KT<KIND>::IMG, fb);
+        ++bulk_issued;
+    };
+    if (kAnyBulk && tid == 0) issue_bulk(0);
     la.load(0);
     lb.load(0);
     for (int c = 0; c < nchk; ++c) {
@@ -302,11 +335,23 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
         if (c + 1 < nchk) {  // next chunk's loads in flight during this chunk's MMAs
             la.load(c + 1);
             lb.load(c + 1);
+            if (kAnyBulk && tid == 0 && !s_fail) {
+                const int s1 = (c + 1) % U_NS;
+                if (c + 1 >= U_NS && !mbar_wait(smem_u32(&s_bar[s1]), (uses[s1] - 1) & 1)) s_fail = 1;
+                else issue_bulk(c + 1);
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (s_fail) break;
         if (tid == 0) {
+            bool landed = true;
+            if (kAnyBulk) {
+                landed = mbar_wait(smem_u32(&s_full[s]), (uint32_t)(c / U_NS) & 1u);
+                ++bulk_waited;
+                if (!landed) s_fail = 1;   // no MMA on a stage whose copy did not land; the commit below still arrives
+            }
+            if (landed) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TB;
             const uint32_t b_hi = a_hi + 2 * TB, b_lo = a_hi + 3 * TB;
@@ -344,12 +389,17 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
                         "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
                 }
             }
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&s_bar[s]))
                          : "memory");
         }
         uses[s]++;
     }
+    // bulk copies issued but not waited for (a failed tile breaks early):
+    // wait for them (bounded) before the shared memory is given up
+    if (kAnyBulk && tid == 0)
+        for (int c = bulk_waited; c < bulk_issued; ++c) mbar_wait(smem_u32(&s_full[c % U_NS]), (uint32_t)(c / U_NS) & 1u);
     // every MMA complete: wait for the last commit of each used stage
     __syncthreads();
     if (!s_fail) {
