@@ -35,6 +35,13 @@
  *   JACOBI_BATCHED_SVD=rowwise     the batched one-sided SVD with one Gram
  *                                  entry per thread instead of staged row
  *                                  tiles (same results bit for bit);
+ *   JACOBI_PIVOT_SCHEDULE=split|fused  round schedule of the cluster pivot
+ *                                  solves (default: fused for 2b > 128,
+ *                                  split below; the same results bit for
+ *                                  bit);
+ *   JACOBI_EMU_IMAGE=0             the emulated FP64 update slices V in
+ *                                  every tile instead of once per step
+ *                                  (the same results bit for bit);
  *   JACOBI_TUNE_CACHE=<path>       file of the batched autotuner's cache;
  *   JACOBI_WORKSPACE_LIMIT=<bytes> cap on one call's workspace (fault
  *                                  injection: JACOBI_ERR_ALLOC before any

@@ -207,8 +207,10 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
         if (p.precision == JACOBI_PREC_FP64_EMU || p.fp64_products == 1) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
-            E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
-            E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+            if (emu_image_wanted()) {
+                E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
+                E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+            }
         }
         E.balance = p.conv == JACOBI_CONV_REL;
         if (ws.failed) return JACOBI_ERR_ALLOC;
@@ -725,8 +727,10 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
         if (p.precision == JACOBI_PREC_FP64_EMU || (p.precision == JACOBI_PREC_FP64 && p.fp64_products == 1)) {
             E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, E.k));
             E.err = ws.get<int>(1);
-            E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
-            E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+            if (emu_image_wanted()) {
+                E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
+                E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+            }
         } else if (p.precision != JACOBI_PREC_FP64) {
             return JACOBI_ERR_UNSUPPORTED;
         }

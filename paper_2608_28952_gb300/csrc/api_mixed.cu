@@ -236,8 +236,10 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     if (p.fp64_products == 1) {   // refinement and closing sweeps with FP64-accurate tensor-core products
         E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, k));
         E.err = L.err;
-        E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, k));
-        E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, k));
+        if (emu_image_wanted()) {
+            E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, k));
+            E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, k));
+        }
         E.balance = p.conv == JACOBI_CONV_REL;
         xexp = ws.get<int>(2 * (size_t)np);
     }

@@ -138,6 +138,15 @@ inline bool capture(SweepGraph& g, F body)
     return ok;
 }
 
+// The emulated FP64 update slices V once per step into images (default);
+// JACOBI_EMU_IMAGE=0 makes every tile slice its V operand itself (the same
+// slices, so the same results bit for bit).
+inline bool emu_image_wanted()
+{
+    const char* e = getenv("JACOBI_EMU_IMAGE");
+    return !(e && e[0] == '0');
+}
+
 // Cluster size for the pivot solves of a step with npairs pairs of order k:
 // automatic unless JACOBI_PIVOT_CLUSTER is set ("1" = one CTA per pair, a
 // power of two <= 8 = that size when it fits).

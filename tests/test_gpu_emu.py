@@ -234,3 +234,33 @@ def test_emu_graded_spectrum_relative_gate(jg):
     assert np.abs(w - w_or).max() <= 1e-13 * np.abs(w_or).max()
     big = np.abs(w_or) >= 1e-3 * np.abs(w_or).max()
     assert (np.abs(w - w_or)[big] / np.abs(w_or[big])).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n,b", [(512, 64), (1024, 128), (300, 50)])
+def test_step_image_of_v_is_bitwise_the_per_tile_slicing(jg, monkeypatch, n, b):
+    """The emulated update slices V once per step into digit images that its
+    tiles stage by bulk copies (default), or slices V inside every tile
+    (JACOBI_EMU_IMAGE=0): the same slices and scales, so the step and the
+    full solve agree bit for bit."""
+    import torch
+
+    import jacobi_inputs as gen
+
+    def _dev(x):
+        return jg.colmajor(x, device="cuda", dtype=torch.float64)
+
+    def _np(t):
+        return t.detach().cpu().numpy()
+
+    A0 = gen.sym_gaussian(n, 6100 + n)
+    out = {}
+    for img in ("1", "0"):
+        monkeypatch.setenv("JACOBI_EMU_IMAGE", img)
+        Ad, Qd = _dev(A0), _dev(np.eye(n))
+        for s in (0, 1):
+            assert jg.jacobi_syev_step(Ad, Qd, s, jg.params(b=b, precision=jg.PREC_FP64_EMU)) == 0
+        w, Q, _, st = jg.syev(A0, b=b, precision=jg.PREC_FP64_EMU)
+        assert st.status == 0
+        out[img] = (_np(Ad), _np(Qd), _np(w), _np(Q))
+    for x, y in zip(out["1"], out["0"]):
+        assert np.array_equal(x, y)
