@@ -39,9 +39,11 @@
  *                                  solves (default: fused for 2b > 128,
  *                                  split below; the same results bit for
  *                                  bit);
- *   JACOBI_EMU_IMAGE=0             the emulated FP64 update slices V in
- *                                  every tile instead of once per step
- *                                  (the same results bit for bit);
+ *   JACOBI_EMU_IMAGE=0             the emulated FP64 products slice their
+ *                                  operands in every tile instead of once
+ *                                  into an image (V per step in the update,
+ *                                  both operands of a refinement product;
+ *                                  the same results bit for bit);
  *   JACOBI_TUNE_CACHE=<path>       file of the batched autotuner's cache;
  *   JACOBI_WORKSPACE_LIMIT=<bytes> cap on one call's workspace (fault
  *                                  injection: JACOBI_ERR_ALLOC before any

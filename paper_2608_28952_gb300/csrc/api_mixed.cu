@@ -233,6 +233,7 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
     L.kind = p.precision == JACOBI_PREC_MIXED_FP16X3 ? 1 : (p.precision == JACOBI_PREC_MIXED_TF32 ? 2 : 0);
     L.err = ws.get<int>(1);
     int* xexp = nullptr;          // line exponents of the emulated refinement products
+    unsigned char* gimg[2] = {nullptr, nullptr};   // their slice images
     if (p.fp64_products == 1) {   // refinement and closing sweeps with FP64-accurate tensor-core products
         E.T64 = ws.get<double>(emu_update_tbuf_doubles(E.ord.dev_per_step, k));
         E.err = L.err;
@@ -242,6 +243,10 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         }
         E.balance = p.conv == JACOBI_CONV_REL;
         xexp = ws.get<int>(2 * (size_t)np);
+        if (emu_image_wanted()) {   // the refinement products' operands sliced once per product
+            gimg[0] = ws.get<unsigned char>(emu_gemm_img_bytes(np, np));
+            gimg[1] = ws.get<unsigned char>(emu_gemm_img_bytes(np, np));
+        }
     }
     if (ws.failed) return JACOBI_ERR_ALLOC;
     L.pcl = E.pcl;
@@ -310,6 +315,9 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         const double nn = (double)np, n3 = nn * nn * nn;
         // C = op(Am) Bm (+ C when acc): FP64 FMA, or FP64-accurate on the tensor cores
         auto g64 = [&](const double* Am, int transA, const double* Bm, int acc, double* Cm, int lower) {
+            if (xexp && gimg[0])
+                return launch_emu_gemm_img(np, np, np, Am, np, transA, Bm, np, acc, Cm, np, lower, xexp, xexp + np,
+                                           gimg[0], gimg[1], L.err, s) == cudaSuccess;
             if (xexp)
                 return launch_emu_gemm_big(np, np, np, Am, np, transA, Bm, np, acc, Cm, np, lower, xexp, xexp + np,
                                            L.err, s) == cudaSuccess;

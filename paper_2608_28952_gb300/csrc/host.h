@@ -138,9 +138,10 @@ inline bool capture(SweepGraph& g, F body)
     return ok;
 }
 
-// The emulated FP64 update slices V once per step into images (default);
-// JACOBI_EMU_IMAGE=0 makes every tile slice its V operand itself (the same
-// slices, so the same results bit for bit).
+// The emulated FP64 products slice an operand once into an image (V once
+// per step in the update; both operands once per refinement product) by
+// default; JACOBI_EMU_IMAGE=0 makes every tile slice its operands itself
+// (the same slices, so the same results bit for bit).
 inline bool emu_image_wanted()
 {
     const char* e = getenv("JACOBI_EMU_IMAGE");

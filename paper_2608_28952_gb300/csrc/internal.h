@@ -199,6 +199,13 @@ cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int t
 cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
                                 int accumulate, double* C, int ldc, int lower, int* xA, int* xB, int* err,
                                 cudaStream_t s);
+// The same product with both operands sliced once into images (imgA:
+// emu_gemm_img_bytes(M, K) bytes, imgB: emu_gemm_img_bytes(N, K)) that the
+// tiles stage by bulk copies, instead of every tile slicing its operands.
+size_t emu_gemm_img_bytes(int lines, int K);
+cudaError_t launch_emu_gemm_img(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                int accumulate, double* C, int ldc, int lower, int* xA, int* xB,
+                                unsigned char* imgA, unsigned char* imgB, int* err, cudaStream_t s);
 // W (N x M, ld ldw) = (op(A) B)^T with K split into chunks of kchunk: the
 // partials (part: ceil(K / kchunk) x M x N doubles) summed in a fixed order.
 cudaError_t launch_emu_gemm_tsplit(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,

@@ -156,15 +156,16 @@ __device__ __forceinline__ double i64_scaled(long long sv, int e)
 //
 // AIMG / BIMG: the operand's slices come pre-made from an image in global
 // memory instead (slice p of chunk c: E_ATILE / E_BTILE bytes in the MMA
-// layout at img + (8 c + p) img_stride, the tile's rows first), staged by
+// layout at img + (8 c + p) stride, the tile's rows first; img_stride for A,
+// img_stride_b for B, which defaults to img_stride), staged by
 // bulk copies of the tensor memory accelerator that complete on the stage's
 // "full" mbarrier; fa / fb are not called for that operand.
 template <bool BIG, bool AIMG = false, bool BIMG = false, class FA, class FB, class ST>
 __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST st, int* err,
                          const unsigned char* imgA = nullptr, const unsigned char* imgB = nullptr,
-                         size_t img_stride = 0)
+                         size_t img_stride = 0, size_t img_stride_b = 0)
 {
-    static_assert(!(BIG && (AIMG || BIMG)), "images serve K <= 256 only");
+    if (img_stride_b == 0) img_stride_b = img_stride;
     constexpr bool kImg = AIMG || BIMG;
     constexpr uint32_t kImgBytes = (AIMG ? ENS * E_ATILE : 0) + (BIMG ? ENS * E_BTILE : 0);
     extern __shared__ __align__(1024) unsigned char esm[];
@@ -282,7 +283,7 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
             if constexpr (BIMG)
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                                  smem_u32(sb + p * E_BTILE)),
-                             "l"(imgB + ((size_t)c * ENS + p) * img_stride), "r"(E_BTILE), "r"(fb_)
+                             "l"(imgB + ((size_t)c * ENS + p) * img_stride_b), "r"(E_BTILE), "r"(fb_)
                              : "memory");
         }
         ++img_issued;
@@ -474,11 +475,13 @@ __global__ void k_emu_line_exps(int lines, int K, const double* __restrict__ X, 
 // above the diagonal are skipped when lower (the caller mirrors).
 // With kchunk > 0 (split K): block z takes K values [z kchunk, (z+1) kchunk)
 // and writes its M x N partial to C + z M N (ld M); the caller sums them.
+template <bool IMG>
 __global__ void __launch_bounds__(E_T, 1) k_emu_gemm_big(int M, int N, int K, const double* __restrict__ A, int lda,
                                                          int transA, const double* __restrict__ B, int ldb,
                                                          int accumulate, double* __restrict__ C, int ldc, int lower,
                                                          const int* __restrict__ xA, const int* __restrict__ xB,
-                                                         int* err, int kchunk)
+                                                         int* err, int kchunk, const unsigned char* imgA,
+                                                         const unsigned char* imgB, size_t strideA, size_t strideB)
 {
     __shared__ int s_eA[EM], s_eB[EN];
     const int m0 = blockIdx.x * EM, n0 = blockIdx.y * EN;
@@ -507,14 +510,41 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_gemm_big(int M, int N, int K, co
         const int nn = n0 + n;
         return (nn < N && k < K) ? B[kb + k + (size_t)ldb * nn] : 0.0;
     };
-    emu_tile<true>(K, fa, fb, s_eA, s_eB,
-                   [&](int m, int n, double v) {
-                       if (m0 + m < M && n0 + n < N) {
-                           double* c = C + (m0 + m) + (size_t)ldc * (n0 + n);
-                           *c = accumulate ? *c + v : v;
-                       }
-                   },
-                   err);
+    auto stc = [&](int m, int n, double v) {
+        if (m0 + m < M && n0 + n < N) {
+            double* c = C + (m0 + m) + (size_t)ldc * (n0 + n);
+            *c = accumulate ? *c + v : v;
+        }
+    };
+    if constexpr (IMG)   // both operands' slices from the images (K chunks from kb, kb a multiple of 32)
+        emu_tile<true, true, true>(K, fa, fb, s_eA, s_eB, stc, err,
+                                   imgA + (size_t)(kb / EK) * ENS * strideA + (size_t)m0 * EK * 2,
+                                   imgB + (size_t)(kb / EK) * ENS * strideB + (size_t)n0 * EK * 2, strideA, strideB);
+    else
+        emu_tile<true>(K, fa, fb, s_eA, s_eB, stc, err);
+}
+
+// The slices of `lines` lines of op(X) over K (line i: X[i + ld k] when
+// trans = 0, X[k + ld i] when trans = 1), with the line scales of
+// k_emu_line_exps (exponent + 2048, 0 for an all-zero line), into an image
+// whose slice blocks hold R rows (R >= lines, a multiple of 64; padding rows
+// zero): slice p of chunk c at img + (8 c + p) R 64 bytes, row r at
+// tile_off(r, k - 32 c).  Block (c, g): rows 64 g .. 64 g + 63.
+__global__ void __launch_bounds__(E_T) k_emu_slice_lines(int lines, int K, const double* __restrict__ X, int ld,
+                                                         int trans, const int* __restrict__ xexp, int R,
+                                                         unsigned char* __restrict__ img)
+{
+    const int c = blockIdx.x, r = blockIdx.y * 64 + (threadIdx.x & 63), g = threadIdx.x >> 6;
+    const size_t sb = (size_t)R * EK * 2;
+    const int k0 = c * EK + g * 8;
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int kk = k0 + u;
+        x[u] = (r < lines && kk < K) ? (trans ? X[kk + (size_t)ld * r] : X[r + (size_t)ld * kk]) : 0.0;
+    }
+    const int v = r < lines ? xexp[r] : 0;
+    store_slices(img + (size_t)c * ENS * sb, (int)sb, r, g * 8, x, v == 0 ? 0 : v - 2048 + 1);
 }
 
 }  // namespace
@@ -529,12 +559,43 @@ cudaError_t launch_emu_gemm(int M, int N, int K, const double* A, int lda, int t
     return cudaGetLastError();
 }
 
+size_t emu_gemm_img_bytes(int lines, int K)
+{
+    const size_t R = ((size_t)lines + EM - 1) / EM * EM;
+    return ((size_t)K + EK - 1) / EK * ENS * R * EK * 2;
+}
+
+cudaError_t launch_emu_gemm_img(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                                int accumulate, double* C, int ldc, int lower, int* xA, int* xB,
+                                unsigned char* imgA, unsigned char* imgB, int* err, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xA, 0, sizeof(int) * M, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(xB, 0, sizeof(int) * N, s)) != cudaSuccess)
+        return e;
+    if (transA)
+        k_emu_line_exps<<<dim3((M + 7) / 8, (K + 255) / 256), 256, 0, s>>>(M, K, A, lda, 0, xA);
+    else
+        k_emu_line_exps<<<dim3((M + 255) / 256, (K + 63) / 64), 256, 0, s>>>(M, K, A, lda, 1, xA);
+    k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
+    const int RA = (M + EM - 1) / EM * EM, RB = (N + EM - 1) / EM * EM, nchk = (K + EK - 1) / EK;
+    k_emu_slice_lines<<<dim3(nchk, RA / 64), E_T, 0, s>>>(M, K, A, lda, transA, xA, RA, imgA);
+    k_emu_slice_lines<<<dim3(nchk, RB / 64), E_T, 0, s>>>(N, K, B, ldb, 1, xB, RB, imgB);
+    dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
+    k_emu_gemm_big<true><<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, accumulate, C, ldc, lower, xA,
+                                                   xB, err, 0, imgA, imgB, (size_t)RA * EK * 2,
+                                                   (size_t)RB * EK * 2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, int transA, const double* B, int ldb,
                                 int accumulate, double* C, int ldc, int lower, int* xA, int* xB, int* err,
                                 cudaStream_t s)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(xA, 0, sizeof(int) * M, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(xB, 0, sizeof(int) * N, s)) != cudaSuccess)
@@ -545,8 +606,8 @@ cudaError_t launch_emu_gemm_big(int M, int N, int K, const double* A, int lda, i
         k_emu_line_exps<<<dim3((M + 255) / 256, (K + 63) / 64), 256, 0, s>>>(M, K, A, lda, 1, xA);
     k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
     dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN);
-    k_emu_gemm_big<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, accumulate, C, ldc, lower, xA, xB,
-                                             err, 0);
+    k_emu_gemm_big<false><<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, accumulate, C, ldc, lower, xA,
+                                                    xB, err, 0, nullptr, nullptr, 0, 0);
     return cudaGetLastError();
 }
 
@@ -569,7 +630,7 @@ cudaError_t launch_emu_gemm_tsplit(int M, int N, int K, const double* A, int lda
                                    cudaStream_t s)
 {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_emu_gemm_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(xA, 0, sizeof(int) * M, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(xB, 0, sizeof(int) * N, s)) != cudaSuccess)
@@ -581,7 +642,8 @@ cudaError_t launch_emu_gemm_tsplit(int M, int N, int K, const double* A, int lda
     k_emu_line_exps<<<dim3((N + 7) / 8, (K + 255) / 256), 256, 0, s>>>(N, K, B, ldb, 0, xB);
     const int nsplit = (K + kchunk - 1) / kchunk;
     dim3 grid((M + EM - 1) / EM, (N + EN - 1) / EN, nsplit);
-    k_emu_gemm_big<<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, 0, part, M, 0, xA, xB, err, kchunk);
+    k_emu_gemm_big<false><<<grid, E_T, E_SMEM, s>>>(M, N, K, A, lda, transA, B, ldb, 0, part, M, 0, xA, xB, err,
+                                                    kchunk, nullptr, nullptr, 0, 0);
     const long long total = (long long)M * N;
     k_emu_sum_t<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, nsplit, part, W, ldw);
     return cudaGetLastError();

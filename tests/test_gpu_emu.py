@@ -264,3 +264,21 @@ def test_step_image_of_v_is_bitwise_the_per_tile_slicing(jg, monkeypatch, n, b):
         out[img] = (_np(Ad), _np(Qd), _np(w), _np(Q))
     for x, y in zip(out["1"], out["0"]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("n,b", [(512, 64), (700, 64)])
+def test_refinement_images_are_bitwise_the_per_tile_slicing(jg, monkeypatch, n, b):
+    """The mixed form with FP64-accurate refinement products: with the
+    products' operands sliced once into images (default) or sliced in every
+    tile (JACOBI_EMU_IMAGE=0), the solve agrees bit for bit (ragged n: the
+    images' padding rows are zero)."""
+    import jacobi_inputs as gen
+    A, lam = gen.sym_known(n, "uniform", seed=6200 + n)
+    out = {}
+    for img in ("1", "0"):
+        monkeypatch.setenv("JACOBI_EMU_IMAGE", img)
+        w, Q, _, st = jg.syev(A, b=b, precision=jg.PREC_MIXED_BF16X3, fp64_products=1)
+        assert st.status == 0 and st.ms_refine > 0
+        out[img] = (w.cpu().numpy(), Q.cpu().numpy())
+    assert np.array_equal(out["1"][0], out["0"][0]) and np.array_equal(out["1"][1], out["0"][1])
+    assert np.abs(out["1"][0] - np.sort(lam)).max() <= 1e-13 * np.abs(lam).max()
