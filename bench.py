@@ -140,7 +140,7 @@ WORKLOADS = {
                               "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
                               "on the bf16 tensor cores), n=4096, b=64, lam ~ U[-1,1], eigenvalues + full Q"),
     "mixed8192emu": dict(kind="evd", n=8192, b=128, spectrum="uniform", seed=6, precision=2, ref_sweeps=14,
-                         refine_steps=1, fp64_products=1, compare_plain=True, compare_batched=True,
+                         refine_steps=2, switch_tol=1e-5, fp64_products=1, compare_plain=True, compare_batched=True,
                          desc="mixed-precision two-sided block Jacobi EVD (bf16 hi/lo x3 tensor-core "
                               "updates, FP64 pivots, refinement and closing-sweep products FP64-accurate "
                               "on the bf16 tensor cores), n=8192, b=128, lam ~ U[-1,1], eigenvalues + full Q"),
@@ -400,6 +400,7 @@ def workload_config(wl, world: int) -> dict:
             **({"precision": {2: "mixed bf16x3", 3: "mixed fp16x3", 4: "mixed tf32x3",
                               5: "fp64 emulated products"}[prec],
                 "refine_steps": wl.get("refine_steps")} if prec else {}),
+            **({"switch_tol": wl["switch_tol"]} if "switch_tol" in wl else {}),
             **({"fp64_products": True} if wl.get("fp64_products") else {}),
             "l2": "inputs larger than L2 (working A, Q double-buffered: 4 x n^2 x 8 B)"}
 
@@ -676,7 +677,7 @@ def run_gpu(args, wl):
     X, ref = make_input(wl)
     b = wl["b"]
     prec = wl.get("precision", 0)
-    extra = {k: wl[k] for k in ("refine_steps", "fp64_products", "svd_qr", "pivot_order") if k in wl}
+    extra = {k: wl[k] for k in ("refine_steps", "switch_tol", "fp64_products", "svd_qr", "pivot_order") if k in wl}
     p = jg.params(b=b, inner_max_sweeps=args.inner_max_sweeps, precision=prec, **extra)
     Xd = jg.colmajor(X, device=dev, dtype=torch.float64)
     Wd = torch.empty_like(Xd.t()).t()  # column-major work copy
@@ -1011,10 +1012,11 @@ def measure_batched(wl, steps, warmup, e2e_steps, want_cpu, world, dev, stream,
     plan = jg.Plan(0 if evd else 1, prec, ncols, m=None if evd else [m for m, _ in shapes],
                    p=jg.params(), stream=stream)
     t0 = time.perf_counter()
-    if wl["f32"] and evd:
+    if evd:
         plan.autotune(X, Y, Z, info, stream)
     tune_s = time.perf_counter() - t0
     shape = plan.shape()
+    blocking = plan.blocking()
 
     def step():
         flat.copy_(flat0)
@@ -1141,6 +1143,7 @@ def measure_batched(wl, steps, warmup, e2e_steps, want_cpu, world, dev, stream,
             "dtype": "f32" if wl["f32"] else "f64", "data": "synthetic (seeded; see config)",
             "config": workload_config(wl, world),
             "plan": {"shape": {"threads": shape[0], "smem_kmax": shape[1], "grid": shape[2]},
+                     "blocking": {"b": blocking[0], "unblocked_up_to_order": blocking[1]},
                      "autotune_s": tune_s,
                      "batch_gb": sum(m * n for m, n in shapes) * (4 if wl["f32"] else 8) / 1e9},
             "eff_tflops_issued": achieved, "accuracy": acc,

@@ -374,8 +374,10 @@ int jacobi_gesvd_batched_f32(int batch, const int* h_m, const int* h_n, float* c
  *   kind: 0 = symmetric EVD, 1 = one-sided SVD;  precision: JACOBI_PREC_FP64
  *   or JACOBI_PREC_FP32 (kind 1: FP32 only).  h_m may be NULL for kind 0.
  * jacobi_plan_autotune times each candidate launch shape (threads per CTA,
- * largest order kept in shared memory) on a sample of the batch, keeps the
- * fastest, and records it in an in-process cache keyed by kind, precision,
+ * largest order kept in shared memory), then each candidate order above
+ * which the blocked method takes over (jacobi_plan_blocking), on a sample of
+ * the batch, keeps the fastest, and records it in an in-process cache keyed
+ * by kind, precision,
  * vectors and the size mix (also written to the file named by the
  * environment variable JACOBI_TUNE_CACHE, if set, and read back by later
  * plans).  Plans are not thread-safe; one plan per stream. */
@@ -388,6 +390,14 @@ int jacobi_plan_autotune(jacobi_plan* plan, void* const* A_or_G, void* const* w_
 int jacobi_plan_execute(jacobi_plan* plan, void* const* A_or_G, void* const* w_or_sigma,
                         void* const* Q_or_V, int* info, jacobi_stats* st, void* stream);
 int jacobi_plan_shape(const jacobi_plan* plan, int* threads, int* smem_kmax, int* grid);
+/* The block size a symmetric-EVD plan uses per size class: orders up to
+ * *min_order are solved unblocked (the whole matrix is one pivot, in shared
+ * memory or spread over a cluster), orders above it by the blocked method of
+ * Algorithm 1 with block size *b (16).  jacobi_plan_autotune chooses
+ * min_order (with the launch shape) by timing candidates on a sample of the
+ * batch; *b = *min_order = 0 for a plan without the blocked route (one-sided
+ * plans, JACOBI_BATCHED_LARGE=l2|cluster).  Returns 0, -1 (plan NULL). */
+int jacobi_plan_blocking(const jacobi_plan* plan, int* b, int* min_order);
 void jacobi_plan_destroy(jacobi_plan* plan);
 
 /*

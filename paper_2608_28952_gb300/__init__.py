@@ -130,6 +130,7 @@ SIGNATURES = {
     "jacobi_plan_autotune": (_I, [_P, _P, _P, _P, _P, _P]),
     "jacobi_plan_execute": (_I, [_P, _P, _P, _P, _P, _SP, _P]),
     "jacobi_plan_shape": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "jacobi_plan_blocking": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "jacobi_plan_destroy": (None, [_P]),
     "jacobi_syev_step_noalloc": (_I, [_I, _P, _I, _P, _I, _PP, _I, _P]),
     "jacobi_lowp_gemm": (_I, [_I, _I, _I, _P, _I, _I, _P, _I, _P, _I, _P]),
@@ -512,6 +513,14 @@ class Plan:
         t, k, g = C.c_int(), C.c_int(), C.c_int()
         lib().jacobi_plan_shape(self._h, C.byref(t), C.byref(k), C.byref(g))
         return t.value, k.value, g.value
+
+    def blocking(self):
+        """(b, min_order): orders above min_order use the blocked method with
+        block size b; at or below it, the unblocked solve (0, 0: no blocked
+        route in this plan)."""
+        b, mo = C.c_int(), C.c_int()
+        lib().jacobi_plan_blocking(self._h, C.byref(b), C.byref(mo))
+        return b.value, mo.value
 
     def close(self):
         if self._h:

@@ -100,7 +100,7 @@ static cudaError_t launch_step(EvdState& E, int s, int cur, cudaStream_t cs, dou
     ua.rot = E.rot;
     ua.cnt = E.cnt;
     if (E.T64) {
-        EmuUpdArgs ea{ua, E.T64, E.err, E.balance, E.vimg, E.vexp};
+        EmuUpdArgs ea{ua, E.T64, E.err, E.balance, E.vimg, E.vexp, E.aimg, E.atab, E.qimg, E.qexp};
         return launch_emu_update(ea, cs);
     }
     return launch_update_evd(ua, cs);
@@ -210,6 +210,14 @@ static int syev_fp64(int n, double* A, int lda, double* w, double* Q, int ldq,
             if (emu_image_wanted()) {
                 E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
                 E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+                if (p.conv != JACOBI_CONV_REL) {   // (balanced products slice per tile)
+                    E.aimg = ws.get<unsigned char>(emu_update_aimg_bytes(E.ord.dev_per_step, E.k));
+                    E.atab = ws.get<int>((size_t)E.ord.dev_per_step * E.np);
+                    if (vec) {
+                        E.qimg = ws.get<unsigned char>(emu_update_qimg_bytes(E.ord.dev_per_step, E.k, E.np));
+                        E.qexp = ws.get<int>((size_t)E.ord.dev_per_step * E.np);
+                    }
+                }
             }
         }
         E.balance = p.conv == JACOBI_CONV_REL;
@@ -730,6 +738,14 @@ extern "C" int jacobi_syev_step(int np, double* A, int lda, double* Q, int ldq,
             if (emu_image_wanted()) {
                 E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, E.k));
                 E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, E.k));
+                if (p.conv != JACOBI_CONV_REL) {   // (balanced products slice per tile)
+                    E.aimg = ws.get<unsigned char>(emu_update_aimg_bytes(E.ord.dev_per_step, E.k));
+                    E.atab = ws.get<int>((size_t)E.ord.dev_per_step * E.np);
+                    if (Q) {
+                        E.qimg = ws.get<unsigned char>(emu_update_qimg_bytes(E.ord.dev_per_step, E.k, E.np));
+                        E.qexp = ws.get<int>((size_t)E.ord.dev_per_step * E.np);
+                    }
+                }
             }
         } else if (p.precision != JACOBI_PREC_FP64) {
             return JACOBI_ERR_UNSUPPORTED;

@@ -29,7 +29,14 @@ constexpr double U32 = 5.9604644775390625e-08;
 struct Shape {
     int threads = 256;
     int smem_kmax = 0;   // EVD: even orders up to this are solved in shared memory
+    int blk_min = -1;    // EVD: orders above this use the blocked method (b = 16), orders
+                         // from smem_kmax up to it the unblocked solve on a cluster
+                         // (-1: the measured default, 320 in FP64, 0 in FP32)
 };
+
+constexpr int kBatchedBlockB = 16;   // the block size of the batched blocked method
+
+int blk_min_of(const Shape& sh, int esize) { return sh.blk_min >= 0 ? sh.blk_min : (esize == 8 ? 320 : 0); }
 
 std::mutex g_tune_mu;
 std::map<std::string, Shape> g_tune;  // key -> tuned shape
@@ -43,9 +50,12 @@ void tune_load_locked()
     if (!path) return;
     FILE* f = fopen(path, "r");
     if (!f) return;
-    char key[256];
-    int th, sk;
-    while (fscanf(f, "%255s %d %d", key, &th, &sk) == 3) g_tune[key] = Shape{th, sk};
+    char line[512], key[256];
+    while (fgets(line, sizeof(line), f)) {
+        int th = 0, sk = 0, bm = -1;
+        const int got = sscanf(line, "%255s %d %d %d", key, &th, &sk, &bm);
+        if (got >= 3) g_tune[key] = Shape{th, sk, got == 4 ? bm : -1};
+    }
     fclose(f);
 }
 
@@ -55,7 +65,8 @@ void tune_store_locked()
     if (!path) return;
     FILE* f = fopen(path, "w");
     if (!f) return;
-    for (auto& kv : g_tune) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.threads, kv.second.smem_kmax);
+    for (auto& kv : g_tune)
+        fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.threads, kv.second.smem_kmax, kv.second.blk_min);
     fclose(f);
 }
 
@@ -191,7 +202,7 @@ cudaError_t plan_launch(jacobi_plan* pl, int* info, cudaStream_t s, const Shape&
             // scalar method issues fewer operations there: measured on GB300,
             // 64 matrices of order 256 in 0.12 s on clusters, 0.20 s blocked;
             // order 384: 0.77 s / 0.69 s)
-            const int blk_min = pl->esize == 8 ? 320 : 0;
+            const int blk_min = blk_min_of(sh, pl->esize);
             int nb = 0;
             while (nb < count) {
                 const int n = pl->h_n[h_list[nb]], k = n + (n & 1);
@@ -465,6 +476,23 @@ extern "C" int jacobi_plan_autotune(jacobi_plan* pl, void* const* A_or_G, void* 
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) { best = ms; bestsh = sh; }
     }
+    // then the block size per size class: the order above which the blocked
+    // method (b = 16) takes over from the unblocked solve on a cluster
+    if (rc == 0 && pl->kind == 0 && pl->large_mode == 2 && pl->d_blk) {
+        for (int bm : {0, 192, 256, 320, 384, 448, 512}) {
+            Shape sh = bestsh;
+            sh.blk_min = bm;
+            const int grid = std::min(grid_for(pl, sh), device_sms() * 4);
+            if (plan_launch_any(pl, info, s, sh, grid, h_sub, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
+            cudaEventRecord(e0, s);
+            if (plan_launch_any(pl, info, s, sh, grid, h_sub, d_sub) != cudaSuccess) { cudaGetLastError(); continue; }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = JACOBI_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bestsh = sh; }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(d_sub);
@@ -572,6 +600,19 @@ extern "C" void jacobi_plan_destroy(jacobi_plan* pl)
     cudaFree(pl->d_blk);
     cudaFree(pl->d_cnt);
     delete pl;
+}
+
+extern "C" int jacobi_plan_blocking(const jacobi_plan* pl, int* b, int* min_order)
+{
+    if (!pl) return -1;
+    if (pl->kind != 0 || pl->large_mode != 2 || !pl->d_blk) {   // no blocked route in this plan
+        if (b) *b = 0;
+        if (min_order) *min_order = 0;
+        return 0;
+    }
+    if (b) *b = kBatchedBlockB;
+    if (min_order) *min_order = std::max(blk_min_of(pl->shape, pl->esize), pl->shape.smem_kmax);
+    return 0;
 }
 
 extern "C" int jacobi_plan_shape(const jacobi_plan* pl, int* threads, int* smem_kmax, int* grid)

@@ -240,6 +240,12 @@ int syev_mixed(int n, double* A, int lda, double* w, double* Q, int ldq, const j
         if (emu_image_wanted()) {
             E.vimg = ws.get<unsigned char>(emu_update_vimg_bytes(E.ord.dev_per_step, k));
             E.vexp = ws.get<int>(emu_update_vexp_ints(E.ord.dev_per_step, k));
+            if (p.conv != JACOBI_CONV_REL) {   // (balanced products slice per tile)
+                E.aimg = ws.get<unsigned char>(emu_update_aimg_bytes(E.ord.dev_per_step, k));
+                E.atab = ws.get<int>((size_t)E.ord.dev_per_step * np);
+                E.qimg = ws.get<unsigned char>(emu_update_qimg_bytes(E.ord.dev_per_step, k, np));
+                E.qexp = ws.get<int>((size_t)E.ord.dev_per_step * np);
+            }
         }
         E.balance = p.conv == JACOBI_CONV_REL;
         xexp = ws.get<int>(2 * (size_t)np);

@@ -222,6 +222,11 @@ struct EvdState {
     // the step's V sliced once (bf16 digit images) and its column scales
     unsigned char* vimg = nullptr;
     int* vexp = nullptr;
+    // and the step's stage-1 operands (A's pair-blocks, Q's column pairs)
+    unsigned char* aimg = nullptr;
+    int* atab = nullptr;
+    unsigned char* qimg = nullptr;
+    int* qexp = nullptr;
     // pivot_order == 2: the per-pair QRCP scratch of the pivoting step
     double* qrws = nullptr;
     // emulated products: balance by the diagonal (relative stop criterion)

@@ -226,10 +226,20 @@ struct EmuUpdArgs {
     // slicing V themselves
     unsigned char* vimg = nullptr;
     int* vexp = nullptr;
+    // optional (with vimg, without balance): the step's stage-1 operands
+    // sliced once as well -- every off-diagonal pair-block A_{P1P2} with its
+    // row scales over P2 (aimg, atab), every column pair Q(:, P) with its row
+    // scales over P (qimg, qtab) -- so the stage-1 tiles slice nothing
+    unsigned char* aimg = nullptr;
+    int* atab = nullptr;
+    unsigned char* qimg = nullptr;
+    int* qexp = nullptr;
 };
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s);
 size_t emu_update_vimg_bytes(int npairs, int k);
 size_t emu_update_vexp_ints(int npairs, int k);
+size_t emu_update_aimg_bytes(int npairs, int k);
+size_t emu_update_qimg_bytes(int npairs, int k, int qrows);
 // The one-sided step's products FP64-accurate on the tensor cores: Gram
 // partials per pair and row panel (the layout the pivot kernel reads), and
 // the column update of G and V.

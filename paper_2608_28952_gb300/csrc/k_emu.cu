@@ -717,6 +717,61 @@ __global__ void __launch_bounds__(E_T) k_emu_slice_v(const double* __restrict__ 
     }
 }
 
+// Row scales of the stage-1 A operands: out[e][i] = 1 + the largest exponent
+// of X(i, P_e) over the 2b columns of pair e (0 when all are zero), for the
+// rows i < rows of X (the working A, or Q).  Thread = row (coalesced).
+__global__ void k_emu_rowexp(int rows, const double* __restrict__ X, int ld, const int2* __restrict__ pairs,
+                             int b, int* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, e = blockIdx.y;
+    if (i >= rows) return;
+    int I, J;
+    eentry(pairs, e, I, J);
+    int mx = -1100;
+    for (int x = 0; x < 2 * b; ++x) mx = max(mx, exp2_of(X[i + (size_t)ld * emap(I, J, b, x)]));
+    out[(size_t)e * rows + i] = mx <= -1100 ? 0 : mx + 1;
+}
+
+// The slices of the stage-1 A operands, once per step.  mode 0: pair-block
+// pb = (e1 < e2), rows = pair e1's 2b rows of A, K = pair e2's 2b columns,
+// row scales atab[e2][row] (the table has `rows` = np rows); its image
+// (nchk x 8 slices x kr x 64 bytes) at img + pb * that.  mode 1: pair e,
+// rows = all `rows` = qrows rows of Q, K = pair e's columns, row scales
+// qexp[e][row]; image nchk x 8 x qr x 64 bytes at img + e * that.  Block (c, row group of 64, item); blocks whose V is the
+// identity (no rotation: the update copies) are skipped.
+__global__ void __launch_bounds__(E_T) k_emu_slice_ops(int mode, const double* __restrict__ X, int ld, int rows,
+                                                       const int2* __restrict__ pairs, const int* __restrict__ rot,
+                                                       int b, int k, const int* __restrict__ tab, int R,
+                                                       unsigned char* __restrict__ img)
+{
+    const int c = blockIdx.x, r = blockIdx.y * 64 + (threadIdx.x & 63), g = threadIdx.x >> 6, item = blockIdx.z;
+    const int nchk = (k + EK - 1) / EK;
+    int eK, I1 = 0, J1 = 0, I2, J2;
+    if (mode == 0) {
+        int e1, e2;
+        edecode_pb(item, e1, e2);
+        eentry(pairs, e1, I1, J1);
+        eentry(pairs, e2, I2, J2);
+        eK = e2;
+    } else {
+        eentry(pairs, item, I2, J2);
+        eK = item;
+    }
+    if (rot[eK] == 0) return;
+    const int nrow = mode == 0 ? k : rows;
+    const int grow = r < nrow ? (mode == 0 ? emap(I1, J1, b, r) : r) : -1;
+    const size_t sb = (size_t)R * EK * 2;
+    const int k0 = c * EK + g * 8;
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int kk = k0 + u;
+        x[u] = (grow >= 0 && kk < k) ? X[grow + (size_t)ld * emap(I2, J2, b, kk)] : 0.0;
+    }
+    const int E = grow >= 0 ? tab[(size_t)eK * rows + grow] : 0;
+    store_slices(img + ((size_t)item * nchk + c) * ENS * sb, (int)sb, r, g * 8, x, E);
+}
+
 // Stage 1.  Items [0, n_sand): tile (mt, nt) of T_pb = A_{P1P2} V2 (FP64,
 // k x k per pair-block); items beyond: tile (rt, nt) of Q'(:,P) = Q(:,P) V_P.
 // V^T (stored after V by the pivot kernel) gives the coalesced operand loads.
@@ -768,17 +823,28 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
             if constexpr (BAL) return pow2_shift(x, -s_cs[kk]);
             return x;
         };
-        line_exponents(EM, k, fa, s_eA, s_scr);
         auto stT = [&](int m, int n, double v) {
             if (m0 + m < k && n0 + n < k) T[(m0 + m) + (size_t)k * (n0 + n)] = v;
         };
-        if (!BAL && a.vimg) {   // V2's slices from the step's image
+        if (!BAL && a.vimg && a.aimg) {   // both operands' slices from the step's images
+            const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+            const size_t sb = emu_img_slice_bytes(k);
+            for (int m = threadIdx.x; m < EM; m += E_T)
+                s_eA[m] = m0 + m < k ? a.atab[(size_t)e2 * u.lda + emap(I1, J1, b, m0 + m)] : 0;
+            for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e2 * kr + n0 + n];
+            __syncthreads();
+            const unsigned char* ia = a.aimg + (size_t)pb * nchk * ENS * sb + (size_t)m0 * EK * 2;
+            const unsigned char* im = a.vimg + (size_t)e2 * nchk * ENS * sb + (size_t)n0 * EK * 2;
+            emu_tile<false, true, true>(k, fa, fb, s_eA, s_eB, stT, a.err, ia, im, sb, sb);
+        } else if (!BAL && a.vimg) {   // V2's slices from the step's image
             const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
             for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e2 * kr + n0 + n];
             __syncthreads();
             const unsigned char* im = a.vimg + (size_t)e2 * nchk * ENS * emu_img_slice_bytes(k) + (size_t)n0 * EK * 2;
+            line_exponents(EM, k, fa, s_eA, s_scr);
             emu_tile<false, false, true>(k, fa, fb, s_eA, s_eB, stT, a.err, nullptr, im, emu_img_slice_bytes(k));
         } else {
+            line_exponents(EM, k, fa, s_eA, s_scr);
             line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
             emu_tile<false>(k, fa, fb, s_eA, s_eB, stT, a.err);
         }
@@ -809,17 +875,27 @@ __global__ void __launch_bounds__(E_T, 1) k_emu_upd1(EmuUpdArgs a, int n_sand)
         return r0 + m < u.qrows && kk < k ? u.Qin[(r0 + m) + (size_t)u.ldq * emap(I, J, b, kk)] : 0.0;
     };
     auto fb = [&](int kk, int n) -> double { return n0 + n < k && kk < k ? Vt[(n0 + n) + (size_t)k * kk] : 0.0; };
-    line_exponents(EM, k, fa, s_eA, s_scr);
     auto stQ = [&](int m, int n, double v) {
         if (r0 + m < u.qrows && n0 + n < k) u.Qout[(r0 + m) + (size_t)u.ldq * emap(I, J, b, n0 + n)] = v;
     };
-    if (a.vimg) {   // V_P's slices from the step's image (the Q items never balance)
+    if (a.vimg && a.qimg) {   // Q(:, P)'s and V_P's slices from the step's images
+        const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
+        const size_t sb = emu_img_slice_bytes(k), sq = emu_img_slice_bytes(u.qrows);
+        for (int m = threadIdx.x; m < EM; m += E_T) s_eA[m] = r0 + m < u.qrows ? a.qexp[(size_t)e * u.qrows + r0 + m] : 0;
+        for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e * kr + n0 + n];
+        __syncthreads();
+        const unsigned char* iq = a.qimg + (size_t)e * nchk * ENS * sq + (size_t)r0 * EK * 2;
+        const unsigned char* im = a.vimg + (size_t)e * nchk * ENS * sb + (size_t)n0 * EK * 2;
+        emu_tile<false, true, true>(k, fa, fb, s_eA, s_eB, stQ, a.err, iq, im, sq, sb);
+    } else if (a.vimg) {   // V_P's slices from the step's image (the Q items never balance)
         const int kr = emu_img_rows(k), nchk = (k + EK - 1) / EK;
         for (int n = threadIdx.x; n < EN; n += E_T) s_eB[n] = a.vexp[(size_t)e * kr + n0 + n];
         __syncthreads();
         const unsigned char* im = a.vimg + (size_t)e * nchk * ENS * emu_img_slice_bytes(k) + (size_t)n0 * EK * 2;
+        line_exponents(EM, k, fa, s_eA, s_scr);
         emu_tile<false, false, true>(k, fa, fb, s_eA, s_eB, stQ, a.err, nullptr, im, emu_img_slice_bytes(k));
     } else {
+        line_exponents(EM, k, fa, s_eA, s_scr);
         line_exponents(EN, k, [&](int n, int kk) { return fb(kk, n); }, s_eB, s_scr);
         emu_tile<false>(k, fa, fb, s_eA, s_eB, stQ, a.err);
     }
@@ -1027,6 +1103,14 @@ size_t emu_update_vimg_bytes(int npairs, int k)
     return (size_t)npairs * ((k + EK - 1) / EK) * ENS * emu_img_slice_bytes(k);
 }
 size_t emu_update_vexp_ints(int npairs, int k) { return (size_t)npairs * emu_img_rows(k); }
+size_t emu_update_aimg_bytes(int npairs, int k)
+{
+    return (size_t)(npairs * (npairs - 1) / 2) * ((k + EK - 1) / EK) * ENS * emu_img_slice_bytes(k);
+}
+size_t emu_update_qimg_bytes(int npairs, int k, int qrows)
+{
+    return (size_t)npairs * ((k + EK - 1) / EK) * ENS * emu_img_slice_bytes(qrows);
+}
 
 cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
 {
@@ -1038,6 +1122,19 @@ cudaError_t launch_emu_update(const EmuUpdArgs& a, cudaStream_t s)
         k_emu_slice_v<<<dim3((u.k + EK - 1) / EK, u.npairs), E_T, 0, s>>>(u.V, u.rot, u.k, a.vexp, a.vimg);
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
+        const int nchk = (u.k + EK - 1) / EK;
+        const int npb = u.npairs * (u.npairs - 1) / 2;
+        if (a.aimg && !a.balance && npb > 0) {   // the pair-blocks of A, sliced once
+            k_emu_rowexp<<<dim3((u.lda + 255) / 256, u.npairs), 256, 0, s>>>(u.lda, u.Ain, u.lda, u.pairs, u.b, a.atab);
+            k_emu_slice_ops<<<dim3(nchk, emu_img_rows(u.k) / 64, npb), E_T, 0, s>>>(
+                0, u.Ain, u.lda, u.lda, u.pairs, u.rot, u.b, u.k, a.atab, emu_img_rows(u.k), a.aimg);
+        }
+        if (a.qimg && u.Qin) {   // the column pairs of Q, sliced once
+            k_emu_rowexp<<<dim3((u.qrows + 255) / 256, u.npairs), 256, 0, s>>>(u.qrows, u.Qin, u.ldq, u.pairs, u.b, a.qexp);
+            k_emu_slice_ops<<<dim3(nchk, emu_img_rows(u.qrows) / 64, u.npairs), E_T, 0, s>>>(
+                1, u.Qin, u.ldq, u.qrows, u.pairs, u.rot, u.b, u.k, a.qexp, emu_img_rows(u.qrows), a.qimg);
+        }
+        if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
     }
     const int npb = u.npairs * (u.npairs - 1) / 2;
     const int n_sand = npb * nmt * nnt;

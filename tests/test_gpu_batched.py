@@ -118,6 +118,31 @@ def test_plan_autotune_and_replay(jg):
     plan.close()
 
 
+@pytest.mark.parametrize("f32", [True, False])
+def test_plan_autotune_chooses_the_block_size_per_size_class(jg, f32):
+    """The autotuner also chooses the order above which the blocked method
+    (b = 16) takes over from the unblocked solve; the plan reports it, and
+    every matrix on either side of it matches the oracle."""
+    import torch
+    r = np.random.default_rng(16)
+    sizes = [int(x) for x in r.integers(150, 513, 200)] + [512, 500, 321, 320, 319, 257, 200]
+    mats = [gen.sym_gaussian(n, 76, i) for i, n in enumerate(sizes)]
+    dt = torch.float32 if f32 else torch.float64
+    As, ws, Qs, info = _mk(jg, mats, dt)
+    plan = jg.Plan(0, jg.PREC_FP32 if f32 else jg.PREC_FP64, sizes, p=jg.params())
+    assert plan.blocking() == (16, plan.blocking()[1])      # default crossover before tuning
+    plan.autotune(As, ws, Qs, info)
+    b, mo = plan.blocking()
+    assert b == 16 and (mo in (0, 192, 256, 320, 384, 448, 512) or mo == plan.shape()[1]), (b, mo)
+    rc, st = plan.execute(As, ws, Qs, info)
+    assert rc == 0 and torch.all(info == 0)
+    tol = (1e-13 * SCALE32) if f32 else 1e-13
+    for i in range(len(sizes) - 7, len(sizes)):
+        w_or = oracle_eig(mats[i])
+        assert np.abs(ws[i].double().cpu().numpy() - w_or).max() <= tol * np.abs(w_or).max(), sizes[i]
+    plan.close()
+
+
 def test_batched_tall_svd_f32(jg):
     import torch
     shapes = [(1024, 64)] * 12 + [(300, 40), (100, 100), (64, 1), (77, 33), (2, 2)]
