@@ -66,6 +66,7 @@ cudaError_t launch_step32(const LowpState& L, int s, int cur, cudaStream_t cs, d
     pa.b = L.b;
     pa.k = L.k;
     pa.V = L.Vb;
+    pa.v32 = 1;   // V only feeds the split products, which take it rounded to FP32
     pa.rot = L.rot;
     pa.tol_rel = inner_tol;
     pa.max_sweeps = inner_max;

@@ -78,6 +78,8 @@ struct PivotArgs {
     int npairs;
     int b, k;
     double* V;                 // [pair][2][k*k]: V then V^T, column-major
+    int v32;                   // accumulate V in FP32 (its output values are FP32 numbers):
+                               // only for a V consumed by the split low-precision products
     int* rot;                  // [pair] rotations applied (0 => V == I)
     double* relmax;            // [pair] (SVD) pre-rotation max normalised off-diag
     double tol_rel;

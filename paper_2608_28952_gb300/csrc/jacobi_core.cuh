@@ -202,11 +202,13 @@ __device__ __forceinline__ void quad_of(const unsigned* qtab, int qi, int& e1, i
 
 // Solve the packed symmetric k x k matrix Ap (k even) in place by blockDim.x
 // threads.  V (k x k, column-major, ld k) accumulates the rotations when not
-// null.  Returns the rotations applied; *sweeps_out = sweeps run.  On return
+// null, in its own type TV (FP32 for a transform that only feeds the split
+// low-precision products: the rotation parameters are rounded to TV once per
+// use).  Returns the rotations applied; *sweeps_out = sweeps run.  On return
 // the diagonal of Ap holds hi + lo rounded once.  Caller: all threads, after
 // Ap, V (= I) and sm.dlo (= 0) are initialised and synchronised.
-template <typename T>
-__device__ int jacobi_solve(T* Ap, T* V, int k, T tol, int max_sweeps, const unsigned* qtab,
+template <typename T, typename TV = T>
+__device__ int jacobi_solve(T* Ap, TV* V, int k, T tol, int max_sweeps, const unsigned* qtab,
                             const CoreSmem<T>& sm, int* sweeps_out)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -276,8 +278,8 @@ __device__ int jacobi_solve(T* Ap, T* V, int k, T tol, int max_sweeps, const uns
                     const int ee = it / k, row = it - ee * k;
                     if (!sm.on[ee]) continue;
                     const int p = sm.p[ee], q = sm.q[ee];
-                    T vp = V[row + (size_t)p * k], vq = V[row + (size_t)q * k];
-                    rot2(sm.s[ee], sm.tau[ee], vp, vq);
+                    TV vp = V[row + (size_t)p * k], vq = V[row + (size_t)q * k];
+                    rot2((TV)sm.s[ee], (TV)sm.tau[ee], vp, vq);
                     V[row + (size_t)p * k] = vp;
                     V[row + (size_t)q * k] = vq;
                 }

@@ -225,9 +225,14 @@ static size_t pivot_smem_bytes(int k)
     return small;
 }
 
-template <bool SMEM>
+template <bool V32> struct VType { using T = double; };
+template <> struct VType<true> { using T = float; };
+
+// V32: V accumulated in FP32 (in the first half of its k x k double region)
+template <bool SMEM, bool V32>
 __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
 {
+    using VT = typename VType<V32>::T;
     extern __shared__ __align__(16) double smem[];
     const int e = blockIdx.x, tid = threadIdx.x;
     const int k = a.k, b = a.b, half = k >> 1;
@@ -235,14 +240,15 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
     const bool frozen = entry(a.pairs, e, I, J);
     const size_t ntp = tri_pad(k);
 
-    double *Ap, *V, *tail;
+    double *Ap, *tail;
+    VT* V;
     if (SMEM) {
         Ap = smem;
-        V = smem + ntp;
-        tail = V + (size_t)k * k;
+        V = reinterpret_cast<VT*>(smem + ntp);
+        tail = smem + ntp + (size_t)k * k;
     } else {
         Ap = a.gscratch + (size_t)e * (ntp + (size_t)k * k);
-        V = Ap + ntp;
+        V = reinterpret_cast<VT*>(Ap + ntp);
         tail = smem;
     }
     CoreSmem<double> cs;
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
             Ap[tri(ii) + jj] = s;
         }
     }
-    for (int idx = tid; idx < k * k; idx += PIV_T) V[idx] = (idx % k == idx / k) ? 1.0 : 0.0;
+    for (int idx = tid; idx < k * k; idx += PIV_T) V[idx] = (idx % k == idx / k) ? VT(1) : VT(0);
     for (int x = tid; x < k; x += PIV_T) cs.dlo[x] = 0.0;
     build_quad_table(quad, half);
     __syncthreads();
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
     // ---- inner sweeps: round-robin over the k indices, k-1 rounds of k/2 rotations
     int sweeps = 0;
     const int total_rot =
-        jacobi_solve<double>(Ap, V, k, a.tol_rel, frozen ? 0 : a.max_sweeps, quad, cs, &sweeps);
+        jacobi_solve<double, VT>(Ap, V, k, a.tol_rel, frozen ? 0 : a.max_sweeps, quad, cs, &sweeps);
 
     // ---- permutation Vhat <- Vhat P: eigenpair at position x moves to
     // s_dest[x]; with order == 1 the non-padding positions receive their
@@ -391,15 +397,11 @@ cudaError_t launch_pivot(const PivotArgs& a, cudaStream_t s)
 {
     if (a.npairs <= 0) return cudaSuccess;
     size_t smem = pivot_smem_bytes(a.k);
-    if (a.k <= 128) {
-        cudaError_t e = cudaFuncSetAttribute(k_pivot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_pivot<true><<<a.npairs, PIV_T, smem, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_pivot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_pivot<false><<<a.npairs, PIV_T, smem, s>>>(a);
-    }
+    void (*kern)(PivotArgs) = a.k <= 128 ? (a.v32 ? k_pivot<true, true> : k_pivot<true, false>)
+                                         : (a.v32 ? k_pivot<false, true> : k_pivot<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.npairs, PIV_T, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -66,7 +66,7 @@ size_t pivot_cluster_smem(int k, int C)
     const int half = k / 2;
     const size_t chunk = (size_t)split_max_chunk(k, C);
     const size_t vrows = (size_t)(k / C) * k;
-    return (chunk + vrows + 4 * (size_t)k + 8 * (size_t)half) * sizeof(double) +
+    return (chunk + vrows + 4 * (size_t)k + 10 * (size_t)half) * sizeof(double) +
            6 * (size_t)half * sizeof(int) + 64;
 }
 
@@ -97,9 +97,16 @@ __device__ __forceinline__ int rr_partner_of(int x, int rd, int k)
     return rr_index_at(k - 1 - rr_position_of(x, rd, k - 1), rd, k - 1);
 }
 
-template <bool kFused>
+template <bool V32> struct PcVType { using T = double; };
+template <> struct PcVType<true> { using T = float; };
+
+// kV32: this CTA's rows of V accumulated in FP32 (rotation parameters rounded
+// to FP32 once, when they are chosen), for a V that only feeds the split
+// low-precision products
+template <bool kFused, bool kV32>
 __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, const unsigned* qtab)
 {
+    using VT = typename PcVType<kV32>::T;
     extern __shared__ __align__(16) double csm[];
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
@@ -124,8 +131,8 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
         return m;
     }();
     double* my_chunk = csm;
-    double* Vl = my_chunk + chunk_max;       // rows x k (ld rows): V(r_lo + i, j) at Vl[i + rows j]
-    double* dhi = Vl + (size_t)rows * k;     // diagonal replica (fused: round-parity buffer 0)
+    VT* Vl = reinterpret_cast<VT*>(my_chunk + chunk_max);   // rows x k (ld rows): V(r_lo + i, j) at Vl[i + rows j]
+    double* dhi = my_chunk + chunk_max + (size_t)rows * k;  // diagonal replica (fused: round-parity buffer 0)
     double* dlo = dhi + k;
     double* dhi1 = dlo + k;                  // fused: round-parity buffer 1
     double* dlo1 = dhi1 + k;
@@ -133,7 +140,9 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     double* rs = rtau + 2 * half;
     double* rt = rs + 2 * half;
     double* rapq = rt + 2 * half;
-    int* rp = (int*)(rapq + 2 * half);
+    float* rs32 = (float*)(rapq + 2 * half);  // kV32: s and tau rounded to FP32, same slots
+    float* rtau32 = rs32 + 2 * half;
+    int* rp = (int*)(rtau32 + 2 * half);
     int* rq = rp + 2 * half;
     int* ron = rq + 2 * half;
     __shared__ int s_cnt[2];   // rotations chosen per sweep (by sweep parity)
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
     }
     for (int idx = tid; idx < rows * k; idx += nt) {
         const int i = idx % rows, j = idx / rows;
-        Vl[idx] = (r_lo + i == j) ? 1.0 : 0.0;
+        Vl[idx] = (r_lo + i == j) ? VT(1) : VT(0);
     }
     cluster.sync();
     for (int x = tid; x < k; x += nt) {
@@ -245,6 +254,10 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                 rs[o] = sv;
                 rt[o] = tv;
                 rapq[o] = apq;
+                if (kV32) {
+                    rs32[o] = (float)sv;
+                    rtau32[o] = (float)tauv;
+                }
                 atomicAdd(cnt, 1);
             }
         }
@@ -311,8 +324,9 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                         const int ee = it / rows, i = it - ee * rows;
                         if (!ron[so + ee]) continue;
                         const int p = rp[so + ee], q = rq[so + ee];
-                        double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
-                        rot2(rs[so + ee], rtau[so + ee], vp, vq);
+                        VT vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                        if constexpr (kV32) rot2(rs32[so + ee], rtau32[so + ee], vp, vq);
+                        else rot2(rs[so + ee], rtau[so + ee], vp, vq);
                         Vl[i + (size_t)rows * p] = vp;
                         Vl[i + (size_t)rows * q] = vq;
                     }
@@ -368,6 +382,10 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                     *cluster.map_shared_rank(&rs[o], u) = sv;
                     *cluster.map_shared_rank(&rt[o], u) = tv;
                     *cluster.map_shared_rank(&rapq[o], u) = axy;
+                    if (kV32) {
+                        *cluster.map_shared_rank(&rtau32[o], u) = (float)tauv;
+                        *cluster.map_shared_rank(&rs32[o], u) = (float)sv;
+                    }
                 }
             }
             if (on) atomicAdd(&cnt0[cslot & 3], 1);
@@ -392,6 +410,10 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                     rs[ee] = sv;
                     rt[ee] = tv;
                     rapq[ee] = apq;
+                    if (kV32) {
+                        rs32[ee] = (float)sv;
+                        rtau32[ee] = (float)tauv;
+                    }
                     if (r == 0) atomicAdd(&s_cntg[0], 1);
                 }
             }
@@ -512,8 +534,9 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
                         const int ee = it / rows, i = it - ee * rows;
                         if (!ron[so + ee]) continue;
                         const int p = rp[so + ee], q = rq[so + ee];
-                        double vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
-                        rot2(rs[so + ee], rtau[so + ee], vp, vq);
+                        VT vp = Vl[i + (size_t)rows * p], vq = Vl[i + (size_t)rows * q];
+                        if constexpr (kV32) rot2(rs32[so + ee], rtau32[so + ee], vp, vq);
+                        else rot2(rs[so + ee], rtau[so + ee], vp, vq);
                         Vl[i + (size_t)rows * p] = vp;
                         Vl[i + (size_t)rows * q] = vq;
                     }
@@ -648,7 +671,9 @@ cudaError_t launch_pivot_cluster(const PivotArgs& a, int C, const unsigned* qtab
     bool fused = a.k > 128;   // measured on GB300: fused 7 % faster at k = 256, 26 % slower at k = 128
     if (env && strcmp(env, "split") == 0) fused = false;
     if (env && strcmp(env, "fused") == 0) fused = true;
-    auto kern = fused ? k_pivot_cluster<true> : k_pivot_cluster<false>;
+    void (*kern)(PivotArgs, int, const unsigned*) =
+        fused ? (a.v32 ? k_pivot_cluster<true, true> : k_pivot_cluster<true, false>)
+              : (a.v32 ? k_pivot_cluster<false, true> : k_pivot_cluster<false, false>);
     const size_t smem = pivot_cluster_smem(a.k, C);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

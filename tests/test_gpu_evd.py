@@ -423,3 +423,24 @@ def test_pivot_schedules_agree_bit_for_bit(jg, monkeypatch, np_, b, cl):
     a, f = out["split"], out["fused"]
     for x, y in zip(a, f):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("np_,b,cl", [(512, 64, "1"), (512, 64, "4"), (1024, 128, "4"), (768, 64, "8")])
+def test_fp32_transform_schedules_agree_bit_for_bit(jg, monkeypatch, np_, b, cl):
+    """The low-precision step accumulates each pivot's V in FP32: the split
+    and fused cluster schedules still agree bit for bit (cluster size 1 runs
+    the one-CTA kernel; its accuracy, like the others', is held to the
+    oracle's step by the mixed-form tests)."""
+    import torch
+    monkeypatch.setenv("JACOBI_PIVOT_CLUSTER", cl)
+    A32 = np.asfortranarray(gen.sym_gaussian(np_, 5600 + np_).astype(np.float32))
+    out = {}
+    for sched in ("split", "fused"):
+        monkeypatch.setenv("JACOBI_PIVOT_SCHEDULE", sched)
+        Ad = jg.colmajor(A32, device="cuda", dtype=torch.float32)
+        Qd = jg.colmajor(np.eye(np_, dtype=np.float32), device="cuda", dtype=torch.float32)
+        for s in (0, 1):
+            assert jg.jacobi_syev_step_lowp(Ad, Qd, s, jg.params(b=b, precision=2)) == 0
+        out[sched] = (_np(Ad), _np(Qd))
+    for x, y in zip(out["split"], out["fused"]):
+        assert np.array_equal(x, y)

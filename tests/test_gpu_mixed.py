@@ -4,8 +4,14 @@ One low-precision step (FP64 pivot solves on the promoted FP32 pivots, block
 updates on the tensor cores from bf16 hi/lo splits) against the oracle's FP64
 step on the same FP32 input, element-wise within the bound of the split
 product: every product loses at most the lo*lo term (2^-18 relative per
-operand pair) and V enters rounded to FP32, two products per A entry, FP32
-accumulation over k terms; so |A' - A'_oracle| <= (2^-15 + 4 k u32) (|V|^T |A| |V|).
+operand pair), two products per A entry, FP32 accumulation over k terms:
+(2^-15 + 4 k u32) (|V|^T |A| |V|).  In these sweeps the pivot accumulates V
+in FP32 (the products take it rounded to FP32 anyway): each of its k - 1
+rounds rotates a row's entry pair (x, y), of norm <= 1, with s and tau
+rounded to FP32 and two FP32 fma roundings, an error of at most 6 u32
+(later exact rotations carry it without growth), so |E| <= 6 k u32 entry-wise
+inside each pair's k x k block (mask B) and A' gains
+6 k u32 (B |A| |V| + |V|^T |A| B), Q' gains 6 k u32 |Q| B.
 
 Full mixed solves are held to ten times the FP64 gates (eigenvalues,
 residual, orthogonality), against the constructed spectrum and the oracle.
@@ -83,15 +89,22 @@ def test_lowp_step_matches_oracle_within_split_bound(jg, np_, b, ordering, steps
         Ag, Qg = _np(Ad).astype(np.float64), _np(Qd).astype(np.float64)
         assert np.array_equal(Ag, Ag.T)
         aV = np.abs(V)
+        B = np.zeros((np_, np_))   # 1 inside each pair's k x k block
+        for I, J in tab[s]:
+            idx = np.r_[I * b:(I + 1) * b, J * b:(J + 1) * b]
+            B[np.ix_(idx, idx)] = 1.0
+        AV = np.abs(A64) @ aV
+        vacc = 6 * k * U32 * (B @ AV + AV.T @ B)
         c = 2.0 ** -15 + 4 * k * U32
-        boundA = c * (aV.T @ np.abs(A64) @ aV) + 1e-30
-        boundQ = c * (np.abs(Q64) @ aV) + 1e-30
+        boundA = c * (aV.T @ np.abs(A64) @ aV) + vacc + 1e-30
+        boundQ = c * (np.abs(Q64) @ aV) + 6 * k * U32 * (np.abs(Q64) @ B) + 1e-30
         if prec == MIXED_F16:
             # fp16 splits: 22 bits in the normal range; entries of V and Q
             # below it (|x| < 2^-14) keep an absolute error of at most 2^-25
             c16 = 2.0 ** -20 + 4 * k * U32
-            boundA = c16 * (aV.T @ np.abs(A64) @ aV) + 2.0 ** -24 * (np.abs(A64) @ np.ones_like(aV)).max() + 1e-30
-            boundQ = c16 * (np.abs(Q64) @ aV) + 2.0 ** -24 * k + 1e-30
+            boundA = (c16 * (aV.T @ np.abs(A64) @ aV) + 2.0 ** -24 * (np.abs(A64) @ np.ones_like(aV)).max()
+                      + vacc + 1e-30)
+            boundQ = c16 * (np.abs(Q64) @ aV) + 2.0 ** -24 * k + 6 * k * U32 * (np.abs(Q64) @ B) + 1e-30
         ra = np.abs(Ag - A_or) / boundA
         rq = np.abs(Qg - Q_or) / boundQ
         assert ra.max() <= 1.0, ra.max()
