@@ -388,8 +388,9 @@ __global__ void __launch_bounds__(PIV_T) k_pivot(PivotArgs a)
         atomicAdd(&a.cnt->inner_sweeps, (unsigned long long)sweeps);
         if (!frozen) atomicAdd(&a.cnt->pair_solves, 1ull);
         // per applied rotation: its row pair in k/2-1 quads (12 flops each, as
-        // left and as right factor) and its column pair of V (6k flops)
-        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)(18 * k));
+        // left and as right factor) and its column pair of V (6k flops, FP32
+        // and not counted here when V is accumulated in FP32)
+        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)((a.v32 ? 12 : 18) * k));
     }
 }
 

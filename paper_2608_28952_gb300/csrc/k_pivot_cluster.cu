@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(PC_T) k_pivot_cluster(PivotArgs a, int C, cons
         atomicAdd(&a.cnt->rotations, (unsigned long long)total_rot);
         atomicAdd(&a.cnt->inner_sweeps, (unsigned long long)sweeps);
         if (!frozen) atomicAdd(&a.cnt->pair_solves, 1ull);
-        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)(18 * k));
+        atomicAdd(&a.cnt->flops_fp64, (unsigned long long)total_rot * (unsigned long long)((a.v32 ? 12 : 18) * k));
     }
     // no CTA may leave while others can still read its shared memory
     cluster.sync();
