@@ -96,23 +96,37 @@ struct Pack8 {
     uint4 hi, lo;
 };
 
+// hi = r(x), lo = r(x - hi) for eight values, two per conversion (the paired
+// round-to-nearest conversions give the same bits as one value at a time);
+// fp16 values are scaled first, bf16 values are not (scale is 1 there).
 template <bool F16>
 __device__ __forceinline__ Pack8 split8(const float (&x)[8], float scale = 1.f)
 {
     Pack8 p;
+    uint32_t hw[4], lw[4];
     if (F16) {
-        __half h[8], l[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) split_f16(x[u] * scale, h[u], l[u]);
-        p.hi = *reinterpret_cast<const uint4*>(h);
-        p.lo = *reinterpret_cast<const uint4*>(l);
+        for (int u = 0; u < 4; ++u) {
+            const float a = x[2 * u] * scale, b = x[2 * u + 1] * scale;
+            const __half2 h = __floats2half2_rn(a, b);
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+            hw[u] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[u] = *reinterpret_cast<const uint32_t*>(&l);
+        }
     } else {
-        __nv_bfloat16 h[8], l[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) split_bf16(x[u] * scale, h[u], l[u]);
-        p.hi = *reinterpret_cast<const uint4*>(h);
-        p.lo = *reinterpret_cast<const uint4*>(l);
+        for (int u = 0; u < 4; ++u) {
+            const float a = x[2 * u], b = x[2 * u + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+            hw[u] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[u] = *reinterpret_cast<const uint32_t*>(&l);
+        }
     }
+    p.hi = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    p.lo = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     return p;
 }
 
@@ -166,8 +180,8 @@ struct GatherF32 {
     size_t ld;
     int rows[2];        // global row of the thread's two items (or -1)
     float scale[2];     // power-of-two scale of the two items' rows (FP16x3)
-    float v[2][8];
-    template <class COL>
+    float v[2][2][8];   // register slot (chunk parity), item, value
+    template <int S, class COL>
     __device__ __forceinline__ void load(int c, COL col)
     {
         const int tid = threadIdx.x;
@@ -177,19 +191,35 @@ struct GatherF32 {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int cc = col(c * TC_BK + g * 8 + u);
-                v[i][u] = (rows[i] >= 0 && cc >= 0) ? __ldg(base + rows[i] + ld * (size_t)cc) : 0.f;
+                v[S][i][u] = (rows[i] >= 0 && cc >= 0) ? __ldg(base + rows[i] + ld * (size_t)cc) : 0.f;
             }
         }
     }
+    template <int S>
     __device__ __forceinline__ void store(unsigned char* dst) const
     {
         const int tid = threadIdx.x;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, r = item & 127, g = item >> 7;
-            store8<KIND>(dst, r, g * 8, v[i], scale[i]);
+            store8<KIND>(dst, r, g * 8, v[S][i], scale[i]);
         }
     }
+};
+
+// The gather over the columns (K) of the pair (I, J): column x of the
+// operand is global column umap(I, J, b, x).
+template <int KIND>
+struct GatherPairCols {
+    GatherF32<KIND>& g;
+    int I, J, b, k;
+    template <int S>
+    __device__ __forceinline__ void load(int c)
+    {
+        g.template load<S>(c, [&](int x) { return x < k ? umap(I, J, b, x) : -1; });
+    }
+    template <int S>
+    __device__ __forceinline__ void store(unsigned char* d) const { g.template store<S>(d); }
 };
 
 // K-major FP32 (T of stage 2 as the B operand): element (n, kk) =
@@ -201,7 +231,8 @@ struct KMajorF32 {
     int k, n0;
     bool vec4;
     const float* cscale;   // shared memory: power-of-two scale of column n (FP16x3), or null
-    float v[2][8];
+    float v[2][2][8];      // register slot (chunk parity), item, value
+    template <int S>
     __device__ __forceinline__ void load(int c)
     {
         const int tid = threadIdx.x;
@@ -213,21 +244,22 @@ struct KMajorF32 {
             if (col < k && vec4 && kk0 + 8 <= k) {
                 const float4 a = __ldg(reinterpret_cast<const float4*>(src));
                 const float4 b = __ldg(reinterpret_cast<const float4*>(src + 4));
-                v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
-                v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
+                v[S][i][0] = a.x; v[S][i][1] = a.y; v[S][i][2] = a.z; v[S][i][3] = a.w;
+                v[S][i][4] = b.x; v[S][i][5] = b.y; v[S][i][6] = b.z; v[S][i][7] = b.w;
             } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[i][u] = (col < k && kk0 + u < k) ? __ldg(src + u) : 0.f;
+                for (int u = 0; u < 8; ++u) v[S][i][u] = (col < k && kk0 + u < k) ? __ldg(src + u) : 0.f;
             }
         }
     }
+    template <int S>
     __device__ __forceinline__ void store(unsigned char* dst) const
     {
         const int tid = threadIdx.x;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int item = tid + U_T * i, g = item & 3, n = item >> 2;
-            store8<KIND>(dst, n, g * 8, v[i], cscale ? cscale[n] : 1.f);
+            store8<KIND>(dst, n, g * 8, v[S][i], cscale ? cscale[n] : 1.f);
         }
     }
 };
@@ -246,7 +278,9 @@ struct ImageTile {
     {
         return img + ((size_t)t * nchk + c) * KT<KIND>::IMG;
     }
+    template <int S>
     __device__ __forceinline__ void load(int) {}
+    template <int S>
     __device__ __forceinline__ void store(unsigned char*) const {}
 };
 
@@ -257,6 +291,11 @@ struct IsBulk {
 template <class L>
 struct IsBulk<L, decltype((void)L::kBulk)> {
     static constexpr bool value = L::kBulk;
+};
+
+template <int S>
+struct Slot {
+    static constexpr int value = S;
 };
 
 // Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
@@ -323,18 +362,28 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
         ++bulk_issued;
     };
     if (kAnyBulk && tid == 0) issue_bulk(0);
-    la.load(0);
-    lb.load(0);
-    for (int c = 0; c < nchk; ++c) {
+    // register-staged operands: chunk c in register slot c % 2, its loads
+    // issued two chunks ahead (a slot is refilled right after its store), so
+    // their latency spans two chunks' MMAs; the slot is a compile-time index
+    la.template load<0>(0);
+    lb.template load<0>(0);
+    if (nchk > 1) {
+        la.template load<1>(1);
+        lb.template load<1>(1);
+    }
+    auto step = [&](int c, auto slot) -> bool {
+        constexpr int S = decltype(slot)::value;
         const int s = c % U_NS;
         unsigned char* st = base + s * KT<KIND>::STAGE;
         // the MMAs that last read this stage (chunk c - U_NS) must be complete
         if (c >= U_NS && !mbar_wait(smem_u32(&s_bar[s]), (uses[s] - 1) & 1)) s_fail = 1;
-        la.store(st);
-        lb.store(st + 2 * TB);
-        if (c + 1 < nchk) {  // next chunk's loads in flight during this chunk's MMAs
-            la.load(c + 1);
-            lb.load(c + 1);
+        la.template store<S>(st);
+        lb.template store<S>(st + 2 * TB);
+        if (c + 2 < nchk) {  // the loads of chunk c + 2 into the slot just stored
+            la.template load<S>(c + 2);
+            lb.template load<S>(c + 2);
+        }
+        if (c + 1 < nchk) {
             if (kAnyBulk && tid == 0 && !s_fail) {
                 const int s1 = (c + 1) % U_NS;
                 if (c + 1 >= U_NS && !mbar_wait(smem_u32(&s_bar[s1]), (uses[s1] - 1) & 1)) s_fail = 1;
@@ -343,7 +392,7 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (s_fail) break;
+        if (s_fail) return false;
         if (tid == 0) {
             bool landed = true;
             if (kAnyBulk) {
@@ -395,6 +444,11 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
                          : "memory");
         }
         uses[s]++;
+        return true;
+    };
+    for (int c = 0; c < nchk; c += 2) {
+        if (!step(c, Slot<0>{})) break;
+        if (c + 1 < nchk && !step(c + 1, Slot<1>{})) break;
     }
     // bulk copies issued but not waited for (a failed tile breaks early):
     // wait for them (bounded) before the shared memory is given up
@@ -512,12 +566,7 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
             }
         }
         ImageTile<KIND> lb{a.vimg + (size_t)e2 * ntk * nchk * KT<KIND>::IMG, nchk, nt};
-        struct LA {
-            GatherF32<KIND>& g;
-            int I2, J2, b, k;
-            __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I2, J2, b, x) : -1; }); }
-            __device__ void store(unsigned char* d) const { g.store(d); }
-        } lawrap{la, I2, J2, b, k};
+        GatherPairCols<KIND> lawrap{la, I2, J2, b, k};
         tc_tile<KIND>(nchk, lawrap, lb,
                      [&](int m, int j0, const float (&v)[8]) {
                          const bool live = m0 + m < k;
@@ -569,12 +618,7 @@ __global__ void __launch_bounds__(U_T) k_tc_upd1(TcUpdArgs a, int n_sand)
         la.scale[i] = 1.f;
     }
     ImageTile<KIND> lb{a.vimg + (size_t)e * ntk * nchk * KT<KIND>::IMG, nchk, nt};
-    struct LA {
-        GatherF32<KIND>& g;
-        int I, J, b, k;
-        __device__ void load(int c) { g.load(c, [&](int x) { return x < k ? umap(I, J, b, x) : -1; }); }
-        __device__ void store(unsigned char* d) const { g.store(d); }
-    } lawrap{la, I, J, b, k};
+    GatherPairCols<KIND> lawrap{la, I, J, b, k};
     tc_tile<KIND>(nchk, lawrap, lb,
                  [&](int m, int j0, const float (&v)[8]) {
                      if (r0 + m >= a.qrows) return;
