@@ -44,7 +44,7 @@ namespace jac {
 namespace {
 
 constexpr int U_T = 256;
-constexpr int U_NS = 3;
+constexpr int U_NS = 3;   // most pipeline stages of any kind
 
 // Operand kinds: 0 bf16 hi/lo, 1 fp16 hi/lo (power-of-two scaled), 2 tf32
 // big/small (x = big + small, big = x with its low 13 mantissa bits cleared,
@@ -54,7 +54,11 @@ struct KT {
     static constexpr int EB = KIND == 2 ? 4 : 2;            // bytes per element in shared memory
     static constexpr int TILE = TC_BM * TC_BK * EB;          // one 128 x 32 part (8 or 16 KB)
     static constexpr int STAGE = 4 * TILE;                   // A hi, A lo, B hi, B lo
-    static constexpr int SMEM = U_NS * STAGE + 1024;
+    // bf16 / fp16: two 32 KB stages, so three CTAs share an SM (one's
+    // epilogue and set-up overlap the others' main loops); tf32 (64 KB
+    // stages, one CTA per SM either way): three
+    static constexpr int NS = KIND == 2 ? 3 : 2;
+    static constexpr int SMEM = NS * STAGE + 1024;
     static constexpr int IMG = 2 * TILE;                     // hi + lo of one operand tile
     static constexpr int SBO = KIND == 2 ? 1024 : 512;       // next 8-row group of core matrices
     static constexpr int KSTEP = KIND == 2 ? 8 : 16;         // K of one MMA
@@ -319,6 +323,7 @@ __device__ void tc_tile(int nchk, LA& la, LB& lb, EP ep, int* err)
     __shared__ __align__(8) uint64_t s_bar[U_NS];
     __shared__ __align__(8) uint64_t s_full[U_NS];   // bulk (TMA) operand copies of a stage landed
     __shared__ int s_fail;
+    constexpr int U_NS = KT<KIND>::NS;   // this kind's stages (the arrays above have room for the most)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)usm + 1023) & ~(uintptr_t)1023);
     constexpr bool kBA = IsBulk<LA>::value, kBB = IsBulk<LB>::value, kAnyBulk = kBA || kBB;
