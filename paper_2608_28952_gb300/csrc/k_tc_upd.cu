@@ -56,7 +56,8 @@ struct KT {
     static constexpr int STAGE = 4 * TILE;                   // A hi, A lo, B hi, B lo
     // bf16 / fp16: two 32 KB stages, so three CTAs share an SM (one's
     // epilogue and set-up overlap the others' main loops); tf32 (64 KB
-    // stages, one CTA per SM either way): three
+    // stages, one CTA per SM either way): three.  At least two: the next
+    // chunk's bulk copy goes into the other stage while this one computes.
     static constexpr int NS = KIND == 2 ? 3 : 2;
     static constexpr int SMEM = NS * STAGE + 1024;
     static constexpr int IMG = 2 * TILE;                     // hi + lo of one operand tile
