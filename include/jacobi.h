@@ -78,7 +78,10 @@ extern "C" {
  *  FP32:          the batched forms' FP32 storage and arithmetic.
  *  MIXED_BF16X3:  low-precision sweeps on FP32 working copies, products on the
  *                 tensor cores from bf16 hi/lo splits (three products), then
- *                 the FP64 refinement and closing sweeps (jacobi_syev).
+ *                 the FP64 refinement and closing sweeps (jacobi_syev).  In
+ *                 the low-precision sweeps the pivot solves (matrix, diagonal,
+ *                 rotation parameters) stay FP64 and accumulate each pivot's
+ *                 transform V in FP32, the precision the products take it in.
  *  MIXED_FP16X3:  the same with fp16 hi/lo splits (22 bits per operand), the
  *                 FP32 operands scaled by powers of two per row / column.
  *  MIXED_TF32:    the same with tf32 big/small splits (x = big + small, big =
@@ -174,7 +177,8 @@ typedef struct {
     long long launches;      /* kernels this call launched                     */
     long long pivot_launches;  /* of which pivot-solve kernels                 */
     long long update_launches; /* of which update kernels                      */
-    double flops_fp64;       /* FP64 flops issued (updates + pivot solves)     */
+    double flops_fp64;       /* FP64 flops issued (updates + pivot solves; a
+                                V accumulated in FP32 is not counted)          */
     double flops_update;     /* of which in the update / Gram kernels          */
     double flops_fp32;       /* FP32 flops issued                              */
     double flops_lowp;       /* bf16 / fp16 / tf32 tensor flops issued         */
@@ -486,8 +490,9 @@ int jacobi_f64emu_gemm(int M, int N, int K, const double* A, int lda, int transA
  * blocks of step `step` are promoted to FP64 and solved in FP64 (as in
  * jacobi_syev_step), D is written back rounded to FP32, and every
  * block-row/column update of A (A'_{P1P2} = V1^T A_{P1P2} V2, mirrored) and
- * column update of Q (Q'(:,P) = Q(:,P) V_P) is formed from V rounded to FP32
- * by the split-precision product of jacobi_lowp_gemm (bf16 splits; fp16
+ * column update of Q (Q'(:,P) = Q(:,P) V_P) is formed from V (accumulated in
+ * FP32 by the pivot solve: |dV| <= 6 k u32 entry-wise inside each pair's
+ * k x k block, k = 2b) by the split-precision product of jacobi_lowp_gemm (bf16 splits; fp16
  * splits with power-of-two row/column scaling for MIXED_FP16X3).  A is a full
  * symmetric np x np FP32 matrix (exactly symmetric), np = N * p->b with N
  * even for round-robin; Q is np x np FP32 or NULL; both device, column-major,
