@@ -24,8 +24,10 @@
 //     stage 2 (V1^T(m, kk) = V1(kk, m)), so stages copy it with 16-byte loads;
 //   * FP32 operands (A blocks, Q columns, T) are loaded eight values per
 //     thread item with all loads of a chunk issued back to back into
-//     registers one chunk ahead, then split and stored to shared memory;
-//   * three pipeline stages of 32 KB; one thread issues the chunk's six MMAs
+//     registers two chunks ahead (two register slots), then split (paired
+//     conversions) and stored to shared memory;
+//   * two pipeline stages of 32 KB (three CTAs per SM; tf32: three stages of
+//     64 KB, one CTA per SM); one thread issues the chunk's six MMAs
 //     and commits them to the stage's mbarrier, which the stage's next
 //     filling waits for (bounded wait: a timeout sets the error word, the
 //     CTA skips the remaining work and still frees its TMEM);
