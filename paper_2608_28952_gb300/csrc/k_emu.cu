@@ -10,10 +10,11 @@
 // p holds d_p 2^{-7(p-1)} (exact in bf16).  Columns of Bop likewise with F_n.
 // Then a = 2^{E_m - 7} sum_p A_p and
 //     C(m, n) = 2^{E_m + F_n - 14} sum_{p + q <= 9} sum_k A_p(m, k) B_q(k, n).
-// A product A_p B_q is an integer times 2^{-7(p + q - 2)}; with K <= 256 the
+// A product A_p B_q is an integer times 2^{-7(p + q - 2)}; with K <= 512 the
 // sums of level l = p + q - 2 <= 4 stay below 2^24 in magnitude (|d_1| <= 128,
-// |d_p| <= 64 for p > 1) and are exact in the FP32 accumulators of the tensor
-// cores, one accumulator per level; levels 5..7 (relative weight <= 2^-35)
+// |d_p| <= 64 for p > 1: level 4, the largest, has 2 * 128 * 64 + 3 * 64 * 64
+// = 28672 per K value, 28672 * 512 < 2^24) and are exact in the FP32
+// accumulators of the tensor cores, one accumulator per level; levels 5..7 (relative weight <= 2^-35)
 // share one.  The accumulators are combined exactly in 64-bit integers (units
 // of 2^-35) and converted once.  The dropped products (p + q > 9), the
 // rounding to 56 fraction bits and the rounding of the lowest levels in the
@@ -26,8 +27,8 @@
 // of A, 128 x 32, and of B, 64 x 32, in the canonical no-swizzle K-major
 // layout); one thread issues the 72 MMAs of a chunk (2 K steps x 36 slice
 // products) and commits them to the stage's mbarrier (bounded waits).  For
-// K > 256 the accumulators are drained into 64-bit integer running sums
-// every 256 K values (emu_tile<true>).
+// K > 256 (emu_tile<true>) the accumulators are drained into 64-bit integer
+// running sums every 512 K values.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,7 +41,7 @@ namespace jac {
 namespace {
 
 constexpr int EM = 128, EN = 64, EK = 32, ENS = 8, ENACC = 6, E_T = 256;
-constexpr int E_KSUPER = 256;   // K values per exact FP32 accumulation
+constexpr int E_KSUPER = 512;   // K values per exact FP32 accumulation (the bound above)
 constexpr int E_ATILE = EM * EK * 2;                      // one A slice tile (8 KB)
 constexpr int E_BTILE = EN * EK * 2;                      // one B slice tile (4 KB)
 constexpr int E_STAGE = ENS * (E_ATILE + E_BTILE);        // 96 KB
@@ -149,10 +150,10 @@ __device__ __forceinline__ double i64_scaled(long long sv, int e)
 // fa(m, k), fb(k, n): FP64 operand values (0 outside); eA[m], eB[n]: the
 // row / column scale exponents in shared memory (filled by the caller, all
 // threads synchronised); st(m, n, v) stores.  K <= 256 unless BIG: then the
-// accumulators are drained every 256 K values (so every level sum stays
-// exact in FP32) into 64-bit integer running sums held in registers, in
+// accumulators are drained every E_KSUPER = 512 K values (so every level sum
+// stays exact in FP32) into 64-bit integer running sums held in registers, in
 // units of 2^{sh - 35} with sh = the shift that keeps |sum| below 2^63
-// (sh = 0 up to K = 8192).
+// (sh = 0 up to K = 8192: 16 drains of |S| < 2^58.02).
 //
 // AIMG / BIMG: the operand's slices come pre-made from an image in global
 // memory instead (slice p of chunk c: E_ATILE / E_BTILE bytes in the MMA
@@ -205,8 +206,8 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
 #pragma unroll
     for (int u = 0; u < (BIG ? 32 : 1); ++u) R[u] = 0;
     // The exact levels hold integers I_l 2^{-7l} (|I_l| < 2^24): their sum is
-    // the integer S = sum_l I_l 2^{7(5-l)} in units of 2^-35 (|S| < 2^58 for
-    // K <= 256), formed exactly in 64-bit integers; the shared low levels
+    // the integer S = sum_l I_l 2^{7(5-l)} in units of 2^-35 (|I_0| <= 2^23,
+    // so |S| < 2^58.02 for K <= 512), formed exactly in 64-bit integers; the shared low levels
     // (weights 2^-35 .. 2^-49) are rounded to that unit, 2^-57 of the level-0
     // unit.  One conversion to FP64, the scale 2^{E_m + F_n - 49} in the
     // exponent field.
@@ -230,7 +231,7 @@ __device__ void emu_tile(int K, FA fa, FB fb, const int* eA, const int* eB, ST s
                 const float up = __int_as_float((127 + (l < ENACC - 1 ? 7 * l : 7 * l - sh)) << 23);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int x = __float2int_rn(__uint_as_float(v[u]) * up);   // |x| < 2^24 (2^17 for the shared one)
+                    const int x = __float2int_rn(__uint_as_float(v[u]) * up);   // |x| < 2^24 (2^18 for the shared one)
                     S[u] += l < ENACC - 1 ? ((long long)x << (7 * (ENACC - 1 - l) - sh)) : (long long)x;
                 }
             }
