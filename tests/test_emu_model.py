@@ -7,8 +7,9 @@ rely on, independently of them.
     when x is within four binades of the scale, else rounded) with balanced
     base-2^7 digits d_1 in [0, 128] and d_2..d_8 in [-64, 63]; each slice
     d_p 2^(-7(p-1)) is exact in bf16 (8 significant bits).
-  * For K <= 256 the level sums of the slice products with p + q - 2 <= 4
-    stay below 2^24, i.e. exact in an FP32 accumulator.
+  * For K <= 512 (the kernels' exact accumulation) the level sums of the
+    slice products with p + q - 2 <= 4 stay below 2^24, i.e. exact in an
+    FP32 accumulator.
   * Keeping the 36 products with p + q <= 9 (levels 5..7 in one FP32
     accumulator) gives |C - AB| <= (9K + 64) 2^-56 2^(E_m + F_n) per entry.
 The model rounds the shared FP32 accumulator once at the end, whereas the
@@ -96,16 +97,17 @@ def test_digits_reconstruct_and_stay_in_range():
         assert all(abs(v) < 256 for v in d)
 
 
-def test_level_sums_stay_exact_in_fp32_for_k_256():
+def test_level_sums_stay_exact_in_fp32_for_k_512():
     """Worst-case digits (|d_1| = 128, |d_p| = 64): the level sums of
-    levels 0..4 over K = 256 terms stay below 2^24."""
-    K = 256
+    levels 0..4 over K = 512 terms (the kernels' exact accumulation) stay
+    below 2^24."""
+    K = 512
     mx = [128] + [64] * 7
     for l in range(5):
         worst = K * sum(mx[p - 1] * mx[q - 1] for p in range(1, 9) for q in range(1, 10 - p) if p + q - 2 == l)
         assert worst < (1 << 24), (l, worst)
     # the largest K that keeps every level exact: 585 (level 4 dominates), so
-    # the long products drain their accumulators every 256 values with margin
+    # the long products drain their accumulators every 512 values
     per_term = max(sum(mx[p - 1] * mx[q - 1] for p in range(1, 9) for q in range(1, 10 - p) if p + q - 2 == l)
                    for l in range(5))
     assert per_term == 2 * 128 * 64 + 3 * 64 * 64
@@ -130,10 +132,11 @@ def test_error_bound(K, seed, graded):
             assert err <= bound, (i, j, float(err / bound))
 
 
-def test_adversarial_lines_of_equal_magnitude():
+@pytest.mark.parametrize("K", [128, 512])
+def test_adversarial_lines_of_equal_magnitude(K):
     """Every entry just below the scale (the largest digits in every slot):
-    still within the bound."""
-    K = 128
+    still within the bound, and over one exact accumulation of K = 512 the
+    level sums stay exact."""
     v = np.full(K, 1.0 - 2.0 ** -53)
     A = (v * np.where(np.arange(K) % 2 == 0, 1.0, -1.0))[None, :]
     B = v[:, None]
